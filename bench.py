@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the preconditioned GLBE time step on GB300.
+
+Default workload (one GPU): the square duct of 256 x 256 cross-section and
+512 nodes streamwise (x periodic, half-way bounce-back walls on y and z),
+body force F_x(y, z) = F0 (1 + 0.5 sin(2 pi y/L_y) cos(2 pi z/L_z)),
+F0 = 1e-6, nu = 0.5, gamma = 0.1, D3Q19 MRT-GLBE, population deviations
+stored in BF16 with FP32 collide arithmetic.  One bench step = 10 time steps
+(one residual period: 9 plain fused steps, 1 fused step with the FP64
+residual reduction and its finalize kernel).  Inputs (1.27 GB per population
+buffer) are larger than L2, so no flush is needed.
+
+The JSON line reports MLUPS (fluid-node updates per second, millions), the
+roofline of the dominant kernel (the plain fused step) against the measured
+HBM copy bandwidth, the end-to-end rate through the C-ABI with host buffers,
+sampled SM clocks, the FP64 CPU oracle timed on a bounded sample, and
+variants: FP32 / FP16 storage on the same duct, the fused D3Q19 + D3Q7 step
+on the 128^3 Hartmann duct, and wall time to a 1e-8 residual at gamma = 0.1
+vs gamma = 1 on the 64 x 64 x 8 Hartmann duct.
+
+Multi-GPU: replicas only (each rank runs the same workload on its own GPU;
+no data-path collective); the value aggregates all ranks, timing is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+W19 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
+
+DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20, help="timed bench steps (10 time steps each)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["glbe", "reference"], default="glbe")
+    ap.add_argument("--storage", choices=["bf16", "f16", "f32"], default="bf16")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """Maximum of a scalar over all ranks (identity for one rank)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        # address the GPU by UUID: CUDA and nvidia-smi may number GPUs differently
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.gpu = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            self.gpu = str(device_index)
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def duct_solver(storage: str, device="cuda"):
+    import torch
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    d = DUCT
+    G = Solver(d["nx"], d["ny"], d["nz"], wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=d["gamma"], nu=d["nu"],
+               force_field=1, storage=storage, device=device)
+    Fx = duct_force_x(d["nx"], d["ny"], d["nz"], d["F0"])[0].reshape(1, -1)
+    F_host = torch.tensor(Fx, dtype=torch.float32).pin_memory()
+    G.set_force(F_host.to(device))
+    fluid = d["nx"] * (d["ny"] - 2) * (d["nz"] - 2)
+    return G, F_host, fluid
+
+
+def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda"):
+    """Hartmann duct of n^3 nodes: x periodic, walls on y and z, B0 along y,
+    nu = eta = 0.01, chi = 0.01 (Pr_m = 0.01), F_x = 1e-6, FP32."""
+    from paper_0809_4730_gb300.glbe import Solver
+    nu = eta = 0.01
+    L = (n - 2) / 2
+    B0 = Ha * math.sqrt(nu * eta) / L
+    G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
+               gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0), device=device)
+    return G, n * (n - 2) * (n - 2)
+
+
+def bytes_per_node(storage: str, mhd: bool, force_comp: int) -> int:
+    ss = 4 if storage == "f32" else 2
+    b = 19 * ss * 2 + 4 * force_comp
+    if mhd:
+        b += 21 * ss * 2 + 3 * 4 * 2
+    return b
+
+
+def timed_steps(G, K, stream):
+    """K bench steps of 10 time steps each on stream; returns (total ms,
+    plain-kernel ms total, plain launches) from CUDA events recorded on the
+    launching stream inside the timed region."""
+    import torch
+    assert G.t % 10 == 0
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for a, b, c in evs:
+        a.record(stream)
+        G.step(1)          # fused step with the residual reduction (+ finalize)
+        b.record(stream)
+        G.step(9)          # nine plain fused steps
+        c.record(stream)
+    end.record(stream)
+    end.synchronize()
+    total = start.elapsed_time(end)
+    plain = sum(b.elapsed_time(c) for _, b, c in evs)
+    return total, plain, 9 * K
+
+
+def run_glbe(args, rank, ws):
+    import torch
+    stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+
+    G, F_host, fluid = duct_solver(args.storage)
+    G.step(10 * args.warmup)
+    G.residual()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        total_ms, plain_ms, nplain = timed_steps(G, args.steps, stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    info = G.residual()
+    total_ms = max_over_ranks(total_ms, ws)
+    updates = 10 * args.steps * fluid
+    mlups = updates / (total_ms * 1e-3) / 1e6 * ws
+    kern_ms = plain_ms / nplain
+    bpn = bytes_per_node(args.storage, False, 1)
+    achieved = bpn * fluid / (kern_ms * 1e-3) / 1e9
+    line = {
+        "metric": "MLUPS (fluid-node updates/s) and % of HBM roofline of the fused GLBE step",
+        "value": round(mlups, 1),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": "square duct 512x256x256 (x periodic, walls y/z), Fx(y,z) = F0(1+0.5 sin cos), "
+                        "F0=1e-6, nu=0.5, gamma=0.1, D3Q19 MRT-GLBE, " + args.storage + " deviation storage, "
+                        "FP32 collide; 1 bench step = 10 time steps incl. FP64 residual",
+            "nodes": DUCT["nx"] * DUCT["ny"] * DUCT["nz"],
+            "fluid_nodes": fluid,
+            "storage": args.storage,
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": hbm_peak,
+            "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4),
+            "traffic": None,
+            "kernel": "step_kernel (plain fused collide+stream)",
+            "bytes_per_node": bpn,
+            "kernel_ms": round(kern_ms, 5),
+            "peak_source": peak_src,
+        },
+        "gpu_launches": 11 * args.steps,
+        "residual_at_end": {"t": info.t, "r": info.r},
+        "clocks": clk.summary(),
+    }
+    # end to end through the C-ABI with host buffers: H2D of the force field
+    # from pinned memory, 10 steps, D2H of the residual record (syncs).
+    from paper_0809_4730_gb300.glbe import glbe_set_force_host
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        glbe_set_force_host(G.ctx, F_host)
+        G.step(10)
+        G.residual()
+    t1 = time.perf_counter()
+    e2e_s = max_over_ranks(t1 - t0, ws)
+    line["e2e"] = {"value": round(updates / e2e_s / 1e6 * ws, 1), "unit": "MLUPS",
+                   "h2d_bytes_per_step": F_host.numel() * 4, "d2h_bytes_per_step": 16 * 8}
+    G.close()
+    del G
+    torch.cuda.empty_cache()
+
+    if not args.no_variants:
+        line["variants"] = variants(args, hbm_peak, stream)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    return line
+
+
+def variants(args, hbm_peak, stream):
+    import torch
+    out = {}
+    for st in ("f32", "f16", "bf16"):
+        if st == args.storage:
+            continue
+        G, _, fluid = duct_solver(st)
+        G.step(30)
+        G.sync()
+        total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
+        kern_ms = plain_ms / nplain
+        bpn = bytes_per_node(st, False, 1)
+        out[f"duct_{st}"] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1),
+                             "kernel_ms": round(kern_ms, 5), "bytes_per_node": bpn,
+                             "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+    # fused D3Q19 + D3Q7 on the 128^3 Hartmann duct (FP32)
+    G, fluid = hartmann_duct_solver()
+    G.step(30)
+    G.sync()
+    total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
+    kern_ms = plain_ms / nplain
+    bpn = bytes_per_node("f32", True, 0)
+    out["mhd_duct_128_f32"] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
+                               "bytes_per_node": bpn,
+                               "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+    G.close()
+    del G
+    torch.cuda.empty_cache()
+    out["time_to_1e-8_hartmann_64x64x8"] = time_to_solution()
+    return out
+
+
+def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
+    """Insulating-wall Hartmann profile with the walls half-way between the
+    solid and first fluid rows (half-width L = (ny - 2)/2)."""
+    L = (ny - 2) / 2
+    A = F * L * L / (nu * Ha * math.tanh(Ha))
+    return [A * (1 - math.cosh(Ha * (y - (ny - 1) / 2) / L) / math.cosh(Ha)) for y in range(ny)]
+
+
+def time_to_solution():
+    """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Ha = 10,
+    Pr_m = 0.01, nu = eta = 0.01) at gamma = gamma_m = 0.1 and 1, same GPU,
+    with the error of the converged u against the analytic profile."""
+    import torch
+    from paper_0809_4730_gb300.glbe import Solver
+    res = {}
+    Ha, nu, eta, chi = 10.0, 0.01, 0.01, 0.01
+    B0 = Ha * math.sqrt(nu * eta) / 31.0
+    ua = hartmann_analytic(64, Ha)
+    for gamma in (0.1, 1.0):
+        G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
+                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, steps, r = G.solve(1e-8, 3_000_000)
+        t1 = time.perf_counter()
+        _, u, _ = G.fields()
+        G.sync()
+        ux = u[0].reshape(8, 64, 64)[0, :, 0].double().cpu().tolist()
+        err = max(abs(ux[y] - ua[y]) for y in range(1, 63)) / max(ua)
+        res[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r, "wall_s": round(t1 - t0, 4),
+                                 "err_vs_analytic": err}
+        G.close()
+    a, b = res["gamma_0.1"], res["gamma_1.0"]
+    res["speedup_wall"] = round(b["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
+    res["speedup_steps"] = round(b["steps"] / max(1, a["steps"]), 2)
+    return res
+
+
+# ---------------------------------------------------------------------------
+# FP64 CPU oracle (the baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample():
+    """A bounded sample of the duct workload the CPU oracle can time: an
+    8-node-long slab of the same 256 x 256 cross-section (x periodic, the
+    force is x-invariant)."""
+    import numpy as np
+    import oracle
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    d = DUCT
+    nx = 8
+    cfg = oracle.Config(nx, d["ny"], d["nz"], wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=d["gamma"], nu=d["nu"])
+    F = duct_force_x(nx, d["ny"], d["nz"], d["F0"]).reshape(3, -1).T.copy()
+    S = oracle.Solver(cfg, Fext=F)
+    fluid = nx * (d["ny"] - 2) * (d["nz"] - 2)
+    return S, fluid, f"oracle FP64 on an {nx}x{d['ny']}x{d['nz']} slab of the duct"
+
+
+def cpu_baseline(target_s: float = 10.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    S, fluid, desc = oracle_sample()
+    t0 = time.perf_counter()
+    S.run(2)
+    dt = max(1e-6, time.perf_counter() - t0)
+    n = max(2, min(400, int(target_s / (dt / 2))))
+    t0 = time.perf_counter()
+    S.run(n)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * fluid / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{desc}, {n} time steps, {dt:.1f} s"}
+
+
+def run_reference(args, rank, ws):
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    S, fluid, desc = oracle_sample()
+    S.run(10 * args.warmup)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.run(10)
+    dt = time.perf_counter() - t0
+    mlups = 10 * args.steps * fluid / dt / 1e6
+    return {
+        "impl": "reference",
+        "metric": "MLUPS (fluid-node updates/s) and % of HBM roofline of the fused GLBE step",
+        "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "square duct 512x256x256 (bounded sample: 8x256x256 slab), Fx(y,z), nu=0.5, "
+                               "gamma=0.1, D3Q19 MRT-GLBE, FP64 CPU oracle", "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": f"{desc}, {10 * args.steps} time steps"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        # CPU oracle: rank 0 alone runs it; other ranks exit without work
+        rank = int(os.environ.get("RANK", "0"))
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, ws)), flush=True)
+        return
+    rank, ws = dist_init(args)
+    line = run_glbe(args, rank, ws)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * glbe.h -- C-ABI of the GB300 (sm_103a) library for the preconditioned
+ * generalized lattice Boltzmann equation (GLBE) with forcing term, coupled to
+ * the preconditioned D3Q7 vector lattice kinetic equation for the magnetic
+ * induction (Premnath, Pattison & Banerjee, arXiv:0809.4730).
+ *
+ * One time step (glbe_step_n) is one fused kernel launch per node:
+ *   - macroscopic fields rho = sum f, j = sum f e + F/(2 gamma)
+ *     (Eq. precondhydrofields);
+ *   - D3Q19 multiple-relaxation-time collision in moment space with the
+ *     gamma-preconditioned equilibrium moments, the preconditioned source
+ *     S* = P_S S and the rates Lambda* (Sec. 3, Eqs. ppostcollision,
+ *     prelax_term, precondsourceterm; tables of App. A);
+ *   - optional D3Q7 vector kinetic equation: B = sum g, g^eq,* with the chi
+ *     scaling, J = (1/(mu chi)) curl B from the non-equilibrium first moment,
+ *     Lorentz force J x B added to the body force (Sec. 4, Sec. 4.1);
+ *   - streaming (Eqs. pstreaming, mstreaming) with half-way bounce-back walls
+ *     for f and anti-bounce-back (insulating walls, B = B0) for g (Sec. 5);
+ *   - every 10th time level: the velocity residual
+ *     r(t) = ||u(t) - u(t-10)||_2 / ||u(t)||_2 with FP64 sums of mass and
+ *     momentum (Sec. 5).
+ *
+ * Conventions
+ *   - Lattice ordering (the paper lists the velocity groups only):
+ *       D3Q19: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..10 = (1,1,0),(-1,1,0),
+ *       (1,-1,0),(-1,-1,0); 11..14 = (1,0,1),(-1,0,1),(1,0,-1),(-1,0,-1);
+ *       15..18 = (0,1,1),(0,-1,1),(0,1,-1),(0,-1,-1).
+ *       D3Q7: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z.
+ *   - Array layout at this boundary: structure of arrays, [component][z][y][x]
+ *     with x fastest; N = nx*ny*nz.  g is [j][a][z][y][x] (component j of B,
+ *     direction a).  All arrays passed in or out are FP32 unless stated.
+ *   - Populations crossing this boundary are deviations from the rest state:
+ *     df_a = f_a - w_a rho0 and dg_ja = g_ja - W_a B0_j.
+ *   - A node is solid when it lies on a wall plane (wall_lo/wall_hi below);
+ *     values of solid nodes in outputs are 0 and in inputs are ignored.
+ *   - Memory: the caller owns every device buffer, including the workspace
+ *     handed to glbe_init (size from glbe_workspace_bytes).  The library never
+ *     allocates or frees device memory.  glbe_destroy frees host state only.
+ *   - Streams: every call enqueues work on params.stream (a cudaStream_t,
+ *     NULL = legacy default stream) and returns without waiting, except
+ *     glbe_residual, glbe_solve and glbe_sync, which synchronise that stream.
+ *   - Errors: every call returns a glbe_status; glbe_last_error() gives a
+ *     thread-local message for the last failure.  No call aborts or throws.
+ *   - A context is used from one host thread at a time; separate contexts are
+ *     independent.
+ */
+#ifndef GLBE_H
+#define GLBE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLBE_ABI_VERSION 1
+
+typedef struct glbe_ctx glbe_ctx;
+
+typedef enum {
+    GLBE_OK = 0,
+    GLBE_ERR_ARG = 1,       /* invalid argument (sizes, pointers, parameters)       */
+    GLBE_ERR_CUDA = 2,      /* a CUDA runtime call or kernel launch failed          */
+    GLBE_ERR_DIVERGED = 3,  /* the residual became NaN/Inf (numerical instability)  */
+    GLBE_ERR_TIMEOUT = 4,   /* glbe_solve hit max_steps before reaching tol         */
+    GLBE_ERR_STATE = 5      /* call not valid in the context's current state        */
+} glbe_status;
+
+typedef enum {
+    GLBE_F32 = 0,   /* deviations stored as FP32                                    */
+    GLBE_BF16 = 1,  /* deviations stored as BF16 (round to nearest even), FP32 math */
+    GLBE_F16 = 2    /* deviations stored as FP16, times storage_scale, FP32 math    */
+} glbe_storage;
+
+typedef struct {
+    int nx, ny, nz;           /* grid; x fastest.  N = nx*ny*nz < 2^31          */
+    int wall_lo[3];           /* 1: plane at index 0 along x/y/z is solid (half-way wall at 0.5) */
+    int wall_hi[3];           /* 1: plane at index n-1 is solid; 0 on both: periodic */
+    double rho0;              /* reference density of the rest state            */
+    double gamma;             /* flow preconditioning parameter, 0 < gamma <= 1 (Sec. 3) */
+    double nu;                /* shear viscosity: 1/s_nu* = 3 nu/gamma + 1/2 on rows 9,11,13,14,15 (Sec. 3) */
+    double s[19];             /* relaxation rates of the other rows (kinetic rates of Sec. 3 by default;
+                                 rows 0,3,5,7 are conserved and cannot change the result) */
+    double F[3];              /* uniform external body force                     */
+    int force_field;          /* 0: none; 1: F_x field [N]; 3: field [3][N]; added to F */
+    int induction;            /* 1: couple the D3Q7 vector lattice (Sec. 4)       */
+    double gamma_m;           /* induction preconditioning parameter, 0 < gamma_m <= 1 */
+    double eta;               /* magnetic diffusivity: tau_m* = eta/(gamma_m theta_m) + 1/2 (Eq. mrelaxationtime) */
+    double chi;               /* low-Pr_m scaling factor chi > 0 (Sec. 4.1)      */
+    double mu;                /* magnetic permeability                           */
+    double B0[3];             /* applied field: initial state and wall value      */
+    int storage;              /* glbe_storage                                    */
+    double storage_scale;     /* multiplier on stored deviations; 0 = default (1 for F32/BF16, 4096 for F16) */
+    void* stream;             /* cudaStream_t owned by the caller                */
+} glbe_params;
+
+/* Latest residual evaluation (time level t, a multiple of 10). */
+typedef struct {
+    long t;                   /* time level of u(t); -1 if none evaluated yet    */
+    double r;                 /* ||u(t)-u(t-10)|| / ||u(t)|| over fluid nodes   */
+    double num, den;          /* sum |u(t)-u(t-10)|^2 and sum |u(t)|^2 (FP64)    */
+    double mass;              /* sum rho over fluid nodes (FP64)                 */
+    double momentum[3];       /* sum rho u over fluid nodes (FP64)               */
+    int nonfinite;            /* number of fluid nodes with a NaN/Inf velocity   */
+} glbe_residual_info;
+
+/* Fills p with the defaults: rho0 = 1, gamma = gamma_m = 1, chi = mu = 1,
+ * the kinetic rates of Sec. 3 (s1 = 1.19; s2 = s10 = s12 = 1.4;
+ * s4 = s6 = s8 = 1.2; s16..18 = 1.98; conserved rows 1.0), F32 storage,
+ * no walls, no force, no induction.  Grid and nu are left 0. */
+void glbe_params_default(glbe_params* p);
+
+/* Bytes of device workspace glbe_init needs for these parameters.
+ * Returns GLBE_ERR_ARG for invalid parameters. */
+glbe_status glbe_workspace_bytes(const glbe_params* p, size_t* bytes);
+
+/* Creates a context on the caller's workspace (device memory of at least
+ * glbe_workspace_bytes, 256-byte aligned) and enqueues the rest-state
+ * initialisation (df = 0, dg = 0, Lorentz force 0, t = 0).  The workspace
+ * must stay allocated until glbe_destroy.  *out is NULL on failure. */
+glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glbe_ctx** out);
+
+/* Copies the body-force field (device, FP32, force_field components, layout
+ * [comp][z][y][x]) into the workspace.  The field is added to params.F.
+ * The source may be freed after the copy completes on the stream. */
+glbe_status glbe_set_force(glbe_ctx* ctx, const float* d_F);
+
+/* Same from host memory (pinned memory makes the copy asynchronous; the host
+ * buffer must stay valid until the stream reaches the copy). */
+glbe_status glbe_set_force_host(glbe_ctx* ctx, const float* h_F);
+
+/* Advances n >= 0 time steps (one fused kernel per step; the residual is
+ * evaluated inside the step that collides a level t with t % 10 == 0). */
+glbe_status glbe_step_n(glbe_ctx* ctx, long n);
+
+/* Synchronises the stream and returns the latest residual evaluation.
+ * GLBE_ERR_DIVERGED if it saw a non-finite velocity. */
+glbe_status glbe_residual(glbe_ctx* ctx, glbe_residual_info* out);
+
+/* Time-marches until r(t) <= tol (t a multiple of 10) or max_steps steps have
+ * been taken, replaying a CUDA graph of 10-step chunks.  *steps_out = time
+ * level t of the converged residual (or the level reached), *r_out = r(t).
+ * GLBE_ERR_TIMEOUT if max_steps was reached first, GLBE_ERR_DIVERGED on
+ * NaN/Inf.  Synchronises the stream. */
+glbe_status glbe_solve(glbe_ctx* ctx, double tol, long max_steps, long* steps_out, double* r_out);
+
+/* Macroscopic fields of the current state, as the next collision sees them
+ * (rho, u = j/rho with the half-force, B = sum g).  d_rho [N], d_u [3][N],
+ * d_B [3][N] (ignored and may be NULL without induction).  Any output may be
+ * NULL. */
+glbe_status glbe_fields(glbe_ctx* ctx, float* d_rho, float* d_u, float* d_B);
+
+/* Current pre-collision state as deviations: d_df [19][N], d_dg [3][7][N]
+ * (induction only), d_FL [3][N] Lorentz force of the last step (induction
+ * only).  NULL outputs are skipped. */
+glbe_status glbe_get_state(glbe_ctx* ctx, float* d_df, float* d_dg, float* d_FL);
+
+/* Replaces the state by the given pre-collision deviations (layout as in
+ * glbe_get_state; NULL d_dg / d_FL leave those parts unchanged) at time
+ * level t >= 0.  Clears the residual snapshot. */
+glbe_status glbe_set_state(glbe_ctx* ctx, const float* d_df, const float* d_dg, const float* d_FL, long t);
+
+/* Current time level. */
+glbe_status glbe_time(const glbe_ctx* ctx, long* t);
+
+/* Synchronises the context's stream; reports asynchronous CUDA errors. */
+glbe_status glbe_sync(glbe_ctx* ctx);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* glbe_last_error(void);
+
+/* Frees the host-side context (not the workspace). NULL is ignored. */
+void glbe_destroy(glbe_ctx* ctx);
+
+/* ABI version of the loaded library (GLBE_ABI_VERSION). */
+int glbe_abi_version(void);
+
+/* sizeof(glbe_params) and sizeof(glbe_residual_info) as compiled into the
+ * library, so that bindings can verify their struct mirrors. */
+void glbe_struct_sizes(size_t* params_bytes, size_t* info_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLBE_H */

@@ -1,0 +1,607 @@
+// glbe_api.cu -- host side of the C-ABI declared in include/glbe.h.
+//
+// The library owns no device memory: glbe_init carves the caller's workspace
+// into the two population buffers (ping-pong of the pull scheme), the lagged
+// Lorentz force, the body-force field, the velocity snapshot of the residual,
+// per-block FP64 partial sums and a small record/history area.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "glbe.h"
+#include "glbe_internal.h"
+
+using namespace glbe;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+glbe_status fail(glbe_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+glbe_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(GLBE_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define GLBE_CUDA(call, what)                         \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr double THETA_M = 0.25;        // theta_m = 1/N_m, N_m = 4 (Sec. 4)
+constexpr unsigned HIST_CAP = 4096;     // residual records kept on the device
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t f[2], g[2], FL, Ffield, usnap, partials, record, hist, misc, total;
+};
+
+size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : 2; }
+
+unsigned step_grid(size_t N) { return (unsigned)((N + STEP_THREADS - 1) / STEP_THREADS); }
+
+Layout make_layout(const glbe_params* p)
+{
+    Layout L{};
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    const size_t ss = storage_bytes(p->storage);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L.f[0] = take(19 * N * ss);
+    L.f[1] = take(19 * N * ss);
+    if (p->induction) {
+        L.g[0] = take(21 * N * ss);
+        L.g[1] = take(21 * N * ss);
+        L.FL = take(3 * N * sizeof(float));
+    } else {
+        L.g[0] = L.g[1] = L.FL = (size_t)-1;
+    }
+    L.Ffield = p->force_field ? take((size_t)p->force_field * N * sizeof(float)) : (size_t)-1;
+    L.usnap = take(3 * N * sizeof(float));
+    L.partials = take((size_t)step_grid(N) * PARTIAL_STRIDE * sizeof(double));
+    L.record = take(RECORD_STRIDE * sizeof(double));
+    L.hist = take((size_t)HIST_CAP * RECORD_STRIDE * sizeof(double));
+    L.misc = take(64);
+    L.total = off;
+    return L;
+}
+
+glbe_status validate(const glbe_params* p)
+{
+    if (!p) return fail(GLBE_ERR_ARG, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GLBE_ERR_ARG, "grid sizes must be >= 1");
+    const unsigned long long N = (unsigned long long)p->nx * p->ny * p->nz;
+    if (N >= (1ull << 31)) return fail(GLBE_ERR_ARG, "nx*ny*nz = %llu must be < 2^31", N);
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; ++d) {
+        if ((p->wall_lo[d] | p->wall_hi[d]) & ~1) return fail(GLBE_ERR_ARG, "wall flags must be 0 or 1");
+        if (n[d] - p->wall_lo[d] - p->wall_hi[d] < 1)
+            return fail(GLBE_ERR_ARG, "axis %d has no fluid plane between its walls", d);
+    }
+    if (!(p->rho0 > 0.0)) return fail(GLBE_ERR_ARG, "rho0 must be > 0");
+    if (!(p->gamma > 0.0 && p->gamma <= 1.0)) return fail(GLBE_ERR_ARG, "gamma must be in (0, 1]");
+    if (!(p->nu > 0.0)) return fail(GLBE_ERR_ARG, "nu must be > 0");
+    for (int k = 0; k < 19; ++k)
+        if (!(p->s[k] > 0.0 && p->s[k] < 2.0)) return fail(GLBE_ERR_ARG, "s[%d] = %g must be in (0, 2)", k, p->s[k]);
+    if (p->force_field != 0 && p->force_field != 1 && p->force_field != 3)
+        return fail(GLBE_ERR_ARG, "force_field must be 0, 1 or 3");
+    if (p->induction != 0 && p->induction != 1) return fail(GLBE_ERR_ARG, "induction must be 0 or 1");
+    if (p->induction) {
+        if (!(p->gamma_m > 0.0 && p->gamma_m <= 1.0)) return fail(GLBE_ERR_ARG, "gamma_m must be in (0, 1]");
+        if (!(p->eta > 0.0)) return fail(GLBE_ERR_ARG, "eta must be > 0");
+        if (!(p->chi > 0.0)) return fail(GLBE_ERR_ARG, "chi must be > 0");
+        if (!(p->mu > 0.0)) return fail(GLBE_ERR_ARG, "mu must be > 0");
+    }
+    if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16)
+        return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16 or GLBE_F16");
+    if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
+        return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
+    return GLBE_OK;
+}
+
+StepParams make_step_params(const glbe_params* p)
+{
+    StepParams s{};
+    s.nx = p->nx;
+    s.ny = p->ny;
+    s.nz = p->nz;
+    s.N = (uint32_t)((size_t)p->nx * p->ny * p->nz);
+    s.div_nx = make_fastdiv((uint32_t)p->nx);
+    s.div_nxy = make_fastdiv((uint32_t)(p->nx * p->ny));
+    for (int d = 0; d < 3; ++d) {
+        s.wlo[d] = p->wall_lo[d];
+        s.whi[d] = p->wall_hi[d];
+        s.F[d] = (float)p->F[d];
+        s.B0[d] = (float)p->B0[d];
+        s.bwall_dev[d] = 0.f;
+    }
+    s.rho0 = (float)p->rho0;
+    s.inv_gamma = (float)(1.0 / p->gamma);
+    s.inv_gamma2 = (float)(1.0 / (p->gamma * p->gamma));
+    // Lambda*: 1/s_nu* = 3 nu / gamma + 1/2 on the viscous rows (Sec. 3)
+    const double snu = 1.0 / (3.0 * p->nu / p->gamma + 0.5);
+    for (int k = 0; k < 19; ++k) s.s[k] = (float)p->s[k];
+    s.s[9] = s.s[11] = s.s[13] = s.s[14] = s.s[15] = (float)snu;
+    s.force_ncomp = p->force_field;
+    if (p->induction) {
+        // tau_m* = eta / (gamma_m theta_m) + 1/2 (Eq. mrelaxationtime)
+        const double tau_m = p->eta / (p->gamma_m * THETA_M) + 0.5;
+        s.conv_coef = (float)(p->chi / p->gamma_m);
+        s.omega_m = (float)(1.0 / tau_m);
+        s.J_coef = (float)(-1.0 / (p->mu * p->chi * tau_m * THETA_M));
+    }
+    double scale = p->storage_scale;
+    if (scale == 0.0) scale = p->storage == GLBE_F16 ? 4096.0 : 1.0;
+    s.scale = (float)scale;
+    s.inv_scale = (float)(1.0 / scale);
+    return s;
+}
+
+__global__ void finalize_kernel(const double* __restrict__ partials, unsigned nblocks, long long* t_dev,
+                                double* record, double* hist, unsigned long long* hist_count, unsigned hist_cap,
+                                int* stop, const double* tol)
+{
+    if (*stop) return;   // a solve already converged: the chunk's remaining work is skipped
+    __shared__ double sh[7][256];
+    for (int k = 0; k < 7; ++k) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * PARTIAL_STRIDE + k];
+        sh[k][threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double num = sh[0][0], den = sh[1][0];
+        const double r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        const long long t = *t_dev;
+        double rec[RECORD_STRIDE] = {0};
+        rec[0] = (double)t;
+        rec[1] = r;
+        rec[2] = num;
+        rec[3] = den;
+        rec[4] = sh[2][0];
+        rec[5] = sh[3][0];
+        rec[6] = sh[4][0];
+        rec[7] = sh[5][0];
+        rec[8] = sh[6][0];
+        for (int k = 0; k < RECORD_STRIDE; ++k) record[k] = rec[k];
+        const unsigned long long c = *hist_count;
+        double* h = hist + (size_t)(c % hist_cap) * RECORD_STRIDE;
+        for (int k = 0; k < RECORD_STRIDE; ++k) h[k] = rec[k];
+        *hist_count = c + 1;
+        *t_dev = t + 10;
+        if ((*tol > 0.0 && r <= *tol) || rec[8] > 0.0 || !isfinite(r)) *stop = 1;
+    }
+}
+
+__global__ void misc_set_kernel(long long* t_dev, long long t, int* stop, int stop_v, double* tol, double tol_v,
+                                double* record, unsigned long long* hist_count, int reset_record)
+{
+    if (t_dev) *t_dev = t;
+    if (stop) *stop = stop_v;
+    if (tol) *tol = tol_v;
+    if (reset_record) {
+        for (int k = 0; k < RECORD_STRIDE; ++k) record[k] = 0.0;
+        record[0] = -1.0;
+        *hist_count = 0;
+    }
+}
+
+}  // namespace
+
+struct glbe_ctx {
+    glbe_params prm;
+    StepParams sp;
+    Layout L;
+    size_t N;
+    unsigned grid;
+    char* ws;
+    void* f[2];
+    void* g[2];
+    float* FL;
+    float* Ffield;
+    float* usnap;
+    double* partials;
+    double* record;
+    double* hist;
+    unsigned long long* hist_count;
+    long long* t_dev;
+    int* stop_dev;
+    double* tol_dev;
+    long t;         // current time level
+    long t_snap;    // level of the velocity snapshot, -1 if none
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t chunk;
+};
+
+namespace {
+
+cudaError_t launch_step_any(glbe_ctx* c, int mode, const StepBuffers& b, const FieldOut& fo, cudaStream_t st)
+{
+    switch (c->prm.storage) {
+    case GLBE_F32: return launch_step_t<ST_F32>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    case GLBE_BF16: return launch_step_t<ST_BF16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    default: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    }
+}
+
+StepBuffers buffers_for(glbe_ctx* c, long t)
+{
+    StepBuffers b{};
+    const int s = (int)(t & 1);
+    b.fsrc = c->f[s];
+    b.fdst = c->f[s ^ 1];
+    b.gsrc = c->prm.induction ? c->g[s] : nullptr;
+    b.gdst = c->prm.induction ? c->g[s ^ 1] : nullptr;
+    b.FL = c->FL;
+    b.Ffield = c->Ffield;
+    b.usnap = c->usnap;
+    b.partials = c->partials;
+    b.have_snap = 0;
+    b.stop = nullptr;
+    return b;
+}
+
+// Enqueues the step from level c->t to c->t + 1 on stream st.
+glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
+{
+    StepBuffers b = buffers_for(c, c->t);
+    b.stop = stop;
+    const FieldOut fo{nullptr, nullptr, nullptr};
+    if (c->t % 10 == 0) {
+        b.have_snap = (c->t_snap >= 0 && c->t_snap == c->t - 10) ? 1 : 0;
+        GLBE_CUDA(launch_step_any(c, MODE_STEP_RESID, b, fo, st), "step kernel (residual)");
+        if (b.have_snap) {
+            GLBE_CUDA(launch_finalize(c->partials, c->grid, c->t_dev, c->record, c->hist, c->hist_count, HIST_CAP,
+                                      c->stop_dev, c->tol_dev, st),
+                      "residual finalize");
+        } else {
+            misc_set_kernel<<<1, 1, 0, st>>>(c->t_dev, (long long)c->t + 10, nullptr, 0, nullptr, 0.0, nullptr,
+                                             nullptr, 0);
+            GLBE_CUDA(cudaGetLastError(), "set residual level");
+        }
+        c->t_snap = c->t;
+    } else {
+        GLBE_CUDA(launch_step_any(c, MODE_STEP, b, fo, st), "step kernel");
+    }
+    c->t += 1;
+    return GLBE_OK;
+}
+
+}  // namespace
+
+namespace glbe {
+cudaError_t launch_finalize(const double* partials, unsigned nblocks, long long* t_dev, double* record, double* hist,
+                            unsigned long long* hist_count, unsigned hist_cap, int* stop, const double* tol,
+                            cudaStream_t st)
+{
+    finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, t_dev, record, hist, hist_count, hist_cap, stop, tol);
+    return cudaGetLastError();
+}
+}  // namespace glbe
+
+extern "C" {
+
+int glbe_abi_version(void) { return GLBE_ABI_VERSION; }
+
+void glbe_struct_sizes(size_t* params_bytes, size_t* info_bytes)
+{
+    if (params_bytes) *params_bytes = sizeof(glbe_params);
+    if (info_bytes) *info_bytes = sizeof(glbe_residual_info);
+}
+
+const char* glbe_last_error(void) { return g_last_error.c_str(); }
+
+void glbe_params_default(glbe_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->rho0 = 1.0;
+    p->gamma = 1.0;
+    for (int k = 0; k < 19; ++k) p->s[k] = 1.0;
+    // kinetic rates of the D3Q19 model quoted in Sec. 3
+    p->s[1] = 1.19;
+    p->s[2] = p->s[10] = p->s[12] = 1.4;
+    p->s[4] = p->s[6] = p->s[8] = 1.2;
+    p->s[16] = p->s[17] = p->s[18] = 1.98;
+    p->gamma_m = 1.0;
+    p->eta = 0.0;
+    p->chi = 1.0;
+    p->mu = 1.0;
+    p->storage = GLBE_F32;
+    p->storage_scale = 0.0;
+    p->stream = nullptr;
+}
+
+glbe_status glbe_workspace_bytes(const glbe_params* p, size_t* bytes)
+{
+    if (!bytes) return fail(GLBE_ERR_ARG, "bytes is NULL");
+    glbe_status s = validate(p);
+    if (s != GLBE_OK) return s;
+    *bytes = make_layout(p).total;
+    return GLBE_OK;
+}
+
+glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glbe_ctx** out)
+{
+    if (!out) return fail(GLBE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    glbe_status s = validate(p);
+    if (s != GLBE_OK) return s;
+    if (!d_workspace) return fail(GLBE_ERR_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_workspace) % ALIGN) != 0)
+        return fail(GLBE_ERR_ARG, "workspace must be %zu-byte aligned", ALIGN);
+    const Layout L = make_layout(p);
+    if (bytes < L.total) return fail(GLBE_ERR_ARG, "workspace of %zu bytes is smaller than the %zu needed", bytes, L.total);
+
+    glbe_ctx* c = new (std::nothrow) glbe_ctx();
+    if (!c) return fail(GLBE_ERR_ARG, "out of host memory");
+    c->prm = *p;
+    c->sp = make_step_params(p);
+    c->L = L;
+    c->N = (size_t)p->nx * p->ny * p->nz;
+    c->grid = step_grid(c->N);
+    c->ws = static_cast<char*>(d_workspace);
+    c->f[0] = c->ws + L.f[0];
+    c->f[1] = c->ws + L.f[1];
+    c->g[0] = p->induction ? c->ws + L.g[0] : nullptr;
+    c->g[1] = p->induction ? c->ws + L.g[1] : nullptr;
+    c->FL = p->induction ? reinterpret_cast<float*>(c->ws + L.FL) : nullptr;
+    c->Ffield = p->force_field ? reinterpret_cast<float*>(c->ws + L.Ffield) : nullptr;
+    c->usnap = reinterpret_cast<float*>(c->ws + L.usnap);
+    c->partials = reinterpret_cast<double*>(c->ws + L.partials);
+    c->record = reinterpret_cast<double*>(c->ws + L.record);
+    c->hist = reinterpret_cast<double*>(c->ws + L.hist);
+    char* misc = c->ws + L.misc;
+    c->hist_count = reinterpret_cast<unsigned long long*>(misc);
+    c->t_dev = reinterpret_cast<long long*>(misc + 8);
+    c->tol_dev = reinterpret_cast<double*>(misc + 16);
+    c->stop_dev = reinterpret_cast<int*>(misc + 24);
+    c->t = 0;
+    c->t_snap = -1;
+    c->stream = static_cast<cudaStream_t>(p->stream);
+    c->cap_stream = nullptr;
+    c->chunk = nullptr;
+
+    // rest state: all deviations zero (all-zero bits in every storage type)
+    cudaError_t e = cudaMemsetAsync(c->ws, 0, L.usnap, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.usnap, 0, 3 * c->N * sizeof(float), c->stream);
+    if (e == cudaSuccess) {
+        misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, 10, c->stop_dev, 0, c->tol_dev, 0.0, c->record,
+                                                c->hist_count, 1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "glbe_init");
+    }
+    *out = c;
+    return GLBE_OK;
+}
+
+void glbe_destroy(glbe_ctx* c)
+{
+    if (!c) return;
+    if (c->chunk) cudaGraphExecDestroy(c->chunk);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+glbe_status glbe_set_force(glbe_ctx* c, const float* d_F)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (!c->prm.force_field) return fail(GLBE_ERR_STATE, "context was created with force_field = 0");
+    if (!d_F) return fail(GLBE_ERR_ARG, "force field is NULL");
+    GLBE_CUDA(cudaMemcpyAsync(c->Ffield, d_F, (size_t)c->prm.force_field * c->N * sizeof(float),
+                              cudaMemcpyDeviceToDevice, c->stream),
+              "glbe_set_force");
+    return GLBE_OK;
+}
+
+glbe_status glbe_set_force_host(glbe_ctx* c, const float* h_F)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (!c->prm.force_field) return fail(GLBE_ERR_STATE, "context was created with force_field = 0");
+    if (!h_F) return fail(GLBE_ERR_ARG, "force field is NULL");
+    GLBE_CUDA(cudaMemcpyAsync(c->Ffield, h_F, (size_t)c->prm.force_field * c->N * sizeof(float),
+                              cudaMemcpyHostToDevice, c->stream),
+              "glbe_set_force_host");
+    return GLBE_OK;
+}
+
+glbe_status glbe_step_n(glbe_ctx* c, long n)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (n < 0) return fail(GLBE_ERR_ARG, "n must be >= 0");
+    for (long k = 0; k < n; ++k) {
+        glbe_status s = enqueue_step(c, c->stream, nullptr);
+        if (s != GLBE_OK) return s;
+    }
+    return GLBE_OK;
+}
+
+glbe_status glbe_sync(glbe_ctx* c)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "glbe_sync");
+    return GLBE_OK;
+}
+
+static glbe_status read_record(glbe_ctx* c, glbe_residual_info* out)
+{
+    double rec[RECORD_STRIDE];
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "residual sync");
+    GLBE_CUDA(cudaMemcpy(rec, c->record, sizeof rec, cudaMemcpyDeviceToHost), "residual read");
+    out->t = (long)rec[0];
+    out->r = rec[1];
+    out->num = rec[2];
+    out->den = rec[3];
+    out->mass = rec[4];
+    out->momentum[0] = rec[5];
+    out->momentum[1] = rec[6];
+    out->momentum[2] = rec[7];
+    out->nonfinite = (int)rec[8];
+    if (out->t >= 0 && (out->nonfinite > 0 || !std::isfinite(out->r)))
+        return fail(GLBE_ERR_DIVERGED, "non-finite velocity at time level %ld", out->t);
+    return GLBE_OK;
+}
+
+glbe_status glbe_residual(glbe_ctx* c, glbe_residual_info* out)
+{
+    if (!c || !out) return fail(GLBE_ERR_ARG, "ctx or out is NULL");
+    return read_record(c, out);
+}
+
+// Builds the graph of one 10-step chunk starting at an even level that is a
+// multiple of 10 with a snapshot at the previous multiple of 10:
+// residual step + finalize, then nine plain steps, each honouring stop_dev.
+static glbe_status build_chunk(glbe_ctx* c)
+{
+    if (c->chunk) return GLBE_OK;
+    if (!c->cap_stream) GLBE_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    const long t_save = c->t, snap_save = c->t_snap;
+    c->t = 10;
+    c->t_snap = 0;
+    GLBE_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    glbe_status s = GLBE_OK;
+    for (int k = 0; k < 10 && s == GLBE_OK; ++k) s = enqueue_step(c, c->cap_stream, c->stop_dev);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->t = t_save;
+    c->t_snap = snap_save;
+    if (s != GLBE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&c->chunk, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->chunk = nullptr;
+        return cuda_fail(e, "graph instantiate");
+    }
+    return GLBE_OK;
+}
+
+glbe_status glbe_solve(glbe_ctx* c, double tol, long max_steps, long* steps_out, double* r_out)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (!(tol > 0.0)) return fail(GLBE_ERR_ARG, "tol must be > 0");
+    if (max_steps < 0) return fail(GLBE_ERR_ARG, "max_steps must be >= 0");
+    const long t_end = c->t + max_steps;
+    // align: level a multiple of 10 with a snapshot of the previous multiple of 10
+    while (!(c->t % 10 == 0 && c->t_snap >= 0 && c->t_snap == c->t - 10) && c->t < t_end) {
+        glbe_status s = enqueue_step(c, c->stream, nullptr);
+        if (s != GLBE_OK) return s;
+    }
+    glbe_status s = build_chunk(c);
+    if (s != GLBE_OK) return s;
+    misc_set_kernel<<<1, 1, 0, c->stream>>>(nullptr, 0, c->stop_dev, 0, c->tol_dev, tol, nullptr, nullptr, 0);
+    GLBE_CUDA(cudaGetLastError(), "solve setup");
+    const long batch = 16;       // chunks between host checks
+    int stop = 0;
+    while (c->t + 10 <= t_end) {
+        long nb = 0;
+        for (; nb < batch && c->t + 10 * (nb + 1) <= t_end; ++nb)
+            GLBE_CUDA(cudaGraphLaunch(c->chunk, c->stream), "graph launch");
+        GLBE_CUDA(cudaStreamSynchronize(c->stream), "solve sync");
+        GLBE_CUDA(cudaMemcpy(&stop, c->stop_dev, sizeof(int), cudaMemcpyDeviceToHost), "solve read");
+        if (stop) {
+            glbe_residual_info info;
+            glbe_status rs = read_record(c, &info);
+            c->t = info.t + 1;          // the residual step of level info.t completed
+            c->t_snap = info.t;
+            if (steps_out) *steps_out = info.t;
+            if (r_out) *r_out = info.r;
+            misc_set_kernel<<<1, 1, 0, c->stream>>>(nullptr, 0, c->stop_dev, 0, c->tol_dev, 0.0, nullptr, nullptr, 0);
+            GLBE_CUDA(cudaGetLastError(), "solve reset");
+            return rs;
+        }
+        c->t += 10 * nb;
+        c->t_snap = c->t - 10;
+    }
+    // finish with plain steps if max_steps is not a multiple of 10
+    while (c->t < t_end) {
+        s = enqueue_step(c, c->stream, nullptr);
+        if (s != GLBE_OK) return s;
+    }
+    glbe_residual_info info;
+    s = read_record(c, &info);
+    if (steps_out) *steps_out = c->t;
+    if (r_out) *r_out = info.t >= 0 ? info.r : NAN;
+    if (s != GLBE_OK) return s;
+    if (info.t >= 0 && info.r <= tol) return GLBE_OK;
+    return fail(GLBE_ERR_TIMEOUT, "residual %g > tol %g after %ld steps", info.r, tol, max_steps);
+}
+
+glbe_status glbe_fields(glbe_ctx* c, float* d_rho, float* d_u, float* d_B)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    StepBuffers b = buffers_for(c, c->t);
+    const FieldOut fo{d_rho, d_u, c->prm.induction ? d_B : nullptr};
+    GLBE_CUDA(launch_step_any(c, MODE_FIELDS, b, fo, c->stream), "fields kernel");
+    return GLBE_OK;
+}
+
+glbe_status glbe_get_state(glbe_ctx* c, float* d_df, float* d_dg, float* d_FL)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    const int s = (int)(c->t & 1);
+    const bool mhd = c->prm.induction;
+    cudaError_t e;
+    switch (c->prm.storage) {
+    case GLBE_F32: e = launch_get_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_BF16: e = launch_get_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    default: e = launch_get_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    }
+    GLBE_CUDA(e, "get_state kernel");
+    return GLBE_OK;
+}
+
+glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, const float* d_FL, long t)
+{
+    if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (t < 0) return fail(GLBE_ERR_ARG, "t must be >= 0");
+    const int s = (int)(t & 1);
+    const bool mhd = c->prm.induction;
+    cudaError_t e;
+    switch (c->prm.storage) {
+    case GLBE_F32: e = launch_set_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_BF16: e = launch_set_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    default: e = launch_set_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    }
+    GLBE_CUDA(e, "set_state kernel");
+    c->t = t;
+    c->t_snap = -1;
+    return GLBE_OK;
+}
+
+glbe_status glbe_time(const glbe_ctx* c, long* t)
+{
+    if (!c || !t) return fail(GLBE_ERR_ARG, "ctx or t is NULL");
+    *t = c->t;
+    return GLBE_OK;
+}
+
+}  // extern "C"

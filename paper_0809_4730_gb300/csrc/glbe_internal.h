@@ -1,0 +1,100 @@
+// glbe_internal.h -- structures shared by the host side of the C-ABI
+// (glbe_api.cu) and the kernel translation units (glbe_step_*.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace glbe {
+
+// Unsigned division by a run-time constant d >= 1 for dividends n < 2^31:
+// q = (umulhi(n, m) + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1 (Granlund & Montgomery, PLDI 1994).
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    return f;
+}
+
+// Per-launch constants of the fused step (passed by value: kernel parameter
+// space, uniform across the grid).
+struct StepParams {
+    int nx, ny, nz;
+    uint32_t N;
+    FastDiv div_nx, div_nxy;
+    int wlo[3], whi[3];
+    float rho0;
+    float inv_gamma;      // 1/gamma
+    float inv_gamma2;     // 1/gamma^2
+    float s[19];          // Lambda* diagonal
+    float F[3];           // uniform force
+    int force_ncomp;      // 0, 1 (F_x field), 3
+    // D3Q7 vector lattice
+    float conv_coef;      // chi / gamma_m
+    float omega_m;        // 1 / tau_m*
+    float J_coef;         // -1 / (mu chi tau_m* theta_m)
+    float B0[3];
+    float bwall_dev[3];   // B_wall - B0 (0: insulating walls at the applied field)
+    // storage of deviations
+    float scale, inv_scale;
+};
+
+// Buffers of one launch.  Populations are deviations in the storage type,
+// layout [a][N] (f) and [j*7 + a][N] (g).
+struct StepBuffers {
+    const void* fsrc;
+    void* fdst;
+    const void* gsrc;
+    void* gdst;
+    float* FL;            // [3][N] Lorentz force of the previous step (in place)
+    const float* Ffield;  // [force_ncomp][N] or null
+    float* usnap;         // [3][N] velocity snapshot of the last residual level
+    double* partials;     // [gridDim.x][8] per-block residual sums
+    int have_snap;        // 1: usnap holds u(t-10)
+    const int* stop;      // null, or a device flag: when set the launch does nothing
+};
+
+enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
+
+constexpr int STEP_THREADS = 256;
+constexpr int PARTIAL_STRIDE = 8;   // doubles per block: num, den, mass, Mx, My, Mz, nonfinite, pad
+
+// Outputs of MODE_FIELDS.
+struct FieldOut {
+    float* rho;
+    float* u;
+    float* B;
+};
+
+// Launchers, explicitly instantiated per storage type in glbe_step_<storage>.cu.
+template <int ST>
+cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                          unsigned grid, cudaStream_t st);
+template <int ST>
+cudaError_t launch_get_state_t(bool mhd, const StepParams& p, const void* fsrc, const void* gsrc, const float* FL,
+                               float* df, float* dg, float* dFL, cudaStream_t st);
+template <int ST>
+cudaError_t launch_set_state_t(bool mhd, const StepParams& p, void* fsrc, void* gsrc, float* FL, const float* df,
+                               const float* dg, const float* dFL, cudaStream_t st);
+
+// Reduces the per-block partials of a residual step in a fixed order into
+// record[0..8] = (t, r, num, den, mass, Mx, My, Mz, nonfinite), with t read
+// from *t_dev and then advanced by 10, and appends the record to the history
+// ring hist[(count % cap) * RECORD_STRIDE].
+constexpr int RECORD_STRIDE = 16;
+// The reduction also raises *stop when r <= *tol (tol > 0) or a velocity is
+// non-finite, and does nothing once *stop is set.
+cudaError_t launch_finalize(const double* partials, unsigned nblocks, long long* t_dev, double* record,
+                            double* hist, unsigned long long* hist_count, unsigned hist_cap, int* stop,
+                            const double* tol, cudaStream_t st);
+
+}  // namespace glbe

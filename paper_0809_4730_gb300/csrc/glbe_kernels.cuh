@@ -1,0 +1,561 @@
+// glbe_kernels.cuh -- fused time step of the preconditioned GLBE (D3Q19 MRT
+// with forcing) and the preconditioned D3Q7 vector kinetic equation for the
+// magnetic induction, arXiv:0809.4730 Secs. 2-4 and App. A.
+//
+// One thread updates one node (pull scheme): it gathers the post-collision
+// populations of the previous step from its upstream neighbours (half-way
+// bounce-back for f, anti-bounce-back for g where the upstream node is solid),
+// forms the macroscopic fields, collides in moment space and writes the new
+// post-collision populations to its own slot of the other buffer.  Buffers
+// hold deviations from the rest state (df = f - w rho0, dg = g - W B0) so that
+// FP32, BF16 and FP16 storage keep the small part that changes.
+//
+// The moment transform is the integer Gram-Schmidt basis of App. A (rows
+// rho, e, e^2, j, q, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m) applied
+// through partial sums over the velocity groups; the inverse uses the
+// orthogonality of the rows, T^-1 = T^t diag(1/|row_k|^2), with
+// |row_k|^2 = 19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4,
+// 8, 8, 8.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "glbe_internal.h"
+
+namespace glbe {
+
+template <int ST> struct Store;
+template <> struct Store<ST_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float cv(float v) { return v; }
+};
+template <> struct Store<ST_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct Store<ST_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v); }
+};
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
+{
+    return (__umulhi(n, f.m) + n) >> f.s;
+}
+
+__device__ __forceinline__ bool plane_solid(int c, int n, int lo, int hi)
+{
+    return (lo && c == 0) || (hi && c == n - 1);
+}
+
+// Node geometry: coordinates, periodic neighbours, solid flags of the
+// neighbouring planes and the row offsets of the nine (y, z) rows D3Q19 uses.
+struct Geo {
+    uint32_t n;
+    int x, y, z, xm, xp;
+    bool solid;
+    bool sxm, sxp, sym, syp, szm, szp;
+    uint32_t r00, rm0, rp0, r0m, r0p, rmm, rpm, rmp, rpp;   // r<y-shift><z-shift>, m: -1, p: +1
+};
+
+__device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
+{
+    Geo g;
+    g.n = n;
+    const uint32_t zy = fdiv(n, p.div_nx);
+    const uint32_t z = fdiv(n, p.div_nxy);
+    g.x = (int)(n - zy * (uint32_t)p.nx);
+    g.y = (int)(zy - z * (uint32_t)p.ny);
+    g.z = (int)z;
+    const int ym = g.y == 0 ? p.ny - 1 : g.y - 1, yp = g.y == p.ny - 1 ? 0 : g.y + 1;
+    const int zm = g.z == 0 ? p.nz - 1 : g.z - 1, zp = g.z == p.nz - 1 ? 0 : g.z + 1;
+    g.xm = g.x == 0 ? p.nx - 1 : g.x - 1;
+    g.xp = g.x == p.nx - 1 ? 0 : g.x + 1;
+    g.solid = plane_solid(g.x, p.nx, p.wlo[0], p.whi[0]) || plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) ||
+              plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]);
+    g.sxm = plane_solid(g.xm, p.nx, p.wlo[0], p.whi[0]);
+    g.sxp = plane_solid(g.xp, p.nx, p.wlo[0], p.whi[0]);
+    g.sym = plane_solid(ym, p.ny, p.wlo[1], p.whi[1]);
+    g.syp = plane_solid(yp, p.ny, p.wlo[1], p.whi[1]);
+    g.szm = plane_solid(zm, p.nz, p.wlo[2], p.whi[2]);
+    g.szp = plane_solid(zp, p.nz, p.wlo[2], p.whi[2]);
+    const uint32_t nx = (uint32_t)p.nx, ny = (uint32_t)p.ny;
+    g.r00 = (z * ny + (uint32_t)g.y) * nx;
+    g.rm0 = (z * ny + (uint32_t)ym) * nx;
+    g.rp0 = (z * ny + (uint32_t)yp) * nx;
+    g.r0m = ((uint32_t)zm * ny + (uint32_t)g.y) * nx;
+    g.r0p = ((uint32_t)zp * ny + (uint32_t)g.y) * nx;
+    g.rmm = ((uint32_t)zm * ny + (uint32_t)ym) * nx;
+    g.rpm = ((uint32_t)zm * ny + (uint32_t)yp) * nx;
+    g.rmp = ((uint32_t)zp * ny + (uint32_t)ym) * nx;
+    g.rpp = ((uint32_t)zp * ny + (uint32_t)yp) * nx;
+    return g;
+}
+
+// Upstream index and solidity of the source of direction a (source = x - e_a).
+// Pull: f_a(x, t+1) = f~_a(x - e_a, t); if x - e_a is solid the link is
+// bounced: f_a(x, t+1) = f~_abar(x, t).
+#define GLBE_DIRS(X)                                              \
+    X(1, 2, g.r00 + g.xm, g.sxm)                                  \
+    X(2, 1, g.r00 + g.xp, g.sxp)                                  \
+    X(3, 4, g.rm0 + g.x, g.sym)                                   \
+    X(4, 3, g.rp0 + g.x, g.syp)                                   \
+    X(5, 6, g.r0m + g.x, g.szm)                                   \
+    X(6, 5, g.r0p + g.x, g.szp)                                   \
+    X(7, 10, g.rm0 + g.xm, g.sxm || g.sym)                        \
+    X(8, 9, g.rm0 + g.xp, g.sxp || g.sym)                         \
+    X(9, 8, g.rp0 + g.xm, g.sxm || g.syp)                         \
+    X(10, 7, g.rp0 + g.xp, g.sxp || g.syp)                        \
+    X(11, 14, g.r0m + g.xm, g.sxm || g.szm)                       \
+    X(12, 13, g.r0m + g.xp, g.sxp || g.szm)                       \
+    X(13, 12, g.r0p + g.xm, g.sxm || g.szp)                       \
+    X(14, 11, g.r0p + g.xp, g.sxp || g.szp)                       \
+    X(15, 18, g.rmm + g.x, g.sym || g.szm)                        \
+    X(16, 17, g.rpm + g.x, g.syp || g.szm)                        \
+    X(17, 16, g.rmp + g.x, g.sym || g.szp)                        \
+    X(18, 15, g.rpp + g.x, g.syp || g.szp)
+
+#define GLBE_DIRS7(X)                      \
+    X(1, 2, g.r00 + g.xm, g.sxm)           \
+    X(2, 1, g.r00 + g.xp, g.sxp)           \
+    X(3, 4, g.rm0 + g.x, g.sym)            \
+    X(4, 3, g.rp0 + g.x, g.syp)            \
+    X(5, 6, g.r0m + g.x, g.szm)            \
+    X(6, 5, g.r0p + g.x, g.szp)
+
+template <int ST>
+__device__ __forceinline__ void load_f(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
+                                       const Geo& g, float (&d)[19])
+{
+    const size_t N = p.N;
+    d[0] = Store<ST>::ld(fs + g.n) * p.inv_scale;
+#define GLBE_LOADF(a, o, src, sol) \
+    d[a] = Store<ST>::ld(fs + ((sol) ? (size_t)(o) * N + g.n : (size_t)(a) * N + (src))) * p.inv_scale;
+    GLBE_DIRS(GLBE_LOADF)
+#undef GLBE_LOADF
+}
+
+// g is [j*7 + a][N]; anti-bounce-back: g_a(x, t+1) = -g~_abar(x, t) + 2 W_a B_wall,
+// i.e. for deviations dg_a = -dg~_abar + 2 W_a (B_wall - B0).
+template <int ST>
+__device__ __forceinline__ void load_g(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
+                                       const Geo& g, float (&q)[21])
+{
+    const size_t N = p.N;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const typename Store<ST>::T* __restrict__ b = gs + (size_t)(j * 7) * N;
+        const float wall = 0.25f * p.bwall_dev[j];   // 2 W_a (B_wall - B0), W_a = 1/8
+        q[j * 7 + 0] = Store<ST>::ld(b + g.n) * p.inv_scale;
+#define GLBE_LOADG(a, o, src, sol)                                                      \
+    q[j * 7 + a] = (sol) ? (wall - Store<ST>::ld(b + (size_t)(o) * N + g.n) * p.inv_scale) \
+                         : Store<ST>::ld(b + (size_t)(a) * N + (src)) * p.inv_scale;
+        GLBE_DIRS7(GLBE_LOADG)
+#undef GLBE_LOADG
+    }
+}
+
+// Everything a node's collision produces besides the new populations.
+struct NodeMacro {
+    float rho, ux, uy, uz;
+    float Bx, By, Bz;
+    float FLx, FLy, FLz;
+};
+
+// Induction part: B, Lorentz force from the previous step's half-force
+// velocity, D3Q7 collision in place.  Returns the new Lorentz force.
+__device__ __forceinline__ void induction_collide(const StepParams& p, float (&q)[21], float rho_inv, float mx,
+                                                  float my, float mz, float Fx, float Fy, float Fz, float FLpx,
+                                                  float FLpy, float FLpz, NodeMacro& mac)
+{
+    // B_j = B0_j + sum_a dg_ja (sum_a W_a = 1), Eq. magneticinduction
+    const float bx = q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6];
+    const float by = q[7] + q[8] + q[9] + q[10] + q[11] + q[12] + q[13];
+    const float bz = q[14] + q[15] + q[16] + q[17] + q[18] + q[19] + q[20];
+    const float Bx = p.B0[0] + bx, By = p.B0[1] + by, Bz = p.B0[2] + bz;
+    // velocity with the previous step's Lorentz force in the half-force
+    const float hg = 0.5f * p.inv_gamma;
+    const float u0x = (mx + hg * (Fx + FLpx)) * rho_inv;
+    const float u0y = (my + hg * (Fy + FLpy)) * rho_inv;
+    const float u0z = (mz + hg * (Fz + FLpz)) * rho_inv;
+    // equilibrium first moment Lambda^eq_kj = (chi/gamma_m)(u_k B_j - B_k u_j)
+    const float c = p.conv_coef;
+    const float Lxy = c * (u0x * By - Bx * u0y);
+    const float Lxz = c * (u0x * Bz - Bx * u0z);
+    const float Lyz = c * (u0y * Bz - By * u0z);
+    // first moments of g: M_kj = g_{+k,j} - g_{-k,j}; non-equilibrium parts
+    const float Nxy = (q[7 + 1] - q[7 + 2]) - Lxy;     // k = x, j = y
+    const float Nyx = (q[0 + 3] - q[0 + 4]) + Lxy;     // k = y, j = x (Lambda^eq_yx = -Lxy)
+    const float Nxz = (q[14 + 1] - q[14 + 2]) - Lxz;
+    const float Nzx = (q[0 + 5] - q[0 + 6]) + Lxz;
+    const float Nyz = (q[14 + 3] - q[14 + 4]) - Lyz;
+    const float Nzy = (q[7 + 5] - q[7 + 6]) + Lyz;
+    // J_i = -(1/(mu chi tau_m theta_m)) eps_ijk Lneq_jk = (1/(mu chi)) (curl B)_i
+    const float Jx = p.J_coef * (Nyz - Nzy);
+    const float Jy = p.J_coef * (Nzx - Nxz);
+    const float Jz = p.J_coef * (Nxy - Nyx);
+    mac.FLx = Jy * Bz - Jz * By;
+    mac.FLy = Jz * Bx - Jx * Bz;
+    mac.FLz = Jx * By - Jy * Bx;
+    mac.Bx = Bx; mac.By = By; mac.Bz = Bz;
+    // g^eq,* deviations: W_0 b_j (rest), W_1 (b_j +- Lambda^eq_kj / theta_m), 1/theta_m = 4
+    const float w = p.omega_m;
+    const float ex0 = 0.25f * bx, ey0 = 0.25f * by, ez0 = 0.25f * bz;
+    const float ex = 0.125f * bx, ey = 0.125f * by, ez = 0.125f * bz;
+    const float Axy = 0.5f * Lxy, Axz = 0.5f * Lxz, Ayz = 0.5f * Lyz;   // W_1 * 4 * L
+    float geq[21] = {
+        ex0, ex, ex, ex - Axy, ex + Axy, ex - Axz, ex + Axz,       // j = x
+        ey0, ey + Axy, ey - Axy, ey, ey, ey - Ayz, ey + Ayz,       // j = y
+        ez0, ez + Axz, ez - Axz, ez + Ayz, ez - Ayz, ez, ez};      // j = z
+#pragma unroll
+    for (int i = 0; i < 21; ++i) q[i] = fmaf(w, geq[i] - q[i], q[i]);
+}
+
+// D3Q19 moment-space collision in place on deviations d (Eq. prelax_term).
+// F is the total force, (jx, jy, jz) = m + F/(2 gamma).
+__device__ __forceinline__ void flow_collide(const StepParams& p, float (&d)[19], float drho, float rho_inv,
+                                             float jx, float jy, float jz, float Fx, float Fy, float Fz)
+{
+    const float ig = p.inv_gamma, ig2 = p.inv_gamma2;
+    const float gri = ig * rho_inv;                   // 1/(gamma rho)
+    const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
+    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
+
+    // group sums
+    const float Ax = d[1] + d[2], Ay = d[3] + d[4], Az = d[5] + d[6];
+    const float Sax = Ax + Ay + Az;
+    const float Gxy = d[7] + d[8] + d[9] + d[10];
+    const float Gxz = d[11] + d[12] + d[13] + d[14];
+    const float Gyz = d[15] + d[16] + d[17] + d[18];
+    const float Sdg = Gxy + Gxz + Gyz;
+    const float Xax = d[1] - d[2], Xxy = d[7] - d[8] + d[9] - d[10], Xxz = d[11] - d[12] + d[13] - d[14];
+    const float Yax = d[3] - d[4], Yxy = d[7] + d[8] - d[9] - d[10], Yyz = d[15] - d[16] + d[17] - d[18];
+    const float Zax = d[5] - d[6], Zxz = d[11] + d[12] - d[13] - d[14], Zyz = d[15] + d[16] - d[17] - d[18];
+
+    // moments of the deviations and their non-equilibrium parts n_k = f^_k - f^eq,*_k
+    // (the rest state contributes -11 rho0 to row 1 and 3 rho0 to row 2 only)
+    const float n1 = (-30.f * d[0] - 11.f * Sax + 8.f * Sdg) + 11.f * drho - 19.f * jj * gri;
+    const float n2 = (12.f * d[0] - 4.f * Sax + Sdg) - 3.f * drho + 5.5f * jj * gri;
+    const float n4 = (-4.f * Xax + Xxy + Xxz) + (2.f / 3.f) * jx;
+    const float n6 = (-4.f * Yax + Yxy + Yyz) + (2.f / 3.f) * jy;
+    const float n8 = (-4.f * Zax + Zxz + Zyz) + (2.f / 3.f) * jz;
+    const float e9 = (3.f * jxx - jj) * gri;
+    const float e11 = (jyy - jzz) * gri;
+    const float n9 = (2.f * Ax - Ay - Az + Gxy + Gxz - 2.f * Gyz) - e9;
+    const float n10 = (-4.f * Ax + 2.f * Ay + 2.f * Az + Gxy + Gxz - 2.f * Gyz) + 0.5f * e9;
+    const float n11 = (Ay - Az + Gxy - Gxz) - e11;
+    const float n12 = (-2.f * Ay + 2.f * Az + Gxy - Gxz) + 0.5f * e11;
+    const float n13 = (d[7] - d[8] - d[9] + d[10]) - jx * jy * gri;
+    const float n14 = (d[15] - d[16] - d[17] + d[18]) - jy * jz * gri;
+    const float n15 = (d[11] - d[12] - d[13] + d[14]) - jx * jz * gri;
+    const float n16 = Xxy - Xxz;
+    const float n17 = Yyz - Yxy;
+    const float n18 = Zxz - Zyz;
+
+    // preconditioned source moments S* = P_S S (App. A, Eq. precondsourceterm)
+    const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
+    const float S1 = 38.f * Fu * ig2, S2 = -11.f * Fu * ig2;
+    const float S4 = (-2.f / 3.f) * Fx * ig, S6 = (-2.f / 3.f) * Fy * ig, S8 = (-2.f / 3.f) * Fz * ig;
+    const float S9 = 2.f * (2.f * Fux - Fuy - Fuz) * ig2, S10 = -0.5f * S9;
+    const float S11 = 2.f * (Fuy - Fuz) * ig2, S12 = -0.5f * S11;
+    const float S13 = (Fx * uy + Fy * ux) * ig2;
+    const float S14 = (Fy * uz + Fz * uy) * ig2;
+    const float S15 = (Fx * uz + Fz * ux) * ig2;
+
+    // delta_k = [-s_k n_k + (1 - s_k/2) S*_k] / |row_k|^2; conserved rows:
+    // delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
+#define GLBE_DK(k, nk, Sk, inv) (((-p.s[k]) * (nk) + (1.f - 0.5f * p.s[k]) * (Sk)) * (inv))
+    const float q1 = GLBE_DK(1, n1, S1, 1.f / 2394.f);
+    const float q2 = GLBE_DK(2, n2, S2, 1.f / 252.f);
+    const float q3 = Fx * ig * 0.1f, q5 = Fy * ig * 0.1f, q7 = Fz * ig * 0.1f;
+    const float q4 = GLBE_DK(4, n4, S4, 1.f / 40.f);
+    const float q6 = GLBE_DK(6, n6, S6, 1.f / 40.f);
+    const float q8 = GLBE_DK(8, n8, S8, 1.f / 40.f);
+    const float q9 = GLBE_DK(9, n9, S9, 1.f / 36.f);
+    const float q10 = GLBE_DK(10, n10, S10, 1.f / 72.f);
+    const float q11 = GLBE_DK(11, n11, S11, 1.f / 12.f);
+    const float q12 = GLBE_DK(12, n12, S12, 1.f / 24.f);
+    const float q13 = GLBE_DK(13, n13, S13, 0.25f);
+    const float q14 = GLBE_DK(14, n14, S14, 0.25f);
+    const float q15 = GLBE_DK(15, n15, S15, 0.25f);
+    const float q16 = -p.s[16] * n16 * 0.125f;
+    const float q17 = -p.s[17] * n17 * 0.125f;
+    const float q18 = -p.s[18] * n18 * 0.125f;
+#undef GLBE_DK
+
+    // f~ = f + T^t delta  (columns of T read from the basis polynomials)
+    d[0] += -30.f * q1 + 12.f * q2;
+    const float A = -11.f * q1 - 4.f * q2;          // axis directions, c^2 = 1
+    const float X9 = 2.f * q9 - 4.f * q10;           // 3c_x^2 - c^2 = 2 on +-x
+    const float Y9 = -q9 + 2.f * q10;                // ... = -1 on +-y, +-z
+    const float W11 = q11 - 2.f * q12;
+    float t = q3 - 4.f * q4;
+    d[1] += A + X9 + t;
+    d[2] += A + X9 - t;
+    t = q5 - 4.f * q6;
+    d[3] += A + Y9 + W11 + t;
+    d[4] += A + Y9 + W11 - t;
+    t = q7 - 4.f * q8;
+    d[5] += A + Y9 - W11 + t;
+    d[6] += A + Y9 - W11 - t;
+    const float Dg = 8.f * q1 + q2;                  // diagonal directions, c^2 = 2
+    const float P = q9 + q10, Q = q11 + q12;
+    {   // (+-1, +-1, 0)
+        const float b = Dg + P + Q, ax = q3 + q4 + q16, by = q5 + q6 - q17;
+        d[7] += b + ax + by + q13;
+        d[8] += b - ax + by - q13;
+        d[9] += b + ax - by - q13;
+        d[10] += b - ax - by + q13;
+    }
+    {   // (+-1, 0, +-1)
+        const float b = Dg + P - Q, ax = q3 + q4 - q16, bz = q7 + q8 + q18;
+        d[11] += b + ax + bz + q15;
+        d[12] += b - ax + bz - q15;
+        d[13] += b + ax - bz - q15;
+        d[14] += b - ax - bz + q15;
+    }
+    {   // (0, +-1, +-1)
+        const float b = Dg - 2.f * P, ay = q5 + q6 + q17, bz = q7 + q8 - q18;
+        d[15] += b + ay + bz + q14;
+        d[16] += b - ay + bz - q14;
+        d[17] += b + ay - bz - q14;
+        d[18] += b - ay - bz + q14;
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    using T = typename Store<ST>::T;
+    if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    const bool inb = i < p.N;
+    const uint32_t n = inb ? i : 0u;
+    const Geo g = make_geo(p, n);
+    const bool fluid = inb && !g.solid;
+    const size_t N = p.N;
+
+    if (MODE == MODE_STEP && !fluid) return;
+    if (MODE == MODE_FIELDS && !inb) return;
+
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (fluid) {
+        float d[19];
+        load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d);
+        float q[21];
+        float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
+        if (MHD) {
+            load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q);
+            FLpx = b.FL[n];
+            FLpy = b.FL[N + n];
+            FLpz = b.FL[2 * N + n];
+        }
+        // density and bare first moment (Eq. precondhydrofields)
+        float drho = 0.f;
+#pragma unroll
+        for (int a = 0; a < 19; ++a) drho += d[a];
+        const float rho = p.rho0 + drho;
+        const float rho_inv = 1.0f / rho;
+        const float mx = (d[1] - d[2]) + (d[7] - d[8] + d[9] - d[10]) + (d[11] - d[12] + d[13] - d[14]);
+        const float my = (d[3] - d[4]) + (d[7] + d[8] - d[9] - d[10]) + (d[15] - d[16] + d[17] - d[18]);
+        const float mz = (d[5] - d[6]) + (d[11] + d[12] - d[13] - d[14]) + (d[15] + d[16] - d[17] - d[18]);
+        // external force
+        float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
+        if (p.force_ncomp >= 1) Fx += __ldg(b.Ffield + n);
+        if (p.force_ncomp == 3) {
+            Fy += __ldg(b.Ffield + N + n);
+            Fz += __ldg(b.Ffield + 2 * N + n);
+        }
+        NodeMacro mac;
+        mac.Bx = mac.By = mac.Bz = 0.f;
+        mac.FLx = mac.FLy = mac.FLz = 0.f;
+        if (MHD) {
+            induction_collide(p, q, rho_inv, mx, my, mz, Fx, Fy, Fz, FLpx, FLpy, FLpz, mac);
+            Fx += mac.FLx;
+            Fy += mac.FLy;
+            Fz += mac.FLz;
+        }
+        const float hg = 0.5f * p.inv_gamma;
+        const float jx = mx + hg * Fx, jy = my + hg * Fy, jz = mz + hg * Fz;
+        const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
+
+        if (MODE == MODE_FIELDS) {
+            if (fo.rho) fo.rho[n] = rho;
+            if (fo.u) { fo.u[n] = ux; fo.u[N + n] = uy; fo.u[2 * N + n] = uz; }
+            if (MHD && fo.B) { fo.B[n] = mac.Bx; fo.B[N + n] = mac.By; fo.B[2 * N + n] = mac.Bz; }
+            return;
+        }
+
+        flow_collide(p, d, drho, rho_inv, jx, jy, jz, Fx, Fy, Fz);
+        T* __restrict__ fd = static_cast<T*>(b.fdst);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = Store<ST>::cv(d[a] * p.scale);
+        if (MHD) {
+            T* __restrict__ gd = static_cast<T*>(b.gdst);
+#pragma unroll
+            for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = Store<ST>::cv(q[a] * p.scale);
+            b.FL[n] = mac.FLx;
+            b.FL[N + n] = mac.FLy;
+            b.FL[2 * N + n] = mac.FLz;
+        }
+        if (MODE == MODE_STEP_RESID) {
+            if (b.have_snap) {
+                const float dx = ux - b.usnap[n], dy = uy - b.usnap[N + n], dz = uz - b.usnap[2 * N + n];
+                acc[0] = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+            }
+            acc[1] = (double)ux * ux + (double)uy * uy + (double)uz * uz;
+            acc[2] = (double)rho;
+            acc[3] = (double)jx;
+            acc[4] = (double)jy;
+            acc[5] = (double)jz;
+            acc[6] = isfinite(ux + uy + uz) ? 0.0 : 1.0;
+            b.usnap[n] = ux;
+            b.usnap[N + n] = uy;
+            b.usnap[2 * N + n] = uz;
+        }
+    } else if (MODE == MODE_FIELDS) {
+        if (fo.rho) fo.rho[n] = 0.f;
+        if (fo.u) { fo.u[n] = 0.f; fo.u[N + n] = 0.f; fo.u[2 * N + n] = 0.f; }
+        if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
+        return;
+    }
+
+    if (MODE == MODE_STEP_RESID) {
+        __shared__ double sh[STEP_THREADS / 32][7];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const double v = warp_sum(acc[k]);
+            if (lane == 0) sh[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < STEP_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+            b.partials[(size_t)blockIdx.x * PARTIAL_STRIDE + threadIdx.x] = s;
+        }
+    }
+}
+
+// Pre-collision state (deviations, FP32, C-ABI layout) of every fluid node.
+template <int ST, bool MHD>
+__global__ void __launch_bounds__(STEP_THREADS) get_state_kernel(const StepParams p, const void* fsrc,
+                                                                 const void* gsrc, const float* FL, float* df,
+                                                                 float* dg, float* dFL)
+{
+    using T = typename Store<ST>::T;
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    if (i >= p.N) return;
+    const Geo g = make_geo(p, i);
+    const size_t N = p.N;
+    if (g.solid) {
+        if (df) for (int a = 0; a < 19; ++a) df[(size_t)a * N + i] = 0.f;
+        if (MHD && dg) for (int a = 0; a < 21; ++a) dg[(size_t)a * N + i] = 0.f;
+        if (MHD && dFL) for (int k = 0; k < 3; ++k) dFL[(size_t)k * N + i] = 0.f;
+        return;
+    }
+    if (df) {
+        float d[19];
+        load_f<ST>(p, static_cast<const T*>(fsrc), g, d);
+        for (int a = 0; a < 19; ++a) df[(size_t)a * N + i] = d[a];
+    }
+    if (MHD && dg) {
+        float q[21];
+        load_g<ST>(p, static_cast<const T*>(gsrc), g, q);
+        for (int a = 0; a < 21; ++a) dg[(size_t)a * N + i] = q[a];
+    }
+    if (MHD && dFL)
+        for (int k = 0; k < 3; ++k) dFL[(size_t)k * N + i] = FL[(size_t)k * N + i];
+}
+
+// Inverse of get_state: each pre-collision value is written into the slot the
+// next pull reads it from (the upstream node's slot, or the own node's
+// opposite slot across a wall).  Every slot of a fluid node is written once.
+template <int ST, bool MHD>
+__global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParams p, void* fsrc, void* gsrc,
+                                                                 float* FL, const float* df, const float* dg,
+                                                                 const float* dFL)
+{
+    using T = typename Store<ST>::T;
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    if (i >= p.N) return;
+    const Geo g = make_geo(p, i);
+    if (g.solid) return;
+    const size_t N = p.N;
+    if (df) {
+        T* fs = static_cast<T*>(fsrc);
+        fs[i] = Store<ST>::cv(df[i] * p.scale);
+#define GLBE_STOREF(a, o, src, sol) \
+    fs[(sol) ? (size_t)(o) * N + i : (size_t)(a) * N + (src)] = Store<ST>::cv(df[(size_t)(a) * N + i] * p.scale);
+        GLBE_DIRS(GLBE_STOREF)
+#undef GLBE_STOREF
+    }
+    if (MHD && dg) {
+        T* gs = static_cast<T*>(gsrc);
+        for (int j = 0; j < 3; ++j) {
+            T* bj = gs + (size_t)(j * 7) * N;
+            const float* vj = dg + (size_t)(j * 7) * N;
+            const float wall = 0.25f * p.bwall_dev[j];
+            bj[i] = Store<ST>::cv(vj[i] * p.scale);
+#define GLBE_STOREG(a, o, src, sol)                                                     \
+    if (sol) bj[(size_t)(o) * N + i] = Store<ST>::cv((wall - vj[(size_t)(a) * N + i]) * p.scale); \
+    else bj[(size_t)(a) * N + (src)] = Store<ST>::cv(vj[(size_t)(a) * N + i] * p.scale);
+            GLBE_DIRS7(GLBE_STOREG)
+#undef GLBE_STOREG
+        }
+    }
+    if (MHD && dFL)
+        for (int k = 0; k < 3; ++k) FL[(size_t)k * N + i] = dFL[(size_t)k * N + i];
+}
+
+template <int ST>
+cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                          unsigned grid, cudaStream_t st)
+{
+    const dim3 blk(STEP_THREADS);
+    if (mhd) {
+        if (mode == MODE_STEP) step_kernel<ST, true, MODE_STEP><<<grid, blk, 0, st>>>(p, b, fo);
+        else if (mode == MODE_STEP_RESID) step_kernel<ST, true, MODE_STEP_RESID><<<grid, blk, 0, st>>>(p, b, fo);
+        else step_kernel<ST, true, MODE_FIELDS><<<grid, blk, 0, st>>>(p, b, fo);
+    } else {
+        if (mode == MODE_STEP) step_kernel<ST, false, MODE_STEP><<<grid, blk, 0, st>>>(p, b, fo);
+        else if (mode == MODE_STEP_RESID) step_kernel<ST, false, MODE_STEP_RESID><<<grid, blk, 0, st>>>(p, b, fo);
+        else step_kernel<ST, false, MODE_FIELDS><<<grid, blk, 0, st>>>(p, b, fo);
+    }
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_get_state_t(bool mhd, const StepParams& p, const void* fsrc, const void* gsrc, const float* FL,
+                               float* df, float* dg, float* dFL, cudaStream_t st)
+{
+    const unsigned grid = (p.N + STEP_THREADS - 1) / STEP_THREADS;
+    if (mhd) get_state_kernel<ST, true><<<grid, STEP_THREADS, 0, st>>>(p, fsrc, gsrc, FL, df, dg, dFL);
+    else get_state_kernel<ST, false><<<grid, STEP_THREADS, 0, st>>>(p, fsrc, gsrc, FL, df, dg, dFL);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_set_state_t(bool mhd, const StepParams& p, void* fsrc, void* gsrc, float* FL, const float* df,
+                               const float* dg, const float* dFL, cudaStream_t st)
+{
+    const unsigned grid = (p.N + STEP_THREADS - 1) / STEP_THREADS;
+    if (mhd) set_state_kernel<ST, true><<<grid, STEP_THREADS, 0, st>>>(p, fsrc, gsrc, FL, df, dg, dFL);
+    else set_state_kernel<ST, false><<<grid, STEP_THREADS, 0, st>>>(p, fsrc, gsrc, FL, df, dg, dFL);
+    return cudaGetLastError();
+}
+
+}  // namespace glbe

@@ -1,0 +1,285 @@
+"""Python binding of the C-ABI in include/glbe.h (argument marshalling only).
+
+Every step of the time march runs in the CUDA library ``libglbe.so``; this
+module loads it with ctypes, mirrors its structs and exposes the entry points
+under the same names.  PyTorch provides device memory (the caller-owned
+workspace and field buffers) and the CUDA stream.
+
+There is no fallback: if the library is missing or cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+GLBE_OK, GLBE_ERR_ARG, GLBE_ERR_CUDA, GLBE_ERR_DIVERGED, GLBE_ERR_TIMEOUT, GLBE_ERR_STATE = range(6)
+GLBE_F32, GLBE_BF16, GLBE_F16 = 0, 1, 2
+STORAGE = {"f32": GLBE_F32, "bf16": GLBE_BF16, "f16": GLBE_F16}
+
+
+class GlbeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+class glbe_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("wall_lo", C.c_int * 3), ("wall_hi", C.c_int * 3),
+        ("rho0", C.c_double), ("gamma", C.c_double), ("nu", C.c_double),
+        ("s", C.c_double * 19), ("F", C.c_double * 3),
+        ("force_field", C.c_int), ("induction", C.c_int),
+        ("gamma_m", C.c_double), ("eta", C.c_double), ("chi", C.c_double), ("mu", C.c_double),
+        ("B0", C.c_double * 3),
+        ("storage", C.c_int), ("storage_scale", C.c_double),
+        ("stream", C.c_void_p),
+    ]
+
+
+class glbe_residual_info(C.Structure):
+    _fields_ = [
+        ("t", C.c_long), ("r", C.c_double), ("num", C.c_double), ("den", C.c_double),
+        ("mass", C.c_double), ("momentum", C.c_double * 3), ("nonfinite", C.c_int),
+    ]
+
+
+# Every symbol include/glbe.h declares, with (restype, argtypes).
+_P = C.POINTER
+_SIGNATURES = {
+    "glbe_params_default": (None, [_P(glbe_params)]),
+    "glbe_workspace_bytes": (C.c_int, [_P(glbe_params), _P(C.c_size_t)]),
+    "glbe_init": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_size_t, _P(C.c_void_p)]),
+    "glbe_set_force": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "glbe_set_force_host": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "glbe_step_n": (C.c_int, [C.c_void_p, C.c_long]),
+    "glbe_residual": (C.c_int, [C.c_void_p, _P(glbe_residual_info)]),
+    "glbe_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_long, _P(C.c_long), _P(C.c_double)]),
+    "glbe_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "glbe_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "glbe_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_long]),
+    "glbe_time": (C.c_int, [C.c_void_p, _P(C.c_long)]),
+    "glbe_sync": (C.c_int, [C.c_void_p]),
+    "glbe_last_error": (C.c_char_p, []),
+    "glbe_destroy": (None, [C.c_void_p]),
+    "glbe_abi_version": (C.c_int, []),
+    "glbe_struct_sizes": (None, [_P(C.c_size_t), _P(C.c_size_t)]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libglbe.so (building it with nvcc if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run paper_0809_4730_gb300.build.build()")
+            lib = C.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            if lib.glbe_abi_version() != 1:
+                raise RuntimeError("libglbe ABI version mismatch")
+            ps, isz = C.c_size_t(0), C.c_size_t(0)
+            lib.glbe_struct_sizes(C.byref(ps), C.byref(isz))
+            if ps.value != C.sizeof(glbe_params) or isz.value != C.sizeof(glbe_residual_info):
+                raise RuntimeError("libglbe struct layout does not match the Python mirror")
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != GLBE_OK:
+        msg = load().glbe_last_error().decode(errors="replace")
+        raise GlbeError(status, where, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C entry points
+# ---------------------------------------------------------------------------
+def glbe_params_default() -> glbe_params:
+    p = glbe_params()
+    load().glbe_params_default(C.byref(p))
+    return p
+
+
+def glbe_workspace_bytes(p: glbe_params) -> int:
+    n = C.c_size_t(0)
+    _check(load().glbe_workspace_bytes(C.byref(p), C.byref(n)), "glbe_workspace_bytes")
+    return n.value
+
+
+def glbe_init(p: glbe_params, workspace) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(load().glbe_init(C.byref(p), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                            C.byref(ctx)), "glbe_init")
+    return ctx
+
+
+def glbe_set_force(ctx, d_F):
+    _check(load().glbe_set_force(ctx, _ptr(d_F)), "glbe_set_force")
+
+
+def glbe_set_force_host(ctx, h_F):
+    _check(load().glbe_set_force_host(ctx, _ptr(h_F)), "glbe_set_force_host")
+
+
+def glbe_step_n(ctx, n: int):
+    _check(load().glbe_step_n(ctx, int(n)), "glbe_step_n")
+
+
+def glbe_residual(ctx) -> glbe_residual_info:
+    info = glbe_residual_info()
+    _check(load().glbe_residual(ctx, C.byref(info)), "glbe_residual")
+    return info
+
+
+def glbe_solve(ctx, tol: float, max_steps: int):
+    steps = C.c_long(0)
+    r = C.c_double(0.0)
+    st = load().glbe_solve(ctx, float(tol), int(max_steps), C.byref(steps), C.byref(r))
+    if st not in (GLBE_OK, GLBE_ERR_TIMEOUT):
+        _check(st, "glbe_solve")
+    return st, steps.value, r.value
+
+
+def glbe_fields(ctx, d_rho, d_u, d_B):
+    _check(load().glbe_fields(ctx, _ptr(d_rho), _ptr(d_u), _ptr(d_B)), "glbe_fields")
+
+
+def glbe_get_state(ctx, d_df, d_dg, d_FL):
+    _check(load().glbe_get_state(ctx, _ptr(d_df), _ptr(d_dg), _ptr(d_FL)), "glbe_get_state")
+
+
+def glbe_set_state(ctx, d_df, d_dg, d_FL, t: int):
+    _check(load().glbe_set_state(ctx, _ptr(d_df), _ptr(d_dg), _ptr(d_FL), int(t)), "glbe_set_state")
+
+
+def glbe_time(ctx) -> int:
+    t = C.c_long(0)
+    _check(load().glbe_time(ctx, C.byref(t)), "glbe_time")
+    return t.value
+
+
+def glbe_sync(ctx):
+    _check(load().glbe_sync(ctx), "glbe_sync")
+
+
+def glbe_destroy(ctx):
+    if ctx:
+        load().glbe_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of one context and its torch-allocated workspace
+# ---------------------------------------------------------------------------
+class Solver:
+    """One lattice context on a CUDA device.
+
+    Keyword arguments map one to one onto the fields of ``glbe_params``;
+    ``storage`` accepts "f32", "bf16" or "f16"; ``s`` overrides the 19 rates.
+    """
+
+    def __init__(self, nx, ny, nz, *, device="cuda", stream=None, **kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        p = glbe_params_default()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        for key, val in kw.items():
+            if key in ("wall_lo", "wall_hi", "F", "B0"):
+                arr = getattr(p, key)
+                for d in range(3):
+                    arr[d] = type(arr[d])(val[d])
+            elif key == "s":
+                for k in range(19):
+                    p.s[k] = float(val[k])
+            elif key == "storage":
+                p.storage = STORAGE[val] if isinstance(val, str) else int(val)
+            elif key in ("induction", "force_field"):
+                setattr(p, key, int(val))
+            else:
+                setattr(p, key, float(val))
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p.stream = C.c_void_p(self.stream.cuda_stream)
+        self.params = p
+        self.N = p.nx * p.ny * p.nz
+        nbytes = glbe_workspace_bytes(p)
+        # 256-byte aligned workspace (the caching allocator aligns to 512 bytes)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = glbe_init(p, self.workspace)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            glbe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def induction(self) -> bool:
+        return bool(self.params.induction)
+
+    def set_force(self, F):
+        glbe_set_force(self.ctx, F.contiguous())
+
+    def step(self, n: int):
+        glbe_step_n(self.ctx, n)
+
+    def residual(self) -> glbe_residual_info:
+        return glbe_residual(self.ctx)
+
+    def solve(self, tol: float, max_steps: int):
+        return glbe_solve(self.ctx, tol, max_steps)
+
+    @property
+    def t(self) -> int:
+        return glbe_time(self.ctx)
+
+    def fields(self):
+        torch = self.torch
+        rho = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        u = torch.empty(3, self.N, dtype=torch.float32, device=self.device)
+        B = torch.empty(3, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        glbe_fields(self.ctx, rho, u, B)
+        return rho, u, B
+
+    def get_state(self):
+        torch = self.torch
+        df = torch.empty(19, self.N, dtype=torch.float32, device=self.device)
+        dg = torch.empty(21, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        FL = torch.empty(3, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        glbe_get_state(self.ctx, df, dg, FL)
+        return df, dg, FL
+
+    def set_state(self, df, dg=None, FL=None, t: int = 0):
+        glbe_set_state(self.ctx, df.contiguous(), None if dg is None else dg.contiguous(),
+                       None if FL is None else FL.contiguous(), t)
+
+    def sync(self):
+        glbe_sync(self.ctx)

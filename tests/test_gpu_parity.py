@@ -1,0 +1,258 @@
+"""Parity of the CUDA library (through its C-ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic and storage, unit round-off u = 2^-24 = 6e-8):
+one step applies about 30 floating-point operations to every population, so a
+step adds at most ~30 u relative to the largest deviation D; over n steps the
+error stays below n * 30 u * D.  For the 23-step cases that is 4e-5 D; the
+tests use 3e-5 D, the tail of a random walk being far below the worst case.
+BF16 storage rounds every population once per step to 8 bits (u = 2^-9 =
+2e-3 relative); FP16 with the default scale 4096 to 11 bits (u = 2.4e-4).
+At steady state the bar is the spec one: velocity L-infinity relative
+error <= 1e-5 against the converged FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import (W19, W7, gpu_fields, gpu_state, make_pair, oracle_state_dev, push_oracle_state,
+                        rel_linf, require_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(orc, mhd, gamma=0.3, **kw):
+    base = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 0), gamma=gamma, nu=0.02, F=(2e-5, -1e-5, 5e-6))
+    if mhd:
+        base.update(induction=True, gamma_m=gamma, eta=0.03, chi=0.4, mu=1.3, B0=(0.01, 0.03, -0.02))
+    base.update(kw)
+    return orc.Config(37, 11, 9, **base)
+
+
+def _perturb(S, seed, scale=2e-3):
+    from paper_0809_4730_gb300.inputs import perturbation
+    cfg = S.cfg
+    p = perturbation(19, cfg.nx, cfg.ny, cfg.nz, scale, seed).reshape(19, -1).T
+    S.f += p * W19[None, :]
+    if cfg.induction:
+        q = perturbation(21, cfg.nx, cfg.ny, cfg.nz, scale * 0.05, seed + 1).reshape(21, -1).T
+        S.g += q.reshape(cfg.N, 3, 7) * W7[None, None, :]
+        S.FL[:] = perturbation(3, cfg.nx, cfg.ny, cfg.nz, 1e-6, seed + 2).reshape(3, -1).T
+
+
+@pytest.mark.parametrize("mhd", [False, True])
+def test_state_roundtrip_is_exact(orc, mhd):
+    cfg = _cfg(orc, mhd)
+    S, G = make_pair(orc, cfg)
+    _perturb(S, 5)
+    push_oracle_state(S, G)
+    df, dg, FL = gpu_state(G)
+    odf, odg, oFL = oracle_state_dev(S)
+    fluid = ~S.solid_mask()
+    assert np.array_equal(df[:, fluid], odf[:, fluid].astype(np.float32).astype(np.float64))
+    if mhd:
+        assert np.array_equal(dg[:, fluid], odg[:, fluid].astype(np.float32).astype(np.float64))
+        assert np.array_equal(FL[:, fluid], oFL[:, fluid].astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("mhd", [False, True])
+@pytest.mark.parametrize("gamma", [1.0, 0.3])
+def test_step_parity_f32(orc, mhd, gamma):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, mhd, gamma=gamma)
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=7)
+    S, G = make_pair(orc, cfg, Fext=Fext)
+    _perturb(S, 11)
+    push_oracle_state(S, G)
+    fluid = ~S.solid_mask()
+    nsteps = 23
+    S.run(nsteps)
+    G.step(nsteps)
+    df, dg, FL = gpu_state(G)
+    odf, odg, oFL = oracle_state_dev(S)
+    assert rel_linf(df, odf, fluid) < 3e-5
+    if mhd:
+        assert rel_linf(dg, odg, fluid) < 3e-5
+        assert rel_linf(FL, oFL, fluid) < 3e-5
+    rho, u, B = gpu_fields(G)
+    orho, ou, oB, _ = S.fields()
+    assert rel_linf(rho - cfg.rho0, orho - cfg.rho0, fluid) < 3e-5
+    assert rel_linf(u, ou.T, fluid) < 3e-5
+    if mhd:
+        assert rel_linf(B, oB.T, fluid) < 3e-5
+    # residual of level 20 (evaluated inside the step that collided it)
+    info = G.residual()
+    h = {row["t"]: row for row in S.hist}
+    assert info.t == 20
+    assert abs(info.r - h[20]["r"]) <= 1e-3 * h[20]["r"]
+    assert abs(info.mass - h[20]["mass"]) <= 1e-6 * h[20]["mass"]
+
+
+@pytest.mark.parametrize("storage,tol", [("bf16", 3e-2), ("f16", 4e-3)])
+def test_step_parity_reduced_storage(orc, storage, tol):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, True, gamma=0.5)
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=3)
+    S, G = make_pair(orc, cfg, Fext=Fext, storage=storage)
+    _perturb(S, 13)
+    push_oracle_state(S, G)
+    # the oracle starts from the state as rounded into the reduced storage
+    df0, dg0, FL0 = gpu_state(G)
+    fluid = ~S.solid_mask()
+    odf, odg, _ = oracle_state_dev(S)
+    assert rel_linf(df0, odf, fluid) < (8e-3 if storage == "bf16" else 1e-3)
+    S.f[fluid] = (df0[:, fluid].T + W19[None, :] * cfg.rho0)
+    B0 = np.asarray(cfg.B0)
+    S.g[fluid] = dg0[:, fluid].T.reshape(-1, 3, 7) + W7[None, None, :] * B0[None, :, None]
+    n = 15
+    S.run(n)
+    G.step(n)
+    df, dg, _ = gpu_state(G)
+    odf, odg, _ = oracle_state_dev(S)
+    assert rel_linf(df, odf, fluid) < tol
+    assert rel_linf(dg, odg, fluid) < tol
+    _, u, _ = gpu_fields(G)
+    _, ou, _, _ = S.fields()
+    assert rel_linf(u, ou.T, fluid) < tol
+
+
+def test_nonfinite_state_is_reported_as_divergence(orc):
+    from paper_0809_4730_gb300.glbe import GLBE_ERR_DIVERGED, GlbeError
+    torch = require_cuda()
+    cfg = _cfg(orc, False)
+    S, G = make_pair(orc, cfg)
+    push_oracle_state(S, G)
+    df, _, _ = G.get_state()
+    fluid_idx = int(np.flatnonzero(~S.solid_mask())[5])
+    df[3, fluid_idx] = float("nan")
+    G.set_state(df, t=0)
+    G.step(21)
+    with pytest.raises(GlbeError) as ei:
+        G.residual()
+    assert ei.value.status == GLBE_ERR_DIVERGED
+
+
+# ---------------------------------------------------------------------------
+# Steady state: plane channel 4x32x4 (walls at y = 0, 31), F_x = 1e-6,
+# tau = 0.8 on the stress moments, gamma = 0.1.  The oracle runs the x/z-
+# invariant column 1x32x1 (identical problem) to r <= 1e-10.
+# ---------------------------------------------------------------------------
+def _channel(orc, gamma, nu, ny=32):
+    return orc.Config(1, ny, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0))
+
+
+def test_steady_channel_parity(orc):
+    from paper_0809_4730_gb300.glbe import Solver
+    gamma = 0.1
+    nu = gamma * (0.8 - 0.5) / 3.0
+    S = orc.Solver(_channel(orc, gamma, nu))
+    S.run(2_000_000, tol=1e-10)
+    _, ou, _, _ = S.fields()
+    G = Solver(4, 32, 4, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0))
+    st, steps, r = G.solve(1e-9, 400_000)
+    _, u, _ = gpu_fields(G)
+    ux = u[0].reshape(4, 32, 4)
+    col = ux[:, :, :].transpose(1, 0, 2).reshape(32, -1)           # [y, (z,x)]
+    want = ou[:, 0]
+    err = np.abs(col - want[:, None]).max() / np.abs(want).max()
+    assert err <= 1e-5, f"velocity L-inf relative error {err:.3e} (GPU r = {r:.2e} after {steps} steps)"
+
+
+def test_preconditioning_cuts_steps(orc):
+    """Steps to r <= 1e-8 on the channel: gamma = 0.1 at least 5x fewer than
+    gamma = 1 at the same physical viscosity; GPU and oracle step counts agree."""
+    from paper_0809_4730_gb300.glbe import Solver
+    nu = 0.1 * 0.3 / 3.0
+    counts = {}
+    for gamma in (1.0, 0.1):
+        S = orc.Solver(_channel(orc, gamma, nu))
+        S.run(2_000_000, tol=1e-8)
+        G = Solver(1, 32, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0))
+        st, steps, r = G.solve(1e-8, 2_000_000)
+        assert st == 0 and r <= 1e-8
+        assert abs(steps - S.t) <= max(20, 0.02 * S.t)
+        counts[gamma] = steps
+    assert counts[1.0] >= 5 * counts[0.1]
+
+
+# ---------------------------------------------------------------------------
+# Steady Hartmann duct 64x64x8 (walls at y = 0, 63), B0 along y, Pr_m = 0.01,
+# nu = eta = 0.01, gamma = gamma_m = 0.1; oracle on the 1x64x1 column.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("Ha", [5, 20])
+def test_steady_hartmann_parity(orc, Ha):
+    from paper_0809_4730_gb300.glbe import Solver
+    nu = eta = 0.01
+    chi = 0.01
+    L = 31.0
+    B0 = Ha * np.sqrt(nu * eta) / L
+    gamma = 0.1
+    cfg = orc.Config(1, 64, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
+                     induction=True, gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
+    S = orc.Solver(cfg)
+    S.run(3_000_000, tol=1e-10)
+    _, ou, oB, _ = S.fields()
+    G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
+               gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
+    st, steps, r = G.solve(1e-9, 1_000_000)
+    _, u, B = gpu_fields(G)
+    ux = u[0].reshape(8, 64, 64).transpose(1, 0, 2).reshape(64, -1)
+    bx = B[0].reshape(8, 64, 64).transpose(1, 0, 2).reshape(64, -1)
+    fl = slice(1, 63)
+    eu = np.abs(ux[fl] - ou[fl, 0][:, None]).max() / np.abs(ou[fl, 0]).max()
+    eb = np.abs(bx[fl] - oB[fl, 0][:, None]).max() / np.abs(oB[fl, 0]).max()
+    assert eu <= 1e-5, f"u error {eu:.3e} (GPU r = {r:.2e}, {steps} steps)"
+    assert eb <= 1e-4, f"b error {eb:.3e}"
+
+
+# ---------------------------------------------------------------------------
+# Full size, bench launch configuration: the 256x256x512 square duct with
+# F_x(y, z).  One step from a seeded random state; sampled nodes are checked
+# against the oracle's single-node collision and the streaming map.
+# ---------------------------------------------------------------------------
+E19 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                [1, 1, 0], [-1, 1, 0], [1, -1, 0], [-1, -1, 0], [1, 0, 1], [-1, 0, 1], [1, 0, -1], [-1, 0, -1],
+                [0, 1, 1], [0, -1, 1], [0, 1, -1], [0, -1, -1]])
+OPP19 = np.array([0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15])
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-6), ("bf16", 2e-3)])
+def test_full_size_duct_sampled(orc, storage, tol):
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    torch = require_cuda()
+    nx, ny, nz = 512, 256, 256
+    N = nx * ny * nz
+    gamma, nu = 0.1, 0.5
+    G = Solver(nx, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, force_field=1,
+               storage=storage)
+    F = duct_force_x(nx, ny, nz)[0].reshape(1, -1)
+    G.set_force(torch.tensor(F, dtype=torch.float32, device="cuda"))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    df0 = (torch.rand(19, N, device="cuda", generator=gen) - 0.5) * 2e-3 * torch.tensor(
+        W19, dtype=torch.float32, device="cuda")[:, None]
+    G.set_state(df0, t=1)
+    pre, _, _ = G.get_state()
+    G.step(1)
+    post, _, _ = G.get_state()
+    G.sync()
+    rng = np.random.default_rng(1)
+    xs, ys, zs = rng.integers(0, nx, 64), rng.integers(1, ny - 1, 64), rng.integers(1, nz - 1, 64)
+    # include wall-adjacent and periodic-edge nodes
+    xs[:4], ys[:4], zs[:4] = [0, nx - 1, 5, 9], [1, ny - 2, 1, ny - 2], [1, nz - 2, nz - 2, 1]
+    cfg = orc.Config(nx, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu)
+    idx = torch.tensor((zs * ny + ys) * nx + xs, device="cuda")
+    pre_s = pre[:, idx].double().cpu().numpy()
+    worst = 0.0
+    for k in range(len(xs)):
+        x, y, z = int(xs[k]), int(ys[k]), int(zs[k])
+        n = (z * ny + y) * nx + x
+        f = pre_s[:, k] + W19
+        ft, _, _ = orc.collide_node(cfg, f, Fext=np.array([F[0, n], 0.0, 0.0]))
+        dft = ft - W19
+        for a in range(19):
+            xt, yt, zt = (x + E19[a, 0]) % nx, y + E19[a, 1], z + E19[a, 2]
+            if yt in (0, ny - 1) or zt in (0, nz - 1):
+                got = post[OPP19[a], n]
+            else:
+                got = post[a, (zt * ny + yt) * nx + xt]
+            worst = max(worst, abs(float(got) - dft[a]) / 1e-3)
+    assert worst < tol
