@@ -157,7 +157,8 @@ glbe_status glbe_get_state(glbe_ctx* ctx, float* d_df, float* d_dg, float* d_FL)
 
 /* Replaces the state by the given pre-collision deviations (layout as in
  * glbe_get_state; NULL d_dg / d_FL leave those parts unchanged) at time
- * level t >= 0.  Clears the residual snapshot. */
+ * level t >= 0.  Clears the residual snapshot, the residual record and a
+ * divergence stop left by an earlier non-finite residual. */
 glbe_status glbe_set_state(glbe_ctx* ctx, const float* d_df, const float* d_dg, const float* d_FL, long t);
 
 /* Current time level. */

@@ -592,6 +592,10 @@ glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, co
     default: e = launch_set_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     }
     GLBE_CUDA(e, "set_state kernel");
+    // a replaced state starts a fresh residual history
+    misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, (long long)t + 10, c->stop_dev, 0, c->tol_dev, 0.0, c->record,
+                                            c->hist_count, 1);
+    GLBE_CUDA(cudaGetLastError(), "set_state reset");
     c->t = t;
     c->t_snap = -1;
     return GLBE_OK;
