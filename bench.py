@@ -51,7 +51,14 @@ def parse():
     ap.add_argument("--storage", choices=["bf16", "f16", "f32"], default="bf16")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
+    args = ap.parse_args()
+    for k in ("nx", "ny", "nz"):
+        if getattr(args, k) is not None:
+            DUCT[k] = getattr(args, k)
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -255,7 +262,8 @@ def run_glbe(args, rank, ws):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": "square duct 512x256x256 (x periodic, walls y/z), Fx(y,z) = F0(1+0.5 sin cos), "
+            "workload": f"square duct {DUCT['nx']}x{DUCT['ny']}x{DUCT['nz']} (x periodic, walls y/z), "
+                        "Fx(y,z) = F0(1+0.5 sin cos), "
                         "F0=1e-6, nu=0.5, gamma=0.1, D3Q19 MRT-GLBE, " + args.storage + " deviation storage, "
                         "FP32 collide; 1 bench step = 10 time steps incl. FP64 residual",
             "nodes": DUCT["nx"] * DUCT["ny"] * DUCT["nz"],
@@ -351,7 +359,8 @@ def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
 def time_to_solution():
     """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Ha = 10,
     Pr_m = 0.01, nu = eta = 0.01) at gamma = gamma_m = 0.1 and 1, same GPU,
-    with the error of the converged u against the analytic profile."""
+    compensated FP32 storage (plain FP32 stalls near r = 7e-8), with the
+    error of the converged u against the analytic profile."""
     import torch
     from paper_0809_4730_gb300.glbe import Solver
     res = {}
@@ -360,7 +369,7 @@ def time_to_solution():
     ua = hartmann_analytic(64, Ha)
     for gamma in (0.1, 1.0):
         G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
-                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
+                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0), storage="f32c")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, steps, r = G.solve(1e-8, 3_000_000)

@@ -69,7 +69,12 @@ typedef enum {
 typedef enum {
     GLBE_F32 = 0,   /* deviations stored as FP32                                    */
     GLBE_BF16 = 1,  /* deviations stored as BF16 (round to nearest even), FP32 math */
-    GLBE_F16 = 2    /* deviations stored as FP16, times storage_scale, FP32 math    */
+    GLBE_F16 = 2,   /* deviations stored as FP16, times storage_scale, FP32 math    */
+    GLBE_F32C = 3   /* compensated: FP32 deviation plus an FP16 remainder (2^36
+                       scaled), updated by an exact two-sum; FP32 math; 6 bytes
+                       per population.  Corrections below one FP32 ulp of the
+                       stored deviation accumulate instead of being dropped, which
+                       removes the FP32 stagnation floor of steady solves.    */
 } glbe_storage;
 
 typedef struct {
@@ -90,7 +95,8 @@ typedef struct {
     double mu;                /* magnetic permeability                           */
     double B0[3];             /* applied field: initial state and wall value      */
     int storage;              /* glbe_storage                                    */
-    double storage_scale;     /* multiplier on stored deviations; 0 = default (1 for F32/BF16, 4096 for F16) */
+    double storage_scale;     /* multiplier on stored deviations; 0 = default (1 for F32/BF16, 4096 for F16;
+                                 ignored for F32C) */
     void* stream;             /* cudaStream_t owned by the caller                */
 } glbe_params;
 

@@ -52,7 +52,7 @@ struct Layout {
     size_t f[2], g[2], FL, Ffield, usnap, partials, record, hist, misc, total;
 };
 
-size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : 2; }
+size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : (st == GLBE_F32C ? 6 : 2); }
 
 unsigned step_grid(size_t N) { return (unsigned)((N + STEP_THREADS - 1) / STEP_THREADS); }
 
@@ -108,8 +108,8 @@ glbe_status validate(const glbe_params* p)
         if (!(p->chi > 0.0)) return fail(GLBE_ERR_ARG, "chi must be > 0");
         if (!(p->mu > 0.0)) return fail(GLBE_ERR_ARG, "mu must be > 0");
     }
-    if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16)
-        return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16 or GLBE_F16");
+    if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16 && p->storage != GLBE_F32C)
+        return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16 or GLBE_F32C");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
     return GLBE_OK;
@@ -147,7 +147,8 @@ StepParams make_step_params(const glbe_params* p)
         s.J_coef = (float)(-1.0 / (p->mu * p->chi * tau_m * THETA_M));
     }
     double scale = p->storage_scale;
-    if (scale == 0.0) scale = p->storage == GLBE_F16 ? 4096.0 : 1.0;
+    if (p->storage == GLBE_F32C) scale = 1.0;   // the compensated form stores unscaled values
+    else if (scale == 0.0) scale = p->storage == GLBE_F16 ? 4096.0 : 1.0;
     s.scale = (float)scale;
     s.inv_scale = (float)(1.0 / scale);
     return s;
@@ -242,7 +243,8 @@ cudaError_t launch_step_any(glbe_ctx* c, int mode, const StepBuffers& b, const F
     switch (c->prm.storage) {
     case GLBE_F32: return launch_step_t<ST_F32>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
     case GLBE_BF16: return launch_step_t<ST_BF16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
-    default: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    case GLBE_F16: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    default: return launch_step_t<ST_F32C>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
     }
 }
 
@@ -573,7 +575,8 @@ glbe_status glbe_get_state(glbe_ctx* c, float* d_df, float* d_dg, float* d_FL)
     switch (c->prm.storage) {
     case GLBE_F32: e = launch_get_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_BF16: e = launch_get_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
-    default: e = launch_get_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_F16: e = launch_get_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    default: e = launch_get_state_t<ST_F32C>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     }
     GLBE_CUDA(e, "get_state kernel");
     return GLBE_OK;
@@ -589,7 +592,8 @@ glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, co
     switch (c->prm.storage) {
     case GLBE_F32: e = launch_set_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_BF16: e = launch_set_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
-    default: e = launch_set_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_F16: e = launch_set_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    default: e = launch_set_state_t<ST_F32C>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     }
     GLBE_CUDA(e, "set_state kernel");
     // a replaced state starts a fresh residual history

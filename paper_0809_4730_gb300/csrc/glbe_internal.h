@@ -62,7 +62,7 @@ struct StepBuffers {
     const int* stop;      // null, or a device flag: when set the launch does nothing
 };
 
-enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };
 enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
 
 constexpr int STEP_THREADS = 256;

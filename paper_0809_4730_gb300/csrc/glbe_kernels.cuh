@@ -25,22 +25,54 @@
 
 namespace glbe {
 
+// Storage of the population deviations.  COMP marks the compensated form:
+// an FP32 high part plus an FP16 low part holding the rounding remainder
+// (scaled by 2^36), updated with an exact two-sum so that corrections far
+// below one FP32 ulp of the stored deviation accumulate instead of being
+// dropped.  The low parts follow the high parts in the same buffer.
+constexpr float LO_SCALE = 68719476736.0f;        // 2^36
+constexpr float LO_INV = 1.4551915228366852e-11f; // 2^-36
+
 template <int ST> struct Store;
 template <> struct Store<ST_F32> {
     using T = float;
+    static constexpr bool COMP = false;
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ float cv(float v) { return v; }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
+    static constexpr bool COMP = false;
     static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
 };
 template <> struct Store<ST_F16> {
     using T = __half;
+    static constexpr bool COMP = false;
     static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v); }
 };
+template <> struct Store<ST_F32C> {
+    using T = float;
+    static constexpr bool COMP = true;
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float cv(float v) { return v; }
+    static __device__ __forceinline__ float ld_lo(const __half* p) { return __half2float(__ldg(p)) * LO_INV; }
+    static __device__ __forceinline__ __half cv_lo(float v) { return __float2half_rn(v * LO_SCALE); }
+};
+
+// h + o + l as a new (high, low) pair: exact two-sum of h and o, the
+// remainder plus the old low part renormalised into the new low part.
+__device__ __forceinline__ void comp_add(float h, float l, float o, float& nh, float& nl)
+{
+    const float s = __fadd_rn(h, o);
+    const float bp = __fsub_rn(s, h);
+    const float ap = __fsub_rn(s, bp);
+    float e = __fadd_rn(__fsub_rn(h, ap), __fsub_rn(o, bp));
+    e = __fadd_rn(e, l);
+    nh = __fadd_rn(s, e);
+    nl = __fsub_rn(e, __fsub_rn(nh, s));
+}
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
 {
@@ -129,21 +161,31 @@ __device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
 
 template <int ST>
 __device__ __forceinline__ void load_f(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
-                                       const Geo& g, float (&d)[19])
+                                       const Geo& g, float (&d)[19], float (&l)[19])
 {
     const size_t N = p.N;
+#define GLBE_SRCF(a, o, src, sol) ((sol) ? (size_t)(o) * N + g.n : (size_t)(a) * N + (src))
+#define GLBE_LOADF(a, o, src, sol) d[a] = Store<ST>::ld(fs + GLBE_SRCF(a, o, src, sol)) * p.inv_scale;
     d[0] = Store<ST>::ld(fs + g.n) * p.inv_scale;
-#define GLBE_LOADF(a, o, src, sol) \
-    d[a] = Store<ST>::ld(fs + ((sol) ? (size_t)(o) * N + g.n : (size_t)(a) * N + (src))) * p.inv_scale;
     GLBE_DIRS(GLBE_LOADF)
 #undef GLBE_LOADF
+    if constexpr (Store<ST>::COMP) {
+        const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * N);
+#define GLBE_LOADL(a, o, src, sol) l[a] = Store<ST>::ld_lo(fl + GLBE_SRCF(a, o, src, sol));
+        l[0] = Store<ST>::ld_lo(fl + g.n);
+        GLBE_DIRS(GLBE_LOADL)
+#undef GLBE_LOADL
+    }
+#undef GLBE_SRCF
 }
 
 // g is [j*7 + a][N]; anti-bounce-back: g_a(x, t+1) = -g~_abar(x, t) + 2 W_a B_wall,
-// i.e. for deviations dg_a = -dg~_abar + 2 W_a (B_wall - B0).
+// i.e. for deviations dg_a = -dg~_abar + 2 W_a (B_wall - B0).  In the
+// compensated form the low part is negated with the high part (exact when
+// B_wall = B0, the only case the C-ABI exposes).
 template <int ST>
 __device__ __forceinline__ void load_g(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
-                                       const Geo& g, float (&q)[21])
+                                       const Geo& g, float (&q)[21], float (&ql)[21])
 {
     const size_t N = p.N;
 #pragma unroll
@@ -156,6 +198,15 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
                          : Store<ST>::ld(b + (size_t)(a) * N + (src)) * p.inv_scale;
         GLBE_DIRS7(GLBE_LOADG)
 #undef GLBE_LOADG
+        if constexpr (Store<ST>::COMP) {
+            const __half* __restrict__ bl = reinterpret_cast<const __half*>(gs + 21 * N) + (size_t)(j * 7) * N;
+            ql[j * 7 + 0] = Store<ST>::ld_lo(bl + g.n);
+#define GLBE_LOADGL(a, o, src, sol)                                             \
+    ql[j * 7 + a] = (sol) ? -Store<ST>::ld_lo(bl + (size_t)(o) * N + g.n)       \
+                          : Store<ST>::ld_lo(bl + (size_t)(a) * N + (src));
+            GLBE_DIRS7(GLBE_LOADGL)
+#undef GLBE_LOADGL
+        }
     }
 }
 
@@ -167,8 +218,9 @@ struct NodeMacro {
 };
 
 // Induction part: B, Lorentz force from the previous step's half-force
-// velocity, D3Q7 collision in place.  Returns the new Lorentz force.
-__device__ __forceinline__ void induction_collide(const StepParams& p, float (&q)[21], float rho_inv, float mx,
+// velocity, and the D3Q7 collision change og = (g^eq - g)/tau_m (Eq. mcollision).
+__device__ __forceinline__ void induction_collide(const StepParams& p, const float (&q)[21], float (&og)[21],
+                                                  float rho_inv, float mx,
                                                   float my, float mz, float Fx, float Fy, float Fz, float FLpx,
                                                   float FLpy, float FLpz, NodeMacro& mac)
 {
@@ -212,12 +264,14 @@ __device__ __forceinline__ void induction_collide(const StepParams& p, float (&q
         ey0, ey + Axy, ey - Axy, ey, ey, ey - Ayz, ey + Ayz,       // j = y
         ez0, ez + Axz, ez - Axz, ez + Ayz, ez - Ayz, ez, ez};      // j = z
 #pragma unroll
-    for (int i = 0; i < 21; ++i) q[i] = fmaf(w, geq[i] - q[i], q[i]);
+    for (int i = 0; i < 21; ++i) og[i] = w * (geq[i] - q[i]);
 }
 
-// D3Q19 moment-space collision in place on deviations d (Eq. prelax_term).
+// D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
+// (I - Lambda*/2) S*] of the deviations d (Eqs. ppostcollision, prelax_term).
 // F is the total force, (jx, jy, jz) = m + F/(2 gamma).
-__device__ __forceinline__ void flow_collide(const StepParams& p, float (&d)[19], float drho, float rho_inv,
+__device__ __forceinline__ void flow_collide(const StepParams& p, const float (&d)[19], float (&om)[19], float drho,
+                                             float rho_inv,
                                              float jx, float jy, float jz, float Fx, float Fy, float Fz)
 {
     const float ig = p.inv_gamma, ig2 = p.inv_gamma2;
@@ -287,43 +341,43 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, float (&d)[19]
     const float q18 = -p.s[18] * n18 * 0.125f;
 #undef GLBE_DK
 
-    // f~ = f + T^t delta  (columns of T read from the basis polynomials)
-    d[0] += -30.f * q1 + 12.f * q2;
+    // om = T^t delta  (columns of T read from the basis polynomials); f~ = f + om
+    om[0] = -30.f * q1 + 12.f * q2;
     const float A = -11.f * q1 - 4.f * q2;          // axis directions, c^2 = 1
     const float X9 = 2.f * q9 - 4.f * q10;           // 3c_x^2 - c^2 = 2 on +-x
     const float Y9 = -q9 + 2.f * q10;                // ... = -1 on +-y, +-z
     const float W11 = q11 - 2.f * q12;
     float t = q3 - 4.f * q4;
-    d[1] += A + X9 + t;
-    d[2] += A + X9 - t;
+    om[1] = A + X9 + t;
+    om[2] = A + X9 - t;
     t = q5 - 4.f * q6;
-    d[3] += A + Y9 + W11 + t;
-    d[4] += A + Y9 + W11 - t;
+    om[3] = A + Y9 + W11 + t;
+    om[4] = A + Y9 + W11 - t;
     t = q7 - 4.f * q8;
-    d[5] += A + Y9 - W11 + t;
-    d[6] += A + Y9 - W11 - t;
+    om[5] = A + Y9 - W11 + t;
+    om[6] = A + Y9 - W11 - t;
     const float Dg = 8.f * q1 + q2;                  // diagonal directions, c^2 = 2
     const float P = q9 + q10, Q = q11 + q12;
     {   // (+-1, +-1, 0)
         const float b = Dg + P + Q, ax = q3 + q4 + q16, by = q5 + q6 - q17;
-        d[7] += b + ax + by + q13;
-        d[8] += b - ax + by - q13;
-        d[9] += b + ax - by - q13;
-        d[10] += b - ax - by + q13;
+        om[7] = b + ax + by + q13;
+        om[8] = b - ax + by - q13;
+        om[9] = b + ax - by - q13;
+        om[10] = b - ax - by + q13;
     }
     {   // (+-1, 0, +-1)
         const float b = Dg + P - Q, ax = q3 + q4 - q16, bz = q7 + q8 + q18;
-        d[11] += b + ax + bz + q15;
-        d[12] += b - ax + bz - q15;
-        d[13] += b + ax - bz - q15;
-        d[14] += b - ax - bz + q15;
+        om[11] = b + ax + bz + q15;
+        om[12] = b - ax + bz - q15;
+        om[13] = b + ax - bz - q15;
+        om[14] = b - ax - bz + q15;
     }
     {   // (0, +-1, +-1)
         const float b = Dg - 2.f * P, ay = q5 + q6 + q17, bz = q7 + q8 - q18;
-        d[15] += b + ay + bz + q14;
-        d[16] += b - ay + bz - q14;
-        d[17] += b + ay - bz - q14;
-        d[18] += b - ay - bz + q14;
+        om[15] = b + ay + bz + q14;
+        om[16] = b - ay + bz - q14;
+        om[17] = b + ay - bz - q14;
+        om[18] = b - ay - bz + q14;
     }
 }
 
@@ -338,7 +392,8 @@ __device__ __forceinline__ V warp_sum(V v)
 template <int ST, bool MHD, int MODE>
 __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
 {
-    using T = typename Store<ST>::T;
+    using S = Store<ST>;
+    using T = typename S::T;
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     const bool inb = i < p.N;
@@ -352,12 +407,12 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
 
     double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (fluid) {
-        float d[19];
-        load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d);
-        float q[21];
+        float d[19], dl[19];
+        load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+        float q[21], ql[21];
         float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
         if (MHD) {
-            load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q);
+            load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q, ql);
             FLpx = b.FL[n];
             FLpy = b.FL[N + n];
             FLpz = b.FL[2 * N + n];
@@ -381,8 +436,9 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         NodeMacro mac;
         mac.Bx = mac.By = mac.Bz = 0.f;
         mac.FLx = mac.FLy = mac.FLz = 0.f;
+        float og[21];
         if (MHD) {
-            induction_collide(p, q, rho_inv, mx, my, mz, Fx, Fy, Fz, FLpx, FLpy, FLpz, mac);
+            induction_collide(p, q, og, rho_inv, mx, my, mz, Fx, Fy, Fz, FLpx, FLpy, FLpz, mac);
             Fx += mac.FLx;
             Fy += mac.FLy;
             Fz += mac.FLz;
@@ -398,14 +454,38 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
             return;
         }
 
-        flow_collide(p, d, drho, rho_inv, jx, jy, jz, Fx, Fy, Fz);
+        float om[19];
+        flow_collide(p, d, om, drho, rho_inv, jx, jy, jz, Fx, Fy, Fz);
+        // f~ = f + om, written to the node's own slot of the other buffer
         T* __restrict__ fd = static_cast<T*>(b.fdst);
+        if constexpr (S::COMP) {
+            __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
 #pragma unroll
-        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = Store<ST>::cv(d[a] * p.scale);
+            for (int a = 0; a < 19; ++a) {
+                float nh, nl;
+                comp_add(d[a], dl[a], om[a], nh, nl);
+                fd[(size_t)a * N + n] = nh;
+                fdl[(size_t)a * N + n] = S::cv_lo(nl);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv((d[a] + om[a]) * p.scale);
+        }
         if (MHD) {
             T* __restrict__ gd = static_cast<T*>(b.gdst);
+            if constexpr (S::COMP) {
+                __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
 #pragma unroll
-            for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = Store<ST>::cv(q[a] * p.scale);
+                for (int a = 0; a < 21; ++a) {
+                    float nh, nl;
+                    comp_add(q[a], ql[a], og[a], nh, nl);
+                    gd[(size_t)a * N + n] = nh;
+                    gdl[(size_t)a * N + n] = S::cv_lo(nl);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv((q[a] + og[a]) * p.scale);
+            }
             b.FL[n] = mac.FLx;
             b.FL[N + n] = mac.FLy;
             b.FL[2 * N + n] = mac.FLz;
@@ -451,6 +531,7 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
 }
 
 // Pre-collision state (deviations, FP32, C-ABI layout) of every fluid node.
+// The compensated form returns high + low rounded to FP32.
 template <int ST, bool MHD>
 __global__ void __launch_bounds__(STEP_THREADS) get_state_kernel(const StepParams p, const void* fsrc,
                                                                  const void* gsrc, const float* FL, float* df,
@@ -468,14 +549,14 @@ __global__ void __launch_bounds__(STEP_THREADS) get_state_kernel(const StepParam
         return;
     }
     if (df) {
-        float d[19];
-        load_f<ST>(p, static_cast<const T*>(fsrc), g, d);
-        for (int a = 0; a < 19; ++a) df[(size_t)a * N + i] = d[a];
+        float d[19], l[19];
+        load_f<ST>(p, static_cast<const T*>(fsrc), g, d, l);
+        for (int a = 0; a < 19; ++a) df[(size_t)a * N + i] = Store<ST>::COMP ? d[a] + l[a] : d[a];
     }
     if (MHD && dg) {
-        float q[21];
-        load_g<ST>(p, static_cast<const T*>(gsrc), g, q);
-        for (int a = 0; a < 21; ++a) dg[(size_t)a * N + i] = q[a];
+        float q[21], ql[21];
+        load_g<ST>(p, static_cast<const T*>(gsrc), g, q, ql);
+        for (int a = 0; a < 21; ++a) dg[(size_t)a * N + i] = Store<ST>::COMP ? q[a] + ql[a] : q[a];
     }
     if (MHD && dFL)
         for (int k = 0; k < 3; ++k) dFL[(size_t)k * N + i] = FL[(size_t)k * N + i];
@@ -484,6 +565,7 @@ __global__ void __launch_bounds__(STEP_THREADS) get_state_kernel(const StepParam
 // Inverse of get_state: each pre-collision value is written into the slot the
 // next pull reads it from (the upstream node's slot, or the own node's
 // opposite slot across a wall).  Every slot of a fluid node is written once.
+// The compensated form starts with a zero low part.
 template <int ST, bool MHD>
 __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParams p, void* fsrc, void* gsrc,
                                                                  float* FL, const float* df, const float* dg,
@@ -497,22 +579,35 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
     const size_t N = p.N;
     if (df) {
         T* fs = static_cast<T*>(fsrc);
-        fs[i] = Store<ST>::cv(df[i] * p.scale);
-#define GLBE_STOREF(a, o, src, sol) \
-    fs[(sol) ? (size_t)(o) * N + i : (size_t)(a) * N + (src)] = Store<ST>::cv(df[(size_t)(a) * N + i] * p.scale);
+        __half* fl = Store<ST>::COMP ? reinterpret_cast<__half*>(fs + 19 * N) : nullptr;
+#define GLBE_SLOTF(a, o, src, sol) ((sol) ? (size_t)(o) * N + i : (size_t)(a) * N + (src))
+#define GLBE_STOREF(a, o, src, sol)                                                         \
+    {                                                                                       \
+        const size_t s_ = GLBE_SLOTF(a, o, src, sol);                                       \
+        fs[s_] = Store<ST>::cv(df[(size_t)(a) * N + i] * p.scale);                          \
+        if (Store<ST>::COMP) fl[s_] = __float2half_rn(0.f);                                 \
+    }
+        GLBE_STOREF(0, 0, i, false)
         GLBE_DIRS(GLBE_STOREF)
 #undef GLBE_STOREF
+#undef GLBE_SLOTF
     }
     if (MHD && dg) {
         T* gs = static_cast<T*>(gsrc);
+        __half* gl = Store<ST>::COMP ? reinterpret_cast<__half*>(gs + 21 * N) : nullptr;
         for (int j = 0; j < 3; ++j) {
             T* bj = gs + (size_t)(j * 7) * N;
+            __half* blj = Store<ST>::COMP ? gl + (size_t)(j * 7) * N : nullptr;
             const float* vj = dg + (size_t)(j * 7) * N;
             const float wall = 0.25f * p.bwall_dev[j];
-            bj[i] = Store<ST>::cv(vj[i] * p.scale);
-#define GLBE_STOREG(a, o, src, sol)                                                     \
-    if (sol) bj[(size_t)(o) * N + i] = Store<ST>::cv((wall - vj[(size_t)(a) * N + i]) * p.scale); \
-    else bj[(size_t)(a) * N + (src)] = Store<ST>::cv(vj[(size_t)(a) * N + i] * p.scale);
+#define GLBE_STOREG(a, o, src, sol)                                                                  \
+    {                                                                                                \
+        const size_t s_ = (sol) ? (size_t)(o) * N + i : (size_t)(a) * N + (src);                     \
+        const float v_ = (sol) ? wall - vj[(size_t)(a) * N + i] : vj[(size_t)(a) * N + i];          \
+        bj[s_] = Store<ST>::cv(v_ * p.scale);                                                        \
+        if (Store<ST>::COMP) blj[s_] = __float2half_rn(0.f);                                         \
+    }
+            GLBE_STOREG(0, 0, i, false)
             GLBE_DIRS7(GLBE_STOREG)
 #undef GLBE_STOREG
         }

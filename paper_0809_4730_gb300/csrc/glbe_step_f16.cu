@@ -1,5 +1,5 @@
 // Instantiates the fused step, field and state kernels for F16 storage of the
-// population deviations (one translation unit per storage type so the three
+// population deviations (one translation unit per storage type so they
 // compile in parallel).
 #include "glbe_kernels.cuh"
 

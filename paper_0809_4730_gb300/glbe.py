@@ -17,8 +17,8 @@ import threading
 from . import build as _build
 
 GLBE_OK, GLBE_ERR_ARG, GLBE_ERR_CUDA, GLBE_ERR_DIVERGED, GLBE_ERR_TIMEOUT, GLBE_ERR_STATE = range(6)
-GLBE_F32, GLBE_BF16, GLBE_F16 = 0, 1, 2
-STORAGE = {"f32": GLBE_F32, "bf16": GLBE_BF16, "f16": GLBE_F16}
+GLBE_F32, GLBE_BF16, GLBE_F16, GLBE_F32C = 0, 1, 2, 3
+STORAGE = {"f32": GLBE_F32, "bf16": GLBE_BF16, "f16": GLBE_F16, "f32c": GLBE_F32C}
 
 
 class GlbeError(RuntimeError):
