@@ -61,6 +61,16 @@ template <> struct Store<ST_F32C> {
     static __device__ __forceinline__ __half cv_lo(float v) { return __float2half_rn(v * LO_SCALE); }
 };
 
+// fl(a + b + c) for |c| small: the exact two-sum of a and b, its remainder
+// plus c, rounded once.
+__device__ __forceinline__ float two_sum_round(float a, float b, float c)
+{
+    const float s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    return __fadd_rn(s, __fadd_rn(e, c));
+}
+
 // h + o + l as a new (high, low) pair: exact two-sum of h and o, the
 // remainder plus the old low part renormalised into the new low part.
 __device__ __forceinline__ void comp_add(float h, float l, float o, float& nh, float& nl)
@@ -267,19 +277,18 @@ __device__ __forceinline__ void induction_collide(const StepParams& p, const flo
     for (int i = 0; i < 21; ++i) og[i] = w * (geq[i] - q[i]);
 }
 
-// D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
-// (I - Lambda*/2) S*] of the deviations d (Eqs. ppostcollision, prelax_term).
-// F is the total force, (jx, jy, jz) = m + F/(2 gamma).
-__device__ __forceinline__ void flow_collide(const StepParams& p, const float (&d)[19], float (&om)[19], float drho,
-                                             float rho_inv,
-                                             float jx, float jy, float jz, float Fx, float Fy, float Fz)
-{
-    const float ig = p.inv_gamma, ig2 = p.inv_gamma2;
-    const float gri = ig * rho_inv;                   // 1/(gamma rho)
-    const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
-    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
+// Moments of a set of 19 deviations that are linear in them: group sums over
+// the rest, axis and the three diagonal planes, then the rows of T (App. A).
+struct Lin {
+    float drho, mx, my, mz;          // rows 0, 3, 5, 7
+    float M1, M2;                    // e, e^2 (rows 1, 2)
+    float Qx, Qy, Qz;                // q (rows 4, 6, 8)
+    float P9, P10, P11, P12, P13, P14, P15, P16, P17, P18;
+};
 
-    // group sums
+__device__ __forceinline__ Lin linear_moments(const float (&d)[19])
+{
+    Lin L;
     const float Ax = d[1] + d[2], Ay = d[3] + d[4], Az = d[5] + d[6];
     const float Sax = Ax + Ay + Az;
     const float Gxy = d[7] + d[8] + d[9] + d[10];
@@ -289,26 +298,92 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const float (&
     const float Xax = d[1] - d[2], Xxy = d[7] - d[8] + d[9] - d[10], Xxz = d[11] - d[12] + d[13] - d[14];
     const float Yax = d[3] - d[4], Yxy = d[7] + d[8] - d[9] - d[10], Yyz = d[15] - d[16] + d[17] - d[18];
     const float Zax = d[5] - d[6], Zxz = d[11] + d[12] - d[13] - d[14], Zyz = d[15] + d[16] - d[17] - d[18];
+    L.drho = d[0] + Sax + Sdg;
+    L.mx = Xax + Xxy + Xxz;
+    L.my = Yax + Yxy + Yyz;
+    L.mz = Zax + Zxz + Zyz;
+    L.M1 = -30.f * d[0] - 11.f * Sax + 8.f * Sdg;
+    L.M2 = 12.f * d[0] - 4.f * Sax + Sdg;
+    L.Qx = -4.f * Xax + Xxy + Xxz;
+    L.Qy = -4.f * Yax + Yxy + Yyz;
+    L.Qz = -4.f * Zax + Zxz + Zyz;
+    L.P9 = 2.f * Ax - Ay - Az + Gxy + Gxz - 2.f * Gyz;
+    L.P10 = -4.f * Ax + 2.f * Ay + 2.f * Az + Gxy + Gxz - 2.f * Gyz;
+    L.P11 = Ay - Az + Gxy - Gxz;
+    L.P12 = -2.f * Ay + 2.f * Az + Gxy - Gxz;
+    L.P13 = d[7] - d[8] - d[9] + d[10];
+    L.P14 = d[15] - d[16] - d[17] + d[18];
+    L.P15 = d[11] - d[12] - d[13] + d[14];
+    L.P16 = Xxy - Xxz;
+    L.P17 = Yyz - Yxy;
+    L.P18 = Zxz - Zyz;
+    return L;
+}
 
-    // moments of the deviations and their non-equilibrium parts n_k = f^_k - f^eq,*_k
-    // (the rest state contributes -11 rho0 to row 1 and 3 rho0 to row 2 only)
-    const float n1 = (-30.f * d[0] - 11.f * Sax + 8.f * Sdg) + 11.f * drho - 19.f * jj * gri;
-    const float n2 = (12.f * d[0] - 4.f * Sax + Sdg) - 3.f * drho + 5.5f * jj * gri;
-    const float n4 = (-4.f * Xax + Xxy + Xxz) + (2.f / 3.f) * jx;
-    const float n6 = (-4.f * Yax + Yxy + Yyz) + (2.f / 3.f) * jy;
-    const float n8 = (-4.f * Zax + Zxz + Zyz) + (2.f / 3.f) * jz;
+// Error-free split d = dh + dl with dh on the grid of multiples of 2^-28
+// (|d| <= 2^-5): integer-weighted sums of the dh are then exact in FP32 while
+// they stay below 2^-4, and the dl (|dl| <= 2^-29) carry the rest.  Moments
+// formed as (exact high sum - equilibrium) + low sum keep the small
+// non-equilibrium parts free of the round-off of the large sums, which
+// otherwise leaves the FP32 time march wandering at r ~ 1e-7 instead of
+// settling on its fixed point.
+constexpr float SPLIT_C = 0.046875f;   // 1.5 * 2^-5
+
+__device__ __forceinline__ void split_exact(const float (&d)[19], float (&dh)[19], float (&dl)[19])
+{
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        dh[a] = __fsub_rn(__fadd_rn(d[a], SPLIT_C), SPLIT_C);
+        dl[a] = __fsub_rn(d[a], dh[a]);
+    }
+}
+
+// Non-equilibrium moments and conserved sums of a node.  H holds the linear
+// moments of the populations (or of their exact high parts) and L those of the
+// low parts (PRECISE) -- L is not read otherwise.
+template <bool PRECISE>
+struct NodeMoments {
+    Lin H, L;
+    __device__ __forceinline__ float drho() const { return PRECISE ? H.drho + L.drho : H.drho; }
+};
+
+// D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
+// (I - Lambda*/2) S*] (Eqs. ppostcollision, prelax_term).  F is the total
+// force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32.
+template <bool PRECISE>
+__device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<PRECISE>& mm, float (&om)[19],
+                                             float rho_inv, float jx, float jy, float jz, float Fx, float Fy,
+                                             float Fz)
+{
+    const float ig = p.inv_gamma, ig2 = p.inv_gamma2;
+    const float gri = ig * rho_inv;                   // 1/(gamma rho)
+    const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
+    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
+    const Lin& H = mm.H;
+    const Lin& L = mm.L;
+#define GLBE_LO(expr) (PRECISE ? (expr) : 0.f)
+#define GLBE_NK(hi, lo) (PRECISE ? (hi) + (lo) : (hi))
+    // n_k = f^_k - f^eq,*_k; the rest state contributes -11 rho0 to row 1 and
+    // 3 rho0 to row 2 only, so the deviations' moments enter directly
+    const float n1 = GLBE_NK((H.M1 + 11.f * H.drho) - 19.f * jj * gri, GLBE_LO(L.M1 + 11.f * L.drho));
+    const float n2 = GLBE_NK((H.M2 - 3.f * H.drho) + 5.5f * jj * gri, GLBE_LO(L.M2 - 3.f * L.drho));
+    const float n4 = GLBE_NK(H.Qx, GLBE_LO(L.Qx)) + (2.f / 3.f) * jx;
+    const float n6 = GLBE_NK(H.Qy, GLBE_LO(L.Qy)) + (2.f / 3.f) * jy;
+    const float n8 = GLBE_NK(H.Qz, GLBE_LO(L.Qz)) + (2.f / 3.f) * jz;
     const float e9 = (3.f * jxx - jj) * gri;
     const float e11 = (jyy - jzz) * gri;
-    const float n9 = (2.f * Ax - Ay - Az + Gxy + Gxz - 2.f * Gyz) - e9;
-    const float n10 = (-4.f * Ax + 2.f * Ay + 2.f * Az + Gxy + Gxz - 2.f * Gyz) + 0.5f * e9;
-    const float n11 = (Ay - Az + Gxy - Gxz) - e11;
-    const float n12 = (-2.f * Ay + 2.f * Az + Gxy - Gxz) + 0.5f * e11;
-    const float n13 = (d[7] - d[8] - d[9] + d[10]) - jx * jy * gri;
-    const float n14 = (d[15] - d[16] - d[17] + d[18]) - jy * jz * gri;
-    const float n15 = (d[11] - d[12] - d[13] + d[14]) - jx * jz * gri;
-    const float n16 = Xxy - Xxz;
-    const float n17 = Yyz - Yxy;
-    const float n18 = Zxz - Zyz;
+    const float n9 = GLBE_NK(H.P9 - e9, GLBE_LO(L.P9));
+    const float n10 = GLBE_NK(H.P10 + 0.5f * e9, GLBE_LO(L.P10));
+    const float n11 = GLBE_NK(H.P11 - e11, GLBE_LO(L.P11));
+    const float n12 = GLBE_NK(H.P12 + 0.5f * e11, GLBE_LO(L.P12));
+    const float n13 = GLBE_NK(H.P13 - jx * jy * gri, GLBE_LO(L.P13));
+    const float n14 = GLBE_NK(H.P14 - jy * jz * gri, GLBE_LO(L.P14));
+    const float n15 = GLBE_NK(H.P15 - jx * jz * gri, GLBE_LO(L.P15));
+    const float n16 = GLBE_NK(H.P16, GLBE_LO(L.P16));
+    const float n17 = GLBE_NK(H.P17, GLBE_LO(L.P17));
+    const float n18 = GLBE_NK(H.P18, GLBE_LO(L.P18));
+#undef GLBE_LO
+#undef GLBE_NK
 
     // preconditioned source moments S* = P_S S (App. A, Eq. precondsourceterm)
     const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
@@ -417,15 +492,27 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
             FLpy = b.FL[N + n];
             FLpz = b.FL[2 * N + n];
         }
-        // density and bare first moment (Eq. precondhydrofields)
-        float drho = 0.f;
+        // moments linear in the populations; density and bare first moment
+        // (Eq. precondhydrofields)
+        constexpr bool PRECISE = (ST == ST_F32 || ST == ST_F32C);
+        NodeMoments<PRECISE> mm;
+        if constexpr (PRECISE) {
+            float dh[19], dlo[19];
+            split_exact(d, dh, dlo);
+            if constexpr (S::COMP) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) drho += d[a];
+                for (int a = 0; a < 19; ++a) dlo[a] += dl[a];
+            }
+            mm.H = linear_moments(dh);
+            mm.L = linear_moments(dlo);
+        } else {
+            mm.H = linear_moments(d);
+        }
+        const float drho = mm.drho();
         const float rho = p.rho0 + drho;
         const float rho_inv = 1.0f / rho;
-        const float mx = (d[1] - d[2]) + (d[7] - d[8] + d[9] - d[10]) + (d[11] - d[12] + d[13] - d[14]);
-        const float my = (d[3] - d[4]) + (d[7] + d[8] - d[9] - d[10]) + (d[15] - d[16] + d[17] - d[18]);
-        const float mz = (d[5] - d[6]) + (d[11] + d[12] - d[13] - d[14]) + (d[15] + d[16] - d[17] - d[18]);
+        const float mxh = mm.H.mx, myh = mm.H.my, mzh = mm.H.mz;
+        const float mxl = PRECISE ? mm.L.mx : 0.f, myl = PRECISE ? mm.L.my : 0.f, mzl = PRECISE ? mm.L.mz : 0.f;
         // external force
         float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
         if (p.force_ncomp >= 1) Fx += __ldg(b.Ffield + n);
@@ -438,13 +525,25 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         mac.FLx = mac.FLy = mac.FLz = 0.f;
         float og[21];
         if (MHD) {
-            induction_collide(p, q, og, rho_inv, mx, my, mz, Fx, Fy, Fz, FLpx, FLpy, FLpz, mac);
+            induction_collide(p, q, og, rho_inv, mxh + mxl, myh + myl, mzh + mzl, Fx, Fy, Fz, FLpx, FLpy, FLpz,
+                              mac);
             Fx += mac.FLx;
             Fy += mac.FLy;
             Fz += mac.FLz;
         }
+        // j = m + F/(2 gamma): in the precise path the high parts and the
+        // half-force are added by an exact two-sum before rounding once
         const float hg = 0.5f * p.inv_gamma;
-        const float jx = mx + hg * Fx, jy = my + hg * Fy, jz = mz + hg * Fz;
+        float jx, jy, jz;
+        if constexpr (PRECISE) {
+            jx = two_sum_round(mxh, hg * Fx, mxl);
+            jy = two_sum_round(myh, hg * Fy, myl);
+            jz = two_sum_round(mzh, hg * Fz, mzl);
+        } else {
+            jx = mxh + hg * Fx;
+            jy = myh + hg * Fy;
+            jz = mzh + hg * Fz;
+        }
         const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
 
         if (MODE == MODE_FIELDS) {
@@ -455,7 +554,7 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         }
 
         float om[19];
-        flow_collide(p, d, om, drho, rho_inv, jx, jy, jz, Fx, Fy, Fz);
+        flow_collide<PRECISE>(p, mm, om, rho_inv, jx, jy, jz, Fx, Fy, Fz);
         // f~ = f + om, written to the node's own slot of the other buffer
         T* __restrict__ fd = static_cast<T*>(b.fdst);
         if constexpr (S::COMP) {
