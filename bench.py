@@ -359,8 +359,8 @@ def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
 def time_to_solution():
     """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Ha = 10,
     Pr_m = 0.01, nu = eta = 0.01) at gamma = gamma_m = 0.1 and 1, same GPU,
-    FP32 storage and arithmetic, with the error of the converged u against
-    the analytic profile."""
+    FP32 arithmetic with compensated (F32C) storage, with the error of the
+    converged u against the analytic profile."""
     import torch
     from paper_0809_4730_gb300.glbe import Solver
     res = {}
@@ -369,7 +369,7 @@ def time_to_solution():
     ua = hartmann_analytic(64, Ha)
     for gamma in (0.1, 1.0):
         G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
-                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
+                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0), storage="f32c")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, steps, r = G.solve(1e-8, 3_000_000)

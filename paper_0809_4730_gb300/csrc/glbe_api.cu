@@ -154,25 +154,33 @@ StepParams make_step_params(const glbe_params* p)
     return s;
 }
 
-__global__ void finalize_kernel(const double* __restrict__ partials, unsigned nblocks, long long* t_dev,
-                                double* record, double* hist, unsigned long long* hist_count, unsigned hist_cap,
-                                int* stop, const double* tol)
+constexpr int FIN_THREADS = 1024;
+
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(const double* __restrict__ partials, unsigned nblocks,
+                                                               double mass0, long long* t_dev, double* record,
+                                                               double* hist, unsigned long long* hist_count,
+                                                               unsigned hist_cap, int* stop, const double* tol)
 {
     if (*stop) return;   // a solve already converged: the chunk's remaining work is skipped
-    __shared__ double sh[7][256];
+    __shared__ double sh[7][FIN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < 7; ++k) {
+        // partials are [k][block]: consecutive threads read consecutive blocks
+        const double* pk = partials + (size_t)k * nblocks;
         double s = 0.0;
-        for (unsigned b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * PARTIAL_STRIDE + k];
-        sh[k][threadIdx.x] = s;
+        for (unsigned b = threadIdx.x; b < nblocks; b += FIN_THREADS) s += pk[b];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][warp] = s;
     }
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        const double num = sh[0][0], den = sh[1][0];
+        double tot[7];
+        for (int k = 0; k < 7; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < FIN_THREADS / 32; ++w) s += sh[k][w];
+            tot[k] = s;
+        }
+        const double num = tot[0], den = tot[1];
         const double r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
         const long long t = *t_dev;
         double rec[RECORD_STRIDE] = {0};
@@ -180,11 +188,11 @@ __global__ void finalize_kernel(const double* __restrict__ partials, unsigned nb
         rec[1] = r;
         rec[2] = num;
         rec[3] = den;
-        rec[4] = sh[2][0];
-        rec[5] = sh[3][0];
-        rec[6] = sh[4][0];
-        rec[7] = sh[5][0];
-        rec[8] = sh[6][0];
+        rec[4] = mass0 + tot[2];
+        rec[5] = tot[3];
+        rec[6] = tot[4];
+        rec[7] = tot[5];
+        rec[8] = tot[6];
         for (int k = 0; k < RECORD_STRIDE; ++k) record[k] = rec[k];
         const unsigned long long c = *hist_count;
         double* h = hist + (size_t)(c % hist_cap) * RECORD_STRIDE;
@@ -229,6 +237,7 @@ struct glbe_ctx {
     long long* t_dev;
     int* stop_dev;
     double* tol_dev;
+    double mass0;   // rho0 x number of fluid nodes
     long t;         // current time level
     long t_snap;    // level of the velocity snapshot, -1 if none
     cudaStream_t stream;
@@ -275,8 +284,8 @@ glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
         b.have_snap = (c->t_snap >= 0 && c->t_snap == c->t - 10) ? 1 : 0;
         GLBE_CUDA(launch_step_any(c, MODE_STEP_RESID, b, fo, st), "step kernel (residual)");
         if (b.have_snap) {
-            GLBE_CUDA(launch_finalize(c->partials, c->grid, c->t_dev, c->record, c->hist, c->hist_count, HIST_CAP,
-                                      c->stop_dev, c->tol_dev, st),
+            GLBE_CUDA(launch_finalize(c->partials, c->grid, c->mass0, c->t_dev, c->record, c->hist, c->hist_count,
+                                      HIST_CAP, c->stop_dev, c->tol_dev, st),
                       "residual finalize");
         } else {
             misc_set_kernel<<<1, 1, 0, st>>>(c->t_dev, (long long)c->t + 10, nullptr, 0, nullptr, 0.0, nullptr,
@@ -294,11 +303,12 @@ glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
 }  // namespace
 
 namespace glbe {
-cudaError_t launch_finalize(const double* partials, unsigned nblocks, long long* t_dev, double* record, double* hist,
-                            unsigned long long* hist_count, unsigned hist_cap, int* stop, const double* tol,
-                            cudaStream_t st)
+cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mass0, long long* t_dev, double* record,
+                            double* hist, unsigned long long* hist_count, unsigned hist_cap, int* stop,
+                            const double* tol, cudaStream_t st)
 {
-    finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, t_dev, record, hist, hist_count, hist_cap, stop, tol);
+    finalize_kernel<<<1, FIN_THREADS, 0, st>>>(partials, nblocks, mass0, t_dev, record, hist, hist_count, hist_cap,
+                                               stop, tol);
     return cudaGetLastError();
 }
 }  // namespace glbe
@@ -380,6 +390,13 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     c->t_dev = reinterpret_cast<long long*>(misc + 8);
     c->tol_dev = reinterpret_cast<double*>(misc + 16);
     c->stop_dev = reinterpret_cast<int*>(misc + 24);
+    {
+        // fluid nodes: product over the axes of the planes not on a wall
+        const long long fx = p->nx - p->wall_lo[0] - p->wall_hi[0];
+        const long long fy = p->ny - p->wall_lo[1] - p->wall_hi[1];
+        const long long fz = p->nz - p->wall_lo[2] - p->wall_hi[2];
+        c->mass0 = p->rho0 * (double)(fx * fy * fz);
+    }
     c->t = 0;
     c->t_snap = -1;
     c->stream = static_cast<cudaStream_t>(p->stream);

@@ -57,7 +57,7 @@ struct StepBuffers {
     float* FL;            // [3][N] Lorentz force of the previous step (in place)
     const float* Ffield;  // [force_ncomp][N] or null
     float* usnap;         // [3][N] velocity snapshot of the last residual level
-    double* partials;     // [gridDim.x][8] per-block residual sums
+    double* partials;     // [8][gridDim.x] per-block residual sums
     int have_snap;        // 1: usnap holds u(t-10)
     const int* stop;      // null, or a device flag: when set the launch does nothing
 };
@@ -66,7 +66,7 @@ enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };
 enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
 
 constexpr int STEP_THREADS = 256;
-constexpr int PARTIAL_STRIDE = 8;   // doubles per block: num, den, mass, Mx, My, Mz, nonfinite, pad
+constexpr int PARTIAL_STRIDE = 8;   // per block: num, den, sum drho, Mx, My, Mz, nonfinite, pad; stored [k][block]
 
 // Outputs of MODE_FIELDS.
 struct FieldOut {
@@ -88,13 +88,13 @@ cudaError_t launch_set_state_t(bool mhd, const StepParams& p, void* fsrc, void* 
 
 // Reduces the per-block partials of a residual step in a fixed order into
 // record[0..8] = (t, r, num, den, mass, Mx, My, Mz, nonfinite), with t read
-// from *t_dev and then advanced by 10, and appends the record to the history
-// ring hist[(count % cap) * RECORD_STRIDE].
+// from *t_dev and then advanced by 10, mass = mass0 + sum drho, and appends
+// the record to the history ring hist[(count % cap) * RECORD_STRIDE].
 constexpr int RECORD_STRIDE = 16;
 // The reduction also raises *stop when r <= *tol (tol > 0) or a velocity is
 // non-finite, and does nothing once *stop is set.
-cudaError_t launch_finalize(const double* partials, unsigned nblocks, long long* t_dev, double* record,
-                            double* hist, unsigned long long* hist_count, unsigned hist_cap, int* stop,
-                            const double* tol, cudaStream_t st);
+cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mass0, long long* t_dev,
+                            double* record, double* hist, unsigned long long* hist_count, unsigned hist_cap,
+                            int* stop, const double* tol, cudaStream_t st);
 
 }  // namespace glbe

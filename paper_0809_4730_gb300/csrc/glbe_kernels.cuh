@@ -220,6 +220,10 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     }
 }
 
+// Grid constant of the error-free split x = xh + xl, xh = (x + C) - C: for
+// |x| <= 2^-5 the high parts are multiples of 2^-28.
+constexpr float SPLIT_C = 0.046875f;   // 1.5 * 2^-5
+
 // Everything a node's collision produces besides the new populations.
 struct NodeMacro {
     float rho, ux, uy, uz;
@@ -229,15 +233,42 @@ struct NodeMacro {
 
 // Induction part: B, Lorentz force from the previous step's half-force
 // velocity, and the D3Q7 collision change og = (g^eq - g)/tau_m (Eq. mcollision).
-__device__ __forceinline__ void induction_collide(const StepParams& p, const float (&q)[21], float (&og)[21],
-                                                  float rho_inv, float mx,
-                                                  float my, float mz, float Fx, float Fy, float Fz, float FLpx,
-                                                  float FLpy, float FLpz, NodeMacro& mac)
+// PRECISE: B_j is formed from the exact split of the populations (qh on the
+// 2^-28 grid, ql the remainder) and g^eq - g as (W_a Bh_j - qh_a) +
+// (W_a Bl_j - ql_a) +- the convective term: W_a is a power of two, so the
+// first bracket is exact and the rounding of the 7-term sum B no longer
+// biases every population's relaxation (a bias the slow magnetic diffusion
+// mode would otherwise integrate into a 3e-5 error of the steady flow).
+template <bool PRECISE, bool COMP>
+__device__ __forceinline__ void induction_collide(const StepParams& p, const float (&q)[21], const float (&qlo)[21],
+                                                  float (&og)[21], float rho_inv, float mx, float my, float mz,
+                                                  float Fx, float Fy, float Fz, float FLpx, float FLpy, float FLpz,
+                                                  NodeMacro& mac)
 {
+    float qh[21], ql[21];
+    if constexpr (PRECISE) {
+#pragma unroll
+        for (int i = 0; i < 21; ++i) {
+            qh[i] = __fsub_rn(__fadd_rn(q[i], SPLIT_C), SPLIT_C);
+            ql[i] = __fsub_rn(q[i], qh[i]);
+            if constexpr (COMP) ql[i] += qlo[i];   // low part of the compensated storage
+        }
+    }
     // B_j = B0_j + sum_a dg_ja (sum_a W_a = 1), Eq. magneticinduction
-    const float bx = q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6];
-    const float by = q[7] + q[8] + q[9] + q[10] + q[11] + q[12] + q[13];
-    const float bz = q[14] + q[15] + q[16] + q[17] + q[18] + q[19] + q[20];
+    float bxh, byh, bzh, bxl = 0.f, byl = 0.f, bzl = 0.f;
+    if constexpr (PRECISE) {
+        bxh = qh[0] + qh[1] + qh[2] + qh[3] + qh[4] + qh[5] + qh[6];
+        byh = qh[7] + qh[8] + qh[9] + qh[10] + qh[11] + qh[12] + qh[13];
+        bzh = qh[14] + qh[15] + qh[16] + qh[17] + qh[18] + qh[19] + qh[20];
+        bxl = ql[0] + ql[1] + ql[2] + ql[3] + ql[4] + ql[5] + ql[6];
+        byl = ql[7] + ql[8] + ql[9] + ql[10] + ql[11] + ql[12] + ql[13];
+        bzl = ql[14] + ql[15] + ql[16] + ql[17] + ql[18] + ql[19] + ql[20];
+    } else {
+        bxh = q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6];
+        byh = q[7] + q[8] + q[9] + q[10] + q[11] + q[12] + q[13];
+        bzh = q[14] + q[15] + q[16] + q[17] + q[18] + q[19] + q[20];
+    }
+    const float bx = bxh + bxl, by = byh + byl, bz = bzh + bzl;
     const float Bx = p.B0[0] + bx, By = p.B0[1] + by, Bz = p.B0[2] + bz;
     // velocity with the previous step's Lorentz force in the half-force
     const float hg = 0.5f * p.inv_gamma;
@@ -264,17 +295,26 @@ __device__ __forceinline__ void induction_collide(const StepParams& p, const flo
     mac.FLy = Jz * Bx - Jx * Bz;
     mac.FLz = Jx * By - Jy * Bx;
     mac.Bx = Bx; mac.By = By; mac.Bz = Bz;
-    // g^eq,* deviations: W_0 b_j (rest), W_1 (b_j +- Lambda^eq_kj / theta_m), 1/theta_m = 4
+    // g^eq,* deviations: W_0 b_j (rest), W_1 (b_j +- Lambda^eq_kj / theta_m), 1/theta_m = 4,
+    // so the convective part is +-W_1 * 4 * L = +-L/2
     const float w = p.omega_m;
-    const float ex0 = 0.25f * bx, ey0 = 0.25f * by, ez0 = 0.25f * bz;
-    const float ex = 0.125f * bx, ey = 0.125f * by, ez = 0.125f * bz;
-    const float Axy = 0.5f * Lxy, Axz = 0.5f * Lxz, Ayz = 0.5f * Lyz;   // W_1 * 4 * L
-    float geq[21] = {
-        ex0, ex, ex, ex - Axy, ex + Axy, ex - Axz, ex + Axz,       // j = x
-        ey0, ey + Axy, ey - Axy, ey, ey, ey - Ayz, ey + Ayz,       // j = y
-        ez0, ez + Axz, ez - Axz, ez + Ayz, ez - Ayz, ez, ez};      // j = z
+    const float Axy = 0.5f * Lxy, Axz = 0.5f * Lxz, Ayz = 0.5f * Lyz;
+    // sign of the convective term of each (j, a): a = 0 rest, 1..6 = +x,-x,+y,-y,+z,-z
+    const float conv[21] = {
+        0.f, 0.f, 0.f, -Axy, Axy, -Axz, Axz,          // j = x: Lambda^eq_yx = -Lxy, Lambda^eq_zx = -Lxz
+        0.f, Axy, -Axy, 0.f, 0.f, -Ayz, Ayz,          // j = y: Lambda^eq_xy = Lxy, Lambda^eq_zy = -Lyz
+        0.f, Axz, -Axz, Ayz, -Ayz, 0.f, 0.f};         // j = z: Lambda^eq_xz = Lxz, Lambda^eq_yz = Lyz
 #pragma unroll
-    for (int i = 0; i < 21; ++i) og[i] = w * (geq[i] - q[i]);
+    for (int i = 0; i < 21; ++i) {
+        const int j = i / 7, a = i % 7;
+        const float W = a == 0 ? 0.25f : 0.125f;
+        const float bh = j == 0 ? bxh : (j == 1 ? byh : bzh);
+        const float bl = j == 0 ? bxl : (j == 1 ? byl : bzl);
+        float neq;
+        if constexpr (PRECISE) neq = (W * bh - qh[i]) + ((W * bl - ql[i]) + conv[i]);
+        else neq = (W * bh + conv[i]) - q[i];
+        og[i] = w * neq;
+    }
 }
 
 // Moments of a set of 19 deviations that are linear in them: group sums over
@@ -327,7 +367,6 @@ __device__ __forceinline__ Lin linear_moments(const float (&d)[19])
 // non-equilibrium parts free of the round-off of the large sums, which
 // otherwise leaves the FP32 time march wandering at r ~ 1e-7 instead of
 // settling on its fixed point.
-constexpr float SPLIT_C = 0.046875f;   // 1.5 * 2^-5
 
 __device__ __forceinline__ void split_exact(const float (&d)[19], float (&dh)[19], float (&dl)[19])
 {
@@ -480,7 +519,10 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
     if (MODE == MODE_STEP && !fluid) return;
     if (MODE == MODE_FIELDS && !inb) return;
 
-    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // residual sums: FP32 per node and per warp (each term is one node's
+    // FP32 quantity), FP64 from the block level on -- GB300's FP64 pipe is
+    // kept off the per-node path
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (fluid) {
         float d[19], dl[19];
         load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
@@ -525,8 +567,8 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         mac.FLx = mac.FLy = mac.FLz = 0.f;
         float og[21];
         if (MHD) {
-            induction_collide(p, q, og, rho_inv, mxh + mxl, myh + myl, mzh + mzl, Fx, Fy, Fz, FLpx, FLpy, FLpz,
-                              mac);
+            induction_collide<PRECISE, S::COMP>(p, q, ql, og, rho_inv, mxh + mxl, myh + myl, mzh + mzl, Fx, Fy, Fz,
+                                                FLpx, FLpy, FLpz, mac);
             Fx += mac.FLx;
             Fy += mac.FLy;
             Fz += mac.FLz;
@@ -592,14 +634,14 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         if (MODE == MODE_STEP_RESID) {
             if (b.have_snap) {
                 const float dx = ux - b.usnap[n], dy = uy - b.usnap[N + n], dz = uz - b.usnap[2 * N + n];
-                acc[0] = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+                acc[0] = dx * dx + dy * dy + dz * dz;
             }
-            acc[1] = (double)ux * ux + (double)uy * uy + (double)uz * uz;
-            acc[2] = (double)rho;
-            acc[3] = (double)jx;
-            acc[4] = (double)jy;
-            acc[5] = (double)jz;
-            acc[6] = isfinite(ux + uy + uz) ? 0.0 : 1.0;
+            acc[1] = ux * ux + uy * uy + uz * uz;
+            acc[2] = drho;                 // the mass is rho0 * (fluid nodes) + sum drho
+            acc[3] = jx;
+            acc[4] = jy;
+            acc[5] = jz;
+            acc[6] = isfinite(ux + uy + uz) ? 0.f : 1.f;
             b.usnap[n] = ux;
             b.usnap[N + n] = uy;
             b.usnap[2 * N + n] = uz;
@@ -616,15 +658,16 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            const double v = warp_sum(acc[k]);
-            if (lane == 0) sh[warp][k] = v;
+            const float v = warp_sum(acc[k]);
+            if (lane == 0) sh[warp][k] = (double)v;
         }
         __syncthreads();
         if (threadIdx.x < 7) {
             double s = 0.0;
 #pragma unroll
             for (int w = 0; w < STEP_THREADS / 32; ++w) s += sh[w][threadIdx.x];
-            b.partials[(size_t)blockIdx.x * PARTIAL_STRIDE + threadIdx.x] = s;
+            // structure of arrays: partials[k][block] (coalesced in the finalize)
+            b.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
         }
     }
 }
