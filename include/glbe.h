@@ -143,6 +143,11 @@ glbe_status glbe_step_n(glbe_ctx* ctx, long n);
  * GLBE_ERR_DIVERGED if it saw a non-finite velocity. */
 glbe_status glbe_residual(glbe_ctx* ctx, glbe_residual_info* out);
 
+/* Copies the most recent residual evaluations (oldest first) into out[0..cap),
+ * at most the last 4096 kept on the device; *n = number copied.
+ * Synchronises the stream. */
+glbe_status glbe_history(glbe_ctx* ctx, glbe_residual_info* out, long cap, long* n);
+
 /* Time-marches until r(t) <= tol (t a multiple of 10) or max_steps steps have
  * been taken, replaying a CUDA graph of 10-step chunks.  *steps_out = time
  * level t of the converged residual (or the level reached), *r_out = r(t).

