@@ -20,7 +20,9 @@ namespace {
 
 thread_local std::string g_last_error;
 
-glbe_status fail(glbe_status s, const char* fmt, ...)
+}  // namespace
+
+glbe_status glbe::fail(glbe_status s, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -30,6 +32,8 @@ glbe_status fail(glbe_status s, const char* fmt, ...)
     g_last_error = buf;
     return s;
 }
+
+namespace {
 
 glbe_status cuda_fail(cudaError_t e, const char* what)
 {
@@ -82,7 +86,9 @@ Layout make_layout(const glbe_params* p)
     return L;
 }
 
-glbe_status validate(const glbe_params* p)
+}  // namespace
+
+glbe_status glbe::validate_params(const glbe_params* p)
 {
     if (!p) return fail(GLBE_ERR_ARG, "params is NULL");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GLBE_ERR_ARG, "grid sizes must be >= 1");
@@ -115,7 +121,7 @@ glbe_status validate(const glbe_params* p)
     return GLBE_OK;
 }
 
-StepParams make_step_params(const glbe_params* p)
+StepParams glbe::make_step_params(const glbe_params* p)
 {
     StepParams s{};
     s.nx = p->nx;
@@ -153,6 +159,8 @@ StepParams make_step_params(const glbe_params* p)
     s.inv_scale = (float)(1.0 / scale);
     return s;
 }
+
+namespace {
 
 constexpr int FIN_THREADS = 1024;
 
@@ -349,7 +357,7 @@ void glbe_params_default(glbe_params* p)
 glbe_status glbe_workspace_bytes(const glbe_params* p, size_t* bytes)
 {
     if (!bytes) return fail(GLBE_ERR_ARG, "bytes is NULL");
-    glbe_status s = validate(p);
+    glbe_status s = validate_params(p);
     if (s != GLBE_OK) return s;
     *bytes = make_layout(p).total;
     return GLBE_OK;
@@ -359,7 +367,7 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
 {
     if (!out) return fail(GLBE_ERR_ARG, "out is NULL");
     *out = nullptr;
-    glbe_status s = validate(p);
+    glbe_status s = validate_params(p);
     if (s != GLBE_OK) return s;
     if (!d_workspace) return fail(GLBE_ERR_ARG, "workspace is NULL");
     if ((reinterpret_cast<uintptr_t>(d_workspace) % ALIGN) != 0)

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "glbe.h"
+
 namespace glbe {
 
 // Unsigned division by a run-time constant d >= 1 for dividends n < 2^31:
@@ -96,5 +98,10 @@ constexpr int RECORD_STRIDE = 16;
 cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mass0, long long* t_dev,
                             double* record, double* hist, unsigned long long* hist_count, unsigned hist_cap,
                             int* stop, const double* tol, cudaStream_t st);
+
+// Host helpers shared by the C-ABI translation units (glbe_api.cu).
+glbe_status fail(glbe_status s, const char* fmt, ...);       // sets the thread-local message
+glbe_status validate_params(const glbe_params* p);
+StepParams make_step_params(const glbe_params* p);
 
 }  // namespace glbe
