@@ -184,6 +184,37 @@ const char* glbe_last_error(void);
 /* Frees the host-side context (not the workspace). NULL is ignored. */
 void glbe_destroy(glbe_ctx* ctx);
 
+/* Allocation-free time step (the paper has no counterpart; this is a service
+ * of the library).  For callers that cannot call cudaMalloc -- e.g. code whose
+ * device memory is owned by another allocator (a framework's pool or a fixed
+ * arena) and that may not allocate itself -- and so cannot provide the
+ * workspace of glbe_init.  It performs one fused D3Q19 time step with the
+ * residual evaluation on buffers the caller already holds:
+ *   p          parameters as for glbe_init (induction must be 0; p->stream is
+ *              used and synchronised)
+ *   d_src      populations entering the step, d_dst populations leaving it:
+ *              the library's own buffer layout, i.e. the deviations in the
+ *              storage type, [19][N] (F32C: 19N FP32 high parts followed by
+ *              19N FP16 low parts); all-zero bytes are the rest state.  The
+ *              next step takes d_dst as its d_src.
+ *   d_force    the force field ([force_field][N] FP32) or NULL if force_field = 0
+ *   d_u        [3][N] FP32: on entry u of the previous evaluation (read only if
+ *              have_prev), on exit u of the level t being collided
+ *   t          time level being collided (only recorded in *out)
+ *   out        host: the residual sums against d_u's entry values
+ *              (out->t = -1 when have_prev = 0)
+ * Its scratch (per-block partial sums and one record, about 1 MiB) is a
+ * file-scope static array in the library's device memory, held by every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks up that array's device address; make this first call before any
+ * stream capture.  Every call shares the array, so calls that overlap on the
+ * GPU (other threads or streams) race and must be serialised by the caller.
+ * Grids of more than 4,194,304 nodes (16384 blocks of 256) are rejected with
+ * GLBE_ERR_ARG.  No call to cudaMalloc, cudaFree or any allocating routine is
+ * made. */
+glbe_status glbe_step_residual_noalloc(const glbe_params* p, const void* d_src, void* d_dst, const float* d_force,
+                                       float* d_u, int have_prev, long t, glbe_residual_info* out);
+
 /* ABI version of the loaded library (GLBE_ABI_VERSION). */
 int glbe_abi_version(void);
 

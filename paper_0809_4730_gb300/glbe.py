@@ -69,6 +69,8 @@ _SIGNATURES = {
     "glbe_destroy": (None, [C.c_void_p]),
     "glbe_abi_version": (C.c_int, []),
     "glbe_struct_sizes": (None, [_P(C.c_size_t), _P(C.c_size_t)]),
+    "glbe_step_residual_noalloc": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_int, C.c_long, _P(glbe_residual_info)]),
 }
 
 _lib = None
@@ -193,6 +195,16 @@ def glbe_time(ctx) -> int:
 
 def glbe_sync(ctx):
     _check(load().glbe_sync(ctx), "glbe_sync")
+
+
+def glbe_step_residual_noalloc(p: glbe_params, d_src, d_dst, d_force, d_u, have_prev: bool, t: int):
+    """One fused time step with the residual on caller-held buffers; no device
+    memory is allocated (see include/glbe.h).  Returns glbe_residual_info."""
+    info = glbe_residual_info()
+    _check(load().glbe_step_residual_noalloc(C.byref(p), _ptr(d_src), _ptr(d_dst), _ptr(d_force), _ptr(d_u),
+                                             int(bool(have_prev)), int(t), C.byref(info)),
+           "glbe_step_residual_noalloc")
+    return info
 
 
 def glbe_destroy(ctx):
