@@ -164,13 +164,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def duct_solver(storage: str, device="cuda"):
+def duct_solver(storage: str, device="cuda", variant: int = 0):
     import torch
     from paper_0809_4730_gb300.glbe import Solver
     from paper_0809_4730_gb300.inputs import duct_force_x
     d = DUCT
     G = Solver(d["nx"], d["ny"], d["nz"], wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=d["gamma"], nu=d["nu"],
-               force_field=1, storage=storage, device=device)
+               force_field=1, storage=storage, device=device, variant=variant)
     Fx = duct_force_x(d["nx"], d["ny"], d["nz"], d["F0"])[0].reshape(1, -1)
     F_host = torch.tensor(Fx, dtype=torch.float32).pin_memory()
     G.set_force(F_host.to(device))
@@ -178,7 +178,7 @@ def duct_solver(storage: str, device="cuda"):
     return G, F_host, fluid
 
 
-def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda"):
+def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda", storage="f32", variant=0):
     """Hartmann duct of n^3 nodes: x periodic, walls on y and z, B0 along y,
     nu = eta = 0.01, chi = 0.01 (Pr_m = 0.01), F_x = 1e-6, FP32."""
     from paper_0809_4730_gb300.glbe import Solver
@@ -186,7 +186,8 @@ def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda"):
     L = (n - 2) / 2
     B0 = Ha * math.sqrt(nu * eta) / L
     G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
-               gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0), device=device)
+               gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0), device=device, storage=storage,
+               variant=variant)
     return G, n * (n - 2) * (n - 2)
 
 
@@ -316,34 +317,36 @@ def run_glbe(args, rank, ws):
 def variants(args, hbm_peak, stream):
     import torch
     out = {}
-    for st in ("f32", "f16", "bf16"):
-        if st == args.storage:
+    for st, variant in (("f32", 0), ("f16", 0), ("bf16", 0), ("bf16", 1), ("f32", 1)):
+        if st == args.storage and variant == 0:
             continue
-        G, _, fluid = duct_solver(st)
+        G, _, fluid = duct_solver(st, variant=variant)
         G.step(30)
         G.sync()
         total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
         kern_ms = plain_ms / nplain
         bpn = bytes_per_node(st, False, 1)
-        out[f"duct_{st}"] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1),
+        out[f"duct_{st}" + ("_one_node_per_thread" if variant == 1 else "")] = {
+                             "mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1),
                              "kernel_ms": round(kern_ms, 5), "bytes_per_node": bpn,
                              "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
         G.close()
         del G
         torch.cuda.empty_cache()
-    # fused D3Q19 + D3Q7 on the 128^3 Hartmann duct (FP32)
-    G, fluid = hartmann_duct_solver()
-    G.step(30)
-    G.sync()
-    total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
-    kern_ms = plain_ms / nplain
-    bpn = bytes_per_node("f32", True, 0)
-    out["mhd_duct_128_f32"] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
-                               "bytes_per_node": bpn,
-                               "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
-    G.close()
-    del G
-    torch.cuda.empty_cache()
+    # fused D3Q19 + D3Q7 on the 128^3 Hartmann duct (FP32 and BF16 storage)
+    for st, variant in (("f32", 0), ("f32", 1), ("bf16", 0)):
+        G, fluid = hartmann_duct_solver(storage=st, variant=variant)
+        G.step(30)
+        G.sync()
+        total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
+        kern_ms = plain_ms / nplain
+        bpn = bytes_per_node(st, True, 0)
+        key = f"mhd_duct_128_{st}" + ("_one_node_per_thread" if variant == 1 else "")
+        out[key] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
+                    "bytes_per_node": bpn, "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        G.close()
+        del G
+        torch.cuda.empty_cache()
     out["time_to_1e-8_hartmann_64x64x8"] = time_to_solution()
     return out
 
@@ -357,33 +360,36 @@ def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
 
 
 def time_to_solution():
-    """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Ha = 10,
-    Pr_m = 0.01, nu = eta = 0.01) at gamma = gamma_m = 0.1 and 1, same GPU,
-    FP32 arithmetic with compensated (F32C) storage, with the error of the
-    converged u against the analytic profile."""
+    """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Pr_m = 0.01,
+    nu = eta = 0.01, Ha = 5, 10, 20) at gamma = gamma_m = 0.1 and 1, same
+    GPU, FP32 arithmetic with compensated (F32C) storage, with the error of
+    the converged u against the analytic profile."""
     import torch
     from paper_0809_4730_gb300.glbe import Solver
     res = {}
-    Ha, nu, eta, chi = 10.0, 0.01, 0.01, 0.01
-    B0 = Ha * math.sqrt(nu * eta) / 31.0
-    ua = hartmann_analytic(64, Ha)
-    for gamma in (0.1, 1.0):
-        G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
-                   gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0), storage="f32c")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, steps, r = G.solve(1e-8, 3_000_000)
-        t1 = time.perf_counter()
-        _, u, _ = G.fields()
-        G.sync()
-        ux = u[0].reshape(8, 64, 64)[0, :, 0].double().cpu().tolist()
-        err = max(abs(ux[y] - ua[y]) for y in range(1, 63)) / max(ua)
-        res[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r, "wall_s": round(t1 - t0, 4),
-                                 "err_vs_analytic": err}
-        G.close()
-    a, b = res["gamma_0.1"], res["gamma_1.0"]
-    res["speedup_wall"] = round(b["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
-    res["speedup_steps"] = round(b["steps"] / max(1, a["steps"]), 2)
+    nu, eta, chi = 0.01, 0.01, 0.01
+    for Ha in (5.0, 10.0, 20.0):
+        B0 = Ha * math.sqrt(nu * eta) / 31.0
+        ua = hartmann_analytic(64, Ha)
+        r_ha = {}
+        for gamma in (0.1, 1.0):
+            G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
+                       induction=1, gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0), storage="f32c")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, steps, r = G.solve(1e-8, 3_000_000)
+            t1 = time.perf_counter()
+            _, u, _ = G.fields()
+            G.sync()
+            ux = u[0].reshape(8, 64, 64)[0, :, 0].double().cpu().tolist()
+            err = max(abs(ux[y] - ua[y]) for y in range(1, 63)) / max(ua)
+            r_ha[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r, "wall_s": round(t1 - t0, 4),
+                                      "err_vs_analytic": err}
+            G.close()
+        a, b = r_ha["gamma_0.1"], r_ha["gamma_1.0"]
+        r_ha["speedup_wall"] = round(b["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
+        r_ha["speedup_steps"] = round(b["steps"] / max(1, a["steps"]), 2)
+        res[f"Ha_{int(Ha)}"] = r_ha
     return res
 
 

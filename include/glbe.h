@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define GLBE_ABI_VERSION 1
+#define GLBE_ABI_VERSION 2
 
 typedef struct glbe_ctx glbe_ctx;
 
@@ -95,9 +95,12 @@ typedef struct {
     double mu;                /* magnetic permeability                           */
     double B0[3];             /* applied field: initial state and wall value      */
     int storage;              /* glbe_storage                                    */
-    double storage_scale;     /* multiplier on stored deviations; 0 = default (1 for F32/BF16, 4096 for F16;
-                                 ignored for F32C) */
+    double storage_scale;     /* F16 only: multiplier on the stored deviations (0 = default 4096);
+                                 ignored for the other storage forms */
     void* stream;             /* cudaStream_t owned by the caller                */
+    int variant;              /* kernel form: 0 = automatic; 1 = one node per thread; 2 = two x-adjacent
+                                 nodes per thread with packed FP32x2 arithmetic (needs an even nx and
+                                 no walls along x, else the one-node form is used) */
 } glbe_params;
 
 /* Latest residual evaluation (time level t, a multiple of 10). */
@@ -209,8 +212,8 @@ void glbe_destroy(glbe_ctx* ctx);
  * looks up that array's device address; make this first call before any
  * stream capture.  Every call shares the array, so calls that overlap on the
  * GPU (other threads or streams) race and must be serialised by the caller.
- * Grids of more than 4,194,304 nodes (16384 blocks of 256) are rejected with
- * GLBE_ERR_ARG.  No call to cudaMalloc, cudaFree or any allocating routine is
+ * Grids of more than 4,194,304 nodes (16384 blocks of 256) and buffers that
+ * are not 16-byte aligned are rejected with GLBE_ERR_ARG.  No call to cudaMalloc, cudaFree or any allocating routine is
  * made. */
 glbe_status glbe_step_residual_noalloc(const glbe_params* p, const void* d_src, void* d_dst, const float* d_force,
                                        float* d_u, int have_prev, long t, glbe_residual_info* out);

@@ -116,6 +116,7 @@ glbe_status glbe::validate_params(const glbe_params* p)
     }
     if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16 && p->storage != GLBE_F32C)
         return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16 or GLBE_F32C");
+    if (p->variant < 0 || p->variant > 2) return fail(GLBE_ERR_ARG, "variant must be 0, 1 or 2");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
     return GLBE_OK;
@@ -153,10 +154,12 @@ StepParams glbe::make_step_params(const glbe_params* p)
         s.J_coef = (float)(-1.0 / (p->mu * p->chi * tau_m * THETA_M));
     }
     double scale = p->storage_scale;
-    if (p->storage == GLBE_F32C) scale = 1.0;   // the compensated form stores unscaled values
-    else if (scale == 0.0) scale = p->storage == GLBE_F16 ? 4096.0 : 1.0;
+    if (p->storage != GLBE_F16) scale = 1.0;   // only FP16 stores scaled deviations
+    else if (scale == 0.0) scale = 4096.0;
     s.scale = (float)scale;
     s.inv_scale = (float)(1.0 / scale);
+    s.variant = p->variant;
+    s.storage = p->storage;
     return s;
 }
 
@@ -255,13 +258,14 @@ struct glbe_ctx {
 
 namespace {
 
-cudaError_t launch_step_any(glbe_ctx* c, int mode, const StepBuffers& b, const FieldOut& fo, cudaStream_t st)
+cudaError_t launch_step_any(glbe_ctx* c, int mode, const StepBuffers& b, const FieldOut& fo, cudaStream_t st,
+                            unsigned* nblocks)
 {
     switch (c->prm.storage) {
-    case GLBE_F32: return launch_step_t<ST_F32>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
-    case GLBE_BF16: return launch_step_t<ST_BF16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
-    case GLBE_F16: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
-    default: return launch_step_t<ST_F32C>(c->prm.induction, mode, c->sp, b, fo, c->grid, st);
+    case GLBE_F32: return launch_step_t<ST_F32>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
+    case GLBE_BF16: return launch_step_t<ST_BF16>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
+    case GLBE_F16: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
+    default: return launch_step_t<ST_F32C>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
     }
 }
 
@@ -290,9 +294,10 @@ glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
     const FieldOut fo{nullptr, nullptr, nullptr};
     if (c->t % 10 == 0) {
         b.have_snap = (c->t_snap >= 0 && c->t_snap == c->t - 10) ? 1 : 0;
-        GLBE_CUDA(launch_step_any(c, MODE_STEP_RESID, b, fo, st), "step kernel (residual)");
+        unsigned nb = 0;
+        GLBE_CUDA(launch_step_any(c, MODE_STEP_RESID, b, fo, st, &nb), "step kernel (residual)");
         if (b.have_snap) {
-            GLBE_CUDA(launch_finalize(c->partials, c->grid, c->mass0, c->t_dev, c->record, c->hist, c->hist_count,
+            GLBE_CUDA(launch_finalize(c->partials, nb, c->mass0, c->t_dev, c->record, c->hist, c->hist_count,
                                       HIST_CAP, c->stop_dev, c->tol_dev, st),
                       "residual finalize");
         } else {
@@ -302,7 +307,7 @@ glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
         }
         c->t_snap = c->t;
     } else {
-        GLBE_CUDA(launch_step_any(c, MODE_STEP, b, fo, st), "step kernel");
+        GLBE_CUDA(launch_step_any(c, MODE_STEP, b, fo, st, nullptr), "step kernel");
     }
     c->t += 1;
     return GLBE_OK;
@@ -617,7 +622,7 @@ glbe_status glbe_fields(glbe_ctx* c, float* d_rho, float* d_u, float* d_B)
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     StepBuffers b = buffers_for(c, c->t);
     const FieldOut fo{d_rho, d_u, c->prm.induction ? d_B : nullptr};
-    GLBE_CUDA(launch_step_any(c, MODE_FIELDS, b, fo, c->stream), "fields kernel");
+    GLBE_CUDA(launch_step_any(c, MODE_FIELDS, b, fo, c->stream, nullptr), "fields kernel");
     return GLBE_OK;
 }
 

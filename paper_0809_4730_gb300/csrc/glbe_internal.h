@@ -47,6 +47,8 @@ struct StepParams {
     float bwall_dev[3];   // B_wall - B0 (0: insulating walls at the applied field)
     // storage of deviations
     float scale, inv_scale;
+    int variant;          // 0 automatic, 1 one node per thread, 2 two nodes per thread
+    int storage;          // Storage of the buffers (for the automatic choice)
 };
 
 // Buffers of one launch.  Populations are deviations in the storage type,
@@ -67,7 +69,8 @@ struct StepBuffers {
 enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };
 enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
 
-constexpr int STEP_THREADS = 256;
+constexpr int STEP_THREADS = 256;   // scalar kernel: one node per thread
+constexpr int PAIR_THREADS = 128;   // paired kernel: two nodes per thread (the same 256 nodes per block)
 constexpr int PARTIAL_STRIDE = 8;   // per block: num, den, sum drho, Mx, My, Mz, nonfinite, pad; stored [k][block]
 
 // Outputs of MODE_FIELDS.
@@ -78,9 +81,12 @@ struct FieldOut {
 };
 
 // Launchers, explicitly instantiated per storage type in glbe_step_<storage>.cu.
+// Launches the fused step over the whole grid -- the paired kernel on
+// x-periodic grids with an even nx (except for MODE_FIELDS), else the scalar
+// one -- and reports the number of blocks (= residual partials) in *nblocks.
 template <int ST>
 cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuffers& b, const FieldOut& fo,
-                          unsigned grid, cudaStream_t st);
+                          cudaStream_t st, unsigned* nblocks);
 template <int ST>
 cudaError_t launch_get_state_t(bool mhd, const StepParams& p, const void* fsrc, const void* gsrc, const float* FL,
                                float* df, float* dg, float* dFL, cudaStream_t st);

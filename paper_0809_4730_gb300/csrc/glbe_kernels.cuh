@@ -2,13 +2,20 @@
 // with forcing) and the preconditioned D3Q7 vector kinetic equation for the
 // magnetic induction, arXiv:0809.4730 Secs. 2-4 and App. A.
 //
-// One thread updates one node (pull scheme): it gathers the post-collision
-// populations of the previous step from its upstream neighbours (half-way
+// Pull scheme: a thread gathers the post-collision populations of the
+// previous step from the upstream neighbours of its node (half-way
 // bounce-back for f, anti-bounce-back for g where the upstream node is solid),
 // forms the macroscopic fields, collides in moment space and writes the new
-// post-collision populations to its own slot of the other buffer.  Buffers
-// hold deviations from the rest state (df = f - w rho0, dg = g - W B0) so that
-// FP32, BF16 and FP16 storage keep the small part that changes.
+// post-collision populations into its own slots of the other buffer.  Buffers
+// hold deviations from the rest state (df = f - w rho0, dg = g - W B0).
+//
+// Two kernels share one statement of the arithmetic, written over a value type
+// V: the scalar kernel (V = float, one node per thread, any geometry) and the
+// paired kernel (V = F2, two x-adjacent nodes per thread, x periodic with an
+// even nx).  F2 maps onto Blackwell's packed FP32x2 add/mul/fma, so the paired
+// kernel issues one arithmetic instruction for two nodes; its populations move
+// as aligned 2-element vectors, and the two x-shifted sources per thread come
+// from one aligned pair plus a lane shuffle.
 //
 // The moment transform is the integer Gram-Schmidt basis of App. A (rows
 // rho, e, e^2, j, q, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m) applied
@@ -25,65 +32,138 @@
 
 namespace glbe {
 
-// Storage of the population deviations.  COMP marks the compensated form:
-// an FP32 high part plus an FP16 low part holding the rounding remainder
-// (scaled by 2^36), updated with an exact two-sum so that corrections far
-// below one FP32 ulp of the stored deviation accumulate instead of being
-// dropped.  The low parts follow the high parts in the same buffer.
+// ---------------------------------------------------------------------------
+// Value types: float, and F2 = two lanes of packed FP32 (sm_100+ FFMA2/FADD2/
+// FMUL2).  Every operation rounds each lane to nearest exactly as the scalar
+// one does.
+// ---------------------------------------------------------------------------
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float c) : v(make_float2(c, c)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(float2 w) : v(w) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { a = a + b; return a; }
+
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+// additions/subtractions that must not be contracted or reassociated
+__device__ __forceinline__ float vadd_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ F2 vadd_rn(F2 a, F2 b) { return a + b; }
+__device__ __forceinline__ F2 vsub_rn(F2 a, F2 b) { return a - b; }
+__device__ __forceinline__ float vrcp(float a) { return 1.0f / a; }
+__device__ __forceinline__ F2 vrcp(F2 a) { return F2(1.0f / a.v.x, 1.0f / a.v.y); }
+__device__ __forceinline__ float lane_sum(float a) { return a; }
+__device__ __forceinline__ float lane_sum(F2 a) { return a.v.x + a.v.y; }
+__device__ __forceinline__ float vnonfinite(float a) { return isfinite(a) ? 0.f : 1.f; }
+__device__ __forceinline__ float vnonfinite(F2 a) { return (isfinite(a.v.x) ? 0.f : 1.f) + (isfinite(a.v.y) ? 0.f : 1.f); }
+
+// fl(a + b + c) for |c| small: the exact two-sum of a and b, its remainder
+// plus c, rounded once.
+template <class V>
+__device__ __forceinline__ V two_sum_round(V a, V b, V c)
+{
+    const V s = vadd_rn(a, b);
+    const V bp = vsub_rn(s, a);
+    const V e = vadd_rn(vsub_rn(a, vsub_rn(s, bp)), vsub_rn(b, bp));
+    return vadd_rn(s, vadd_rn(e, c));
+}
+
+// h + o + l as a new (high, low) pair: exact two-sum of h and o, the
+// remainder plus the old low part renormalised into the new low part.
+template <class V>
+__device__ __forceinline__ void comp_add(V h, V l, V o, V& nh, V& nl)
+{
+    const V s = vadd_rn(h, o);
+    const V bp = vsub_rn(s, h);
+    const V ap = vsub_rn(s, bp);
+    V e = vadd_rn(vsub_rn(h, ap), vsub_rn(o, bp));
+    e = vadd_rn(e, l);
+    nh = vadd_rn(s, e);
+    nl = vsub_rn(e, vsub_rn(nh, s));
+}
+
+// ---------------------------------------------------------------------------
+// Storage of the population deviations.  Only FP16 is stored scaled (by
+// p.scale).  COMP marks the compensated form: an FP32 high part plus an FP16
+// low part holding the rounding remainder (scaled by 2^36), updated with an
+// exact two-sum; the low parts follow the high parts in the same buffer.
+// ---------------------------------------------------------------------------
 constexpr float LO_SCALE = 68719476736.0f;        // 2^36
 constexpr float LO_INV = 1.4551915228366852e-11f; // 2^-36
 
 template <int ST> struct Store;
 template <> struct Store<ST_F32> {
     using T = float;
-    static constexpr bool COMP = false;
-    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ float cv(float v) { return v; }
+    static constexpr bool COMP = false, SCALED = false;
+    static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ T cv(float v) { return v; }
+    static __device__ __forceinline__ F2 ld2(const T* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
+    static __device__ __forceinline__ void st2(T* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
-    static constexpr bool COMP = false;
+    static constexpr bool COMP = false, SCALED = false;
     static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ F2 ld2(const T* p)
+    {
+        return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p))));
+    }
+    static __device__ __forceinline__ void st2(T* p, F2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+    }
 };
 template <> struct Store<ST_F16> {
     using T = __half;
-    static constexpr bool COMP = false;
+    static constexpr bool COMP = false, SCALED = true;
     static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ F2 ld2(const T* p)
+    {
+        return F2(__half22float2(__ldg(reinterpret_cast<const __half2*>(p))));
+    }
+    static __device__ __forceinline__ void st2(T* p, F2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
 };
 template <> struct Store<ST_F32C> {
     using T = float;
-    static constexpr bool COMP = true;
-    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ float cv(float v) { return v; }
+    static constexpr bool COMP = true, SCALED = false;
+    static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ T cv(float v) { return v; }
+    static __device__ __forceinline__ F2 ld2(const T* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
+    static __device__ __forceinline__ void st2(T* p, F2 v) { *reinterpret_cast<float2*>(p) = v.v; }
     static __device__ __forceinline__ float ld_lo(const __half* p) { return __half2float(__ldg(p)) * LO_INV; }
     static __device__ __forceinline__ __half cv_lo(float v) { return __float2half_rn(v * LO_SCALE); }
+    static __device__ __forceinline__ F2 ld2_lo(const __half* p)
+    {
+        const float2 w = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        return F2(w.x * LO_INV, w.y * LO_INV);
+    }
+    static __device__ __forceinline__ void st2_lo(__half* p, F2 v)
+    {
+        *reinterpret_cast<__half2*>(p) = __float22half2_rn(make_float2(v.v.x * LO_SCALE, v.v.y * LO_SCALE));
+    }
 };
 
-// fl(a + b + c) for |c| small: the exact two-sum of a and b, its remainder
-// plus c, rounded once.
-__device__ __forceinline__ float two_sum_round(float a, float b, float c)
-{
-    const float s = __fadd_rn(a, b);
-    const float bp = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
-    return __fadd_rn(s, __fadd_rn(e, c));
-}
+template <int ST>
+__device__ __forceinline__ float unscale(const StepParams& p, float v) { return Store<ST>::SCALED ? v * p.inv_scale : v; }
+template <int ST>
+__device__ __forceinline__ F2 unscale(const StepParams& p, F2 v) { return Store<ST>::SCALED ? v * F2(p.inv_scale) : v; }
+template <int ST>
+__device__ __forceinline__ float toscale(const StepParams& p, float v) { return Store<ST>::SCALED ? v * p.scale : v; }
+template <int ST>
+__device__ __forceinline__ F2 toscale(const StepParams& p, F2 v) { return Store<ST>::SCALED ? v * F2(p.scale) : v; }
 
-// h + o + l as a new (high, low) pair: exact two-sum of h and o, the
-// remainder plus the old low part renormalised into the new low part.
-__device__ __forceinline__ void comp_add(float h, float l, float o, float& nh, float& nl)
-{
-    const float s = __fadd_rn(h, o);
-    const float bp = __fsub_rn(s, h);
-    const float ap = __fsub_rn(s, bp);
-    float e = __fadd_rn(__fsub_rn(h, ap), __fsub_rn(o, bp));
-    e = __fadd_rn(e, l);
-    nh = __fadd_rn(s, e);
-    nl = __fsub_rn(e, __fsub_rn(nh, s));
-}
-
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f)
 {
     return (__umulhi(n, f.m) + n) >> f.s;
@@ -104,6 +184,26 @@ struct Geo {
     uint32_t r00, rm0, rp0, r0m, r0p, rmm, rpm, rmp, rpp;   // r<y-shift><z-shift>, m: -1, p: +1
 };
 
+__device__ __forceinline__ void row_geometry(const StepParams& p, int y, int z, Geo& g)
+{
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+    g.sym = plane_solid(ym, p.ny, p.wlo[1], p.whi[1]);
+    g.syp = plane_solid(yp, p.ny, p.wlo[1], p.whi[1]);
+    g.szm = plane_solid(zm, p.nz, p.wlo[2], p.whi[2]);
+    g.szp = plane_solid(zp, p.nz, p.wlo[2], p.whi[2]);
+    const uint32_t nx = (uint32_t)p.nx, ny = (uint32_t)p.ny;
+    g.r00 = ((uint32_t)z * ny + (uint32_t)y) * nx;
+    g.rm0 = ((uint32_t)z * ny + (uint32_t)ym) * nx;
+    g.rp0 = ((uint32_t)z * ny + (uint32_t)yp) * nx;
+    g.r0m = ((uint32_t)zm * ny + (uint32_t)y) * nx;
+    g.r0p = ((uint32_t)zp * ny + (uint32_t)y) * nx;
+    g.rmm = ((uint32_t)zm * ny + (uint32_t)ym) * nx;
+    g.rpm = ((uint32_t)zm * ny + (uint32_t)yp) * nx;
+    g.rmp = ((uint32_t)zp * ny + (uint32_t)ym) * nx;
+    g.rpp = ((uint32_t)zp * ny + (uint32_t)yp) * nx;
+}
+
 __device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
 {
     Geo g;
@@ -113,34 +213,50 @@ __device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
     g.x = (int)(n - zy * (uint32_t)p.nx);
     g.y = (int)(zy - z * (uint32_t)p.ny);
     g.z = (int)z;
-    const int ym = g.y == 0 ? p.ny - 1 : g.y - 1, yp = g.y == p.ny - 1 ? 0 : g.y + 1;
-    const int zm = g.z == 0 ? p.nz - 1 : g.z - 1, zp = g.z == p.nz - 1 ? 0 : g.z + 1;
     g.xm = g.x == 0 ? p.nx - 1 : g.x - 1;
     g.xp = g.x == p.nx - 1 ? 0 : g.x + 1;
     g.solid = plane_solid(g.x, p.nx, p.wlo[0], p.whi[0]) || plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) ||
               plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]);
     g.sxm = plane_solid(g.xm, p.nx, p.wlo[0], p.whi[0]);
     g.sxp = plane_solid(g.xp, p.nx, p.wlo[0], p.whi[0]);
-    g.sym = plane_solid(ym, p.ny, p.wlo[1], p.whi[1]);
-    g.syp = plane_solid(yp, p.ny, p.wlo[1], p.whi[1]);
-    g.szm = plane_solid(zm, p.nz, p.wlo[2], p.whi[2]);
-    g.szp = plane_solid(zp, p.nz, p.wlo[2], p.whi[2]);
-    const uint32_t nx = (uint32_t)p.nx, ny = (uint32_t)p.ny;
-    g.r00 = (z * ny + (uint32_t)g.y) * nx;
-    g.rm0 = (z * ny + (uint32_t)ym) * nx;
-    g.rp0 = (z * ny + (uint32_t)yp) * nx;
-    g.r0m = ((uint32_t)zm * ny + (uint32_t)g.y) * nx;
-    g.r0p = ((uint32_t)zp * ny + (uint32_t)g.y) * nx;
-    g.rmm = ((uint32_t)zm * ny + (uint32_t)ym) * nx;
-    g.rpm = ((uint32_t)zm * ny + (uint32_t)yp) * nx;
-    g.rmp = ((uint32_t)zp * ny + (uint32_t)ym) * nx;
-    g.rpp = ((uint32_t)zp * ny + (uint32_t)yp) * nx;
+    row_geometry(p, g.y, g.z, g);
     return g;
 }
 
-// Upstream index and solidity of the source of direction a (source = x - e_a).
-// Pull: f_a(x, t+1) = f~_a(x - e_a, t); if x - e_a is solid the link is
-// bounced: f_a(x, t+1) = f~_abar(x, t).
+// Pair geometry: nodes x0, x0 + 1 (x0 even) of one row of an x-periodic grid.
+struct GeoP {
+    Geo g;             // row data; g.x = x0, g.n = linear index of node x0
+    int xl, xr;        // x0 - 1 and x0 + 2, wrapped
+    bool left_own;     // the value at x0 - 1 is not in the left lane (warp or row start)
+    bool right_own;    // the value at x0 + 2 is not in the right lane (warp or row end)
+};
+
+__device__ __forceinline__ GeoP make_geo_pair(const StepParams& p, uint32_t n0)
+{
+    GeoP q;
+    Geo& g = q.g;
+    g.n = n0;
+    const uint32_t zy = fdiv(n0, p.div_nx);
+    const uint32_t z = fdiv(n0, p.div_nxy);
+    g.x = (int)(n0 - zy * (uint32_t)p.nx);
+    g.y = (int)(zy - z * (uint32_t)p.ny);
+    g.z = (int)z;
+    g.xm = g.xp = 0;
+    g.solid = plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) || plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]);
+    g.sxm = g.sxp = false;
+    row_geometry(p, g.y, g.z, g);
+    q.xl = g.x == 0 ? p.nx - 1 : g.x - 1;
+    q.xr = g.x + 2 == p.nx ? 0 : g.x + 2;
+    const int lane = threadIdx.x & 31;
+    q.left_own = lane == 0 || g.x == 0;
+    q.right_own = lane == 31 || g.x + 2 == p.nx;
+    return q;
+}
+
+// Upstream row and solidity of the source of direction a (source = x - e_a),
+// with the opposite direction o.  Pull: f_a(x, t+1) = f~_a(x - e_a, t); if
+// x - e_a is solid the link is bounced: f_a(x, t+1) = f~_o(x, t).
+// Scalar form: (a, o, source index, solid).
 #define GLBE_DIRS(X)                                              \
     X(1, 2, g.r00 + g.xm, g.sxm)                                  \
     X(2, 1, g.r00 + g.xp, g.sxp)                                  \
@@ -169,14 +285,46 @@ __device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
     X(5, 6, g.r0m + g.x, g.szm)            \
     X(6, 5, g.r0p + g.x, g.szp)
 
+// Pair form: (a, o, source row, solid, x-shift e_x of the direction).
+#define GLBE_PDIRS(X)                      \
+    X(1, 2, g.r00, false, 1)               \
+    X(2, 1, g.r00, false, -1)              \
+    X(3, 4, g.rm0, g.sym, 0)               \
+    X(4, 3, g.rp0, g.syp, 0)               \
+    X(5, 6, g.r0m, g.szm, 0)               \
+    X(6, 5, g.r0p, g.szp, 0)               \
+    X(7, 10, g.rm0, g.sym, 1)              \
+    X(8, 9, g.rm0, g.sym, -1)              \
+    X(9, 8, g.rp0, g.syp, 1)               \
+    X(10, 7, g.rp0, g.syp, -1)             \
+    X(11, 14, g.r0m, g.szm, 1)             \
+    X(12, 13, g.r0m, g.szm, -1)            \
+    X(13, 12, g.r0p, g.szp, 1)             \
+    X(14, 11, g.r0p, g.szp, -1)            \
+    X(15, 18, g.rmm, g.sym || g.szm, 0)    \
+    X(16, 17, g.rpm, g.syp || g.szm, 0)    \
+    X(17, 16, g.rmp, g.sym || g.szp, 0)    \
+    X(18, 15, g.rpp, g.syp || g.szp, 0)
+
+#define GLBE_PDIRS7(X)                     \
+    X(1, 2, g.r00, false, 1)               \
+    X(2, 1, g.r00, false, -1)              \
+    X(3, 4, g.rm0, g.sym, 0)               \
+    X(4, 3, g.rp0, g.syp, 0)               \
+    X(5, 6, g.r0m, g.szm, 0)               \
+    X(6, 5, g.r0p, g.szp, 0)
+
+// ---------------------------------------------------------------------------
+// Gathers
+// ---------------------------------------------------------------------------
 template <int ST>
 __device__ __forceinline__ void load_f(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
                                        const Geo& g, float (&d)[19], float (&l)[19])
 {
     const size_t N = p.N;
 #define GLBE_SRCF(a, o, src, sol) ((sol) ? (size_t)(o) * N + g.n : (size_t)(a) * N + (src))
-#define GLBE_LOADF(a, o, src, sol) d[a] = Store<ST>::ld(fs + GLBE_SRCF(a, o, src, sol)) * p.inv_scale;
-    d[0] = Store<ST>::ld(fs + g.n) * p.inv_scale;
+#define GLBE_LOADF(a, o, src, sol) d[a] = unscale<ST>(p, Store<ST>::ld(fs + GLBE_SRCF(a, o, src, sol)));
+    d[0] = unscale<ST>(p, Store<ST>::ld(fs + g.n));
     GLBE_DIRS(GLBE_LOADF)
 #undef GLBE_LOADF
     if constexpr (Store<ST>::COMP) {
@@ -202,10 +350,10 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     for (int j = 0; j < 3; ++j) {
         const typename Store<ST>::T* __restrict__ b = gs + (size_t)(j * 7) * N;
         const float wall = 0.25f * p.bwall_dev[j];   // 2 W_a (B_wall - B0), W_a = 1/8
-        q[j * 7 + 0] = Store<ST>::ld(b + g.n) * p.inv_scale;
-#define GLBE_LOADG(a, o, src, sol)                                                      \
-    q[j * 7 + a] = (sol) ? (wall - Store<ST>::ld(b + (size_t)(o) * N + g.n) * p.inv_scale) \
-                         : Store<ST>::ld(b + (size_t)(a) * N + (src)) * p.inv_scale;
+        q[j * 7 + 0] = unscale<ST>(p, Store<ST>::ld(b + g.n));
+#define GLBE_LOADG(a, o, src, sol)                                                               \
+    q[j * 7 + a] = (sol) ? (wall - unscale<ST>(p, Store<ST>::ld(b + (size_t)(o) * N + g.n)))    \
+                         : unscale<ST>(p, Store<ST>::ld(b + (size_t)(a) * N + (src)));
         GLBE_DIRS7(GLBE_LOADG)
 #undef GLBE_LOADG
         if constexpr (Store<ST>::COMP) {
@@ -220,15 +368,120 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     }
 }
 
+// One population of a pair: the two sources of direction a with x-shift ex
+// from row `row` (solid: bounce-back from the own row's opposite slot o).
+// ex = 0: one aligned pair.  ex = +1: node x0 needs x0 - 1 (the left lane's
+// pair, or an own load at a warp or row start), node x0 + 1 needs x0.
+// ex = -1: node x0 needs x0 + 1, node x0 + 1 needs x0 + 2 (the right lane's
+// pair, or an own load at a warp or row end).  Every lane executes the
+// shuffles; bounced rows never use them.
+template <class LD2, class LD1>
+__device__ __forceinline__ F2 pair_gather(const GeoP& q, size_t base_a, size_t base_o, uint32_t row, bool sol,
+                                          int ex, LD2 ld2, LD1 ld1)
+{
+    const Geo& g = q.g;
+    const F2 v = sol ? ld2(base_o + g.r00 + (uint32_t)g.x) : ld2(base_a + row + (uint32_t)g.x);
+    if (ex > 0) {
+        const float t = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+        if (sol) return v;
+        const float left = q.left_own ? ld1(base_a + row + (uint32_t)q.xl) : t;
+        return F2(left, v.v.x);
+    }
+    if (ex < 0) {
+        const float t = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+        if (sol) return v;
+        const float right = q.right_own ? ld1(base_a + row + (uint32_t)q.xr) : t;
+        return F2(v.v.y, right);
+    }
+    return v;
+}
+
+template <int ST>
+__device__ __forceinline__ void load_f_pair(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
+                                            const GeoP& q, F2 (&d)[19], F2 (&l)[19])
+{
+    using S = Store<ST>;
+    const size_t N = p.N;
+    const Geo& g = q.g;
+    auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(fs + i)); };
+    auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(fs + i)); };
+    d[0] = ld2((size_t)g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADF(a, o, row, sol, ex) d[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, ld2, ld1);
+    GLBE_PDIRS(GLBE_PLOADF)
+#undef GLBE_PLOADF
+    if constexpr (S::COMP) {
+        const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * N);
+        auto lo2 = [&](size_t i) { return S::ld2_lo(fl + i); };
+        auto lo1 = [&](size_t i) { return S::ld_lo(fl + i); };
+        l[0] = lo2((size_t)g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADL(a, o, row, sol, ex) l[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, lo2, lo1);
+        GLBE_PDIRS(GLBE_PLOADL)
+#undef GLBE_PLOADL
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ void load_g_pair(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
+                                            const GeoP& q, F2 (&v)[21], F2 (&vl)[21])
+{
+    using S = Store<ST>;
+    const size_t N = p.N;
+    const Geo& g = q.g;
+    auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(gs + i)); };
+    auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(gs + i)); };
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const size_t jb = (size_t)(j * 7) * N;
+        const F2 wall(0.25f * p.bwall_dev[j]);
+        v[j * 7] = ld2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADG(a, o, row, sol, ex)                                                              \
+    {                                                                                                \
+        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, ld2, ld1); \
+        v[j * 7 + a] = (sol) ? wall - t_ : t_;                                                       \
+    }
+        GLBE_PDIRS7(GLBE_PLOADG)
+#undef GLBE_PLOADG
+        if constexpr (S::COMP) {
+            const __half* __restrict__ gl = reinterpret_cast<const __half*>(gs + 21 * N);
+            auto lo2 = [&](size_t i) { return S::ld2_lo(gl + i); };
+            auto lo1 = [&](size_t i) { return S::ld_lo(gl + i); };
+            vl[j * 7] = lo2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADGL(a, o, row, sol, ex)                                                              \
+    {                                                                                                 \
+        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, lo2, lo1); \
+        vl[j * 7 + a] = (sol) ? -t_ : t_;                                                             \
+    }
+            GLBE_PDIRS7(GLBE_PLOADGL)
+#undef GLBE_PLOADGL
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic of one node (V = float) or one pair of nodes (V = F2)
+// ---------------------------------------------------------------------------
+
 // Grid constant of the error-free split x = xh + xl, xh = (x + C) - C: for
-// |x| <= 2^-5 the high parts are multiples of 2^-28.
+// |x| <= 2^-5 the high parts are multiples of 2^-28, so integer-weighted sums
+// of them are exact in FP32 while they stay below 2^-4, and the xl
+// (|xl| <= 2^-29) carry the rest.  Moments formed as (exact high sum -
+// equilibrium) + low sum keep the small non-equilibrium parts free of the
+// round-off of the large sums, which otherwise leaves the FP32 time march
+// wandering at r ~ 1e-7 instead of settling on its fixed point.
 constexpr float SPLIT_C = 0.046875f;   // 1.5 * 2^-5
 
-// Everything a node's collision produces besides the new populations.
+template <class V>
+__device__ __forceinline__ void split_exact(const V& x, V& xh, V& xl)
+{
+    xh = vsub_rn(vadd_rn(x, V(SPLIT_C)), V(SPLIT_C));
+    xl = vsub_rn(x, xh);
+}
+
+// Everything the induction part produces besides the new populations.
+template <class V>
 struct NodeMacro {
-    float rho, ux, uy, uz;
-    float Bx, By, Bz;
-    float FLx, FLy, FLz;
+    V Bx, By, Bz;
+    V FLx, FLy, FLz;
 };
 
 // Induction part: B, Lorentz force from the previous step's half-force
@@ -239,23 +492,21 @@ struct NodeMacro {
 // first bracket is exact and the rounding of the 7-term sum B no longer
 // biases every population's relaxation (a bias the slow magnetic diffusion
 // mode would otherwise integrate into a 3e-5 error of the steady flow).
-template <bool PRECISE, bool COMP>
-__device__ __forceinline__ void induction_collide(const StepParams& p, const float (&q)[21], const float (&qlo)[21],
-                                                  float (&og)[21], float rho_inv, float mx, float my, float mz,
-                                                  float Fx, float Fy, float Fz, float FLpx, float FLpy, float FLpz,
-                                                  NodeMacro& mac)
+template <class V, bool PRECISE, bool COMP>
+__device__ __forceinline__ void induction_collide(const StepParams& p, const V (&q)[21], const V (&qlo)[21],
+                                                  V (&og)[21], V rho_inv, V mx, V my, V mz, V Fx, V Fy, V Fz,
+                                                  V FLpx, V FLpy, V FLpz, NodeMacro<V>& mac)
 {
-    float qh[21], ql[21];
+    V qh[21], ql[21];
     if constexpr (PRECISE) {
 #pragma unroll
         for (int i = 0; i < 21; ++i) {
-            qh[i] = __fsub_rn(__fadd_rn(q[i], SPLIT_C), SPLIT_C);
-            ql[i] = __fsub_rn(q[i], qh[i]);
+            split_exact(q[i], qh[i], ql[i]);
             if constexpr (COMP) ql[i] += qlo[i];   // low part of the compensated storage
         }
     }
     // B_j = B0_j + sum_a dg_ja (sum_a W_a = 1), Eq. magneticinduction
-    float bxh, byh, bzh, bxl = 0.f, byl = 0.f, bzl = 0.f;
+    V bxh, byh, bzh, bxl(0.f), byl(0.f), bzl(0.f);
     if constexpr (PRECISE) {
         bxh = qh[0] + qh[1] + qh[2] + qh[3] + qh[4] + qh[5] + qh[6];
         byh = qh[7] + qh[8] + qh[9] + qh[10] + qh[11] + qh[12] + qh[13];
@@ -268,89 +519,99 @@ __device__ __forceinline__ void induction_collide(const StepParams& p, const flo
         byh = q[7] + q[8] + q[9] + q[10] + q[11] + q[12] + q[13];
         bzh = q[14] + q[15] + q[16] + q[17] + q[18] + q[19] + q[20];
     }
-    const float bx = bxh + bxl, by = byh + byl, bz = bzh + bzl;
-    const float Bx = p.B0[0] + bx, By = p.B0[1] + by, Bz = p.B0[2] + bz;
+    const V bx = PRECISE ? bxh + bxl : bxh, by = PRECISE ? byh + byl : byh, bz = PRECISE ? bzh + bzl : bzh;
+    const V Bx = V(p.B0[0]) + bx, By = V(p.B0[1]) + by, Bz = V(p.B0[2]) + bz;
     // velocity with the previous step's Lorentz force in the half-force
-    const float hg = 0.5f * p.inv_gamma;
-    const float u0x = (mx + hg * (Fx + FLpx)) * rho_inv;
-    const float u0y = (my + hg * (Fy + FLpy)) * rho_inv;
-    const float u0z = (mz + hg * (Fz + FLpz)) * rho_inv;
+    const V hg(0.5f * p.inv_gamma);
+    const V u0x = (mx + hg * (Fx + FLpx)) * rho_inv;
+    const V u0y = (my + hg * (Fy + FLpy)) * rho_inv;
+    const V u0z = (mz + hg * (Fz + FLpz)) * rho_inv;
     // equilibrium first moment Lambda^eq_kj = (chi/gamma_m)(u_k B_j - B_k u_j)
-    const float c = p.conv_coef;
-    const float Lxy = c * (u0x * By - Bx * u0y);
-    const float Lxz = c * (u0x * Bz - Bx * u0z);
-    const float Lyz = c * (u0y * Bz - By * u0z);
+    const V c(p.conv_coef);
+    const V Lxy = c * (u0x * By - Bx * u0y);
+    const V Lxz = c * (u0x * Bz - Bx * u0z);
+    const V Lyz = c * (u0y * Bz - By * u0z);
     // first moments of g: M_kj = g_{+k,j} - g_{-k,j}; non-equilibrium parts
-    const float Nxy = (q[7 + 1] - q[7 + 2]) - Lxy;     // k = x, j = y
-    const float Nyx = (q[0 + 3] - q[0 + 4]) + Lxy;     // k = y, j = x (Lambda^eq_yx = -Lxy)
-    const float Nxz = (q[14 + 1] - q[14 + 2]) - Lxz;
-    const float Nzx = (q[0 + 5] - q[0 + 6]) + Lxz;
-    const float Nyz = (q[14 + 3] - q[14 + 4]) - Lyz;
-    const float Nzy = (q[7 + 5] - q[7 + 6]) + Lyz;
+    const V Nxy = (q[7 + 1] - q[7 + 2]) - Lxy;     // k = x, j = y
+    const V Nyx = (q[0 + 3] - q[0 + 4]) + Lxy;     // k = y, j = x (Lambda^eq_yx = -Lxy)
+    const V Nxz = (q[14 + 1] - q[14 + 2]) - Lxz;
+    const V Nzx = (q[0 + 5] - q[0 + 6]) + Lxz;
+    const V Nyz = (q[14 + 3] - q[14 + 4]) - Lyz;
+    const V Nzy = (q[7 + 5] - q[7 + 6]) + Lyz;
     // J_i = -(1/(mu chi tau_m theta_m)) eps_ijk Lneq_jk = (1/(mu chi)) (curl B)_i
-    const float Jx = p.J_coef * (Nyz - Nzy);
-    const float Jy = p.J_coef * (Nzx - Nxz);
-    const float Jz = p.J_coef * (Nxy - Nyx);
+    const V Jc(p.J_coef);
+    const V Jx = Jc * (Nyz - Nzy);
+    const V Jy = Jc * (Nzx - Nxz);
+    const V Jz = Jc * (Nxy - Nyx);
     mac.FLx = Jy * Bz - Jz * By;
     mac.FLy = Jz * Bx - Jx * Bz;
     mac.FLz = Jx * By - Jy * Bx;
-    mac.Bx = Bx; mac.By = By; mac.Bz = Bz;
+    mac.Bx = Bx;
+    mac.By = By;
+    mac.Bz = Bz;
     // g^eq,* deviations: W_0 b_j (rest), W_1 (b_j +- Lambda^eq_kj / theta_m), 1/theta_m = 4,
     // so the convective part is +-W_1 * 4 * L = +-L/2
-    const float w = p.omega_m;
-    const float Axy = 0.5f * Lxy, Axz = 0.5f * Lxz, Ayz = 0.5f * Lyz;
-    // sign of the convective term of each (j, a): a = 0 rest, 1..6 = +x,-x,+y,-y,+z,-z
-    const float conv[21] = {
-        0.f, 0.f, 0.f, -Axy, Axy, -Axz, Axz,          // j = x: Lambda^eq_yx = -Lxy, Lambda^eq_zx = -Lxz
-        0.f, Axy, -Axy, 0.f, 0.f, -Ayz, Ayz,          // j = y: Lambda^eq_xy = Lxy, Lambda^eq_zy = -Lyz
-        0.f, Axz, -Axz, Ayz, -Ayz, 0.f, 0.f};         // j = z: Lambda^eq_xz = Lxz, Lambda^eq_yz = Lyz
+    const V w(p.omega_m);
+    const V Axy = V(0.5f) * Lxy, Axz = V(0.5f) * Lxz, Ayz = V(0.5f) * Lyz;
+    const V zero(0.f);
+    // convective term of each (j, a): a = 0 rest, 1..6 = +x,-x,+y,-y,+z,-z
+    const V conv[21] = {
+        zero, zero, zero, -Axy, Axy, -Axz, Axz,       // j = x: Lambda^eq_yx = -Lxy, Lambda^eq_zx = -Lxz
+        zero, Axy, -Axy, zero, zero, -Ayz, Ayz,       // j = y: Lambda^eq_xy = Lxy, Lambda^eq_zy = -Lyz
+        zero, Axz, -Axz, Ayz, -Ayz, zero, zero};      // j = z: Lambda^eq_xz = Lxz, Lambda^eq_yz = Lyz
 #pragma unroll
     for (int i = 0; i < 21; ++i) {
         const int j = i / 7, a = i % 7;
-        const float W = a == 0 ? 0.25f : 0.125f;
-        const float bh = j == 0 ? bxh : (j == 1 ? byh : bzh);
-        const float bl = j == 0 ? bxl : (j == 1 ? byl : bzl);
-        float neq;
-        if constexpr (PRECISE) neq = (W * bh - qh[i]) + ((W * bl - ql[i]) + conv[i]);
-        else neq = (W * bh + conv[i]) - q[i];
+        const V W(a == 0 ? 0.25f : 0.125f);
+        const V bh = j == 0 ? bxh : (j == 1 ? byh : bzh);
+        V neq;
+        if constexpr (PRECISE) {
+            const V bl = j == 0 ? bxl : (j == 1 ? byl : bzl);
+            neq = (W * bh - qh[i]) + ((W * bl - ql[i]) + conv[i]);
+        } else {
+            neq = (W * bh + conv[i]) - q[i];
+        }
         og[i] = w * neq;
     }
 }
 
 // Moments of a set of 19 deviations that are linear in them: group sums over
 // the rest, axis and the three diagonal planes, then the rows of T (App. A).
+template <class V>
 struct Lin {
-    float drho, mx, my, mz;          // rows 0, 3, 5, 7
-    float M1, M2;                    // e, e^2 (rows 1, 2)
-    float Qx, Qy, Qz;                // q (rows 4, 6, 8)
-    float P9, P10, P11, P12, P13, P14, P15, P16, P17, P18;
+    V drho, mx, my, mz;          // rows 0, 3, 5, 7
+    V M1, M2;                    // e, e^2 (rows 1, 2)
+    V Qx, Qy, Qz;                // q (rows 4, 6, 8)
+    V P9, P10, P11, P12, P13, P14, P15, P16, P17, P18;
 };
 
-__device__ __forceinline__ Lin linear_moments(const float (&d)[19])
+template <class V>
+__device__ __forceinline__ Lin<V> linear_moments(const V (&d)[19])
 {
-    Lin L;
-    const float Ax = d[1] + d[2], Ay = d[3] + d[4], Az = d[5] + d[6];
-    const float Sax = Ax + Ay + Az;
-    const float Gxy = d[7] + d[8] + d[9] + d[10];
-    const float Gxz = d[11] + d[12] + d[13] + d[14];
-    const float Gyz = d[15] + d[16] + d[17] + d[18];
-    const float Sdg = Gxy + Gxz + Gyz;
-    const float Xax = d[1] - d[2], Xxy = d[7] - d[8] + d[9] - d[10], Xxz = d[11] - d[12] + d[13] - d[14];
-    const float Yax = d[3] - d[4], Yxy = d[7] + d[8] - d[9] - d[10], Yyz = d[15] - d[16] + d[17] - d[18];
-    const float Zax = d[5] - d[6], Zxz = d[11] + d[12] - d[13] - d[14], Zyz = d[15] + d[16] - d[17] - d[18];
+    Lin<V> L;
+    const V Ax = d[1] + d[2], Ay = d[3] + d[4], Az = d[5] + d[6];
+    const V Sax = Ax + Ay + Az;
+    const V Gxy = d[7] + d[8] + d[9] + d[10];
+    const V Gxz = d[11] + d[12] + d[13] + d[14];
+    const V Gyz = d[15] + d[16] + d[17] + d[18];
+    const V Sdg = Gxy + Gxz + Gyz;
+    const V Xax = d[1] - d[2], Xxy = d[7] - d[8] + d[9] - d[10], Xxz = d[11] - d[12] + d[13] - d[14];
+    const V Yax = d[3] - d[4], Yxy = d[7] + d[8] - d[9] - d[10], Yyz = d[15] - d[16] + d[17] - d[18];
+    const V Zax = d[5] - d[6], Zxz = d[11] + d[12] - d[13] - d[14], Zyz = d[15] + d[16] - d[17] - d[18];
     L.drho = d[0] + Sax + Sdg;
     L.mx = Xax + Xxy + Xxz;
     L.my = Yax + Yxy + Yyz;
     L.mz = Zax + Zxz + Zyz;
-    L.M1 = -30.f * d[0] - 11.f * Sax + 8.f * Sdg;
-    L.M2 = 12.f * d[0] - 4.f * Sax + Sdg;
-    L.Qx = -4.f * Xax + Xxy + Xxz;
-    L.Qy = -4.f * Yax + Yxy + Yyz;
-    L.Qz = -4.f * Zax + Zxz + Zyz;
-    L.P9 = 2.f * Ax - Ay - Az + Gxy + Gxz - 2.f * Gyz;
-    L.P10 = -4.f * Ax + 2.f * Ay + 2.f * Az + Gxy + Gxz - 2.f * Gyz;
+    L.M1 = V(-30.f) * d[0] - V(11.f) * Sax + V(8.f) * Sdg;
+    L.M2 = V(12.f) * d[0] - V(4.f) * Sax + Sdg;
+    L.Qx = V(-4.f) * Xax + Xxy + Xxz;
+    L.Qy = V(-4.f) * Yax + Yxy + Yyz;
+    L.Qz = V(-4.f) * Zax + Zxz + Zyz;
+    const V two(2.f);
+    L.P9 = two * Ax - Ay - Az + Gxy + Gxz - two * Gyz;
+    L.P10 = V(-4.f) * Ax + two * Ay + two * Az + Gxy + Gxz - two * Gyz;
     L.P11 = Ay - Az + Gxy - Gxz;
-    L.P12 = -2.f * Ay + 2.f * Az + Gxy - Gxz;
+    L.P12 = V(-2.f) * Ay + two * Az + Gxy - Gxz;
     L.P13 = d[7] - d[8] - d[9] + d[10];
     L.P14 = d[15] - d[16] - d[17] + d[18];
     L.P15 = d[11] - d[12] - d[13] + d[14];
@@ -360,139 +621,183 @@ __device__ __forceinline__ Lin linear_moments(const float (&d)[19])
     return L;
 }
 
-// Error-free split d = dh + dl with dh on the grid of multiples of 2^-28
-// (|d| <= 2^-5): integer-weighted sums of the dh are then exact in FP32 while
-// they stay below 2^-4, and the dl (|dl| <= 2^-29) carry the rest.  Moments
-// formed as (exact high sum - equilibrium) + low sum keep the small
-// non-equilibrium parts free of the round-off of the large sums, which
-// otherwise leaves the FP32 time march wandering at r ~ 1e-7 instead of
-// settling on its fixed point.
-
-__device__ __forceinline__ void split_exact(const float (&d)[19], float (&dh)[19], float (&dl)[19])
-{
-#pragma unroll
-    for (int a = 0; a < 19; ++a) {
-        dh[a] = __fsub_rn(__fadd_rn(d[a], SPLIT_C), SPLIT_C);
-        dl[a] = __fsub_rn(d[a], dh[a]);
-    }
-}
-
-// Non-equilibrium moments and conserved sums of a node.  H holds the linear
-// moments of the populations (or of their exact high parts) and L those of the
-// low parts (PRECISE) -- L is not read otherwise.
-template <bool PRECISE>
+// Linear moments of a node: H of the populations (or of their exact high
+// parts) and L of the low parts (PRECISE only; L is not read otherwise).
+template <class V, bool PRECISE>
 struct NodeMoments {
-    Lin H, L;
-    __device__ __forceinline__ float drho() const { return PRECISE ? H.drho + L.drho : H.drho; }
+    Lin<V> H, L;
+    __device__ __forceinline__ V drho() const { return PRECISE ? H.drho + L.drho : H.drho; }
 };
 
 // D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
 // (I - Lambda*/2) S*] (Eqs. ppostcollision, prelax_term).  F is the total
 // force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32.
-template <bool PRECISE>
-__device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<PRECISE>& mm, float (&om)[19],
-                                             float rho_inv, float jx, float jy, float jz, float Fx, float Fy,
-                                             float Fz)
+template <class V, bool PRECISE>
+__device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<V, PRECISE>& mm, V (&om)[19],
+                                             V rho_inv, V jx, V jy, V jz, V Fx, V Fy, V Fz)
 {
-    const float ig = p.inv_gamma, ig2 = p.inv_gamma2;
-    const float gri = ig * rho_inv;                   // 1/(gamma rho)
-    const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
-    const float jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
-    const Lin& H = mm.H;
-    const Lin& L = mm.L;
-#define GLBE_LO(expr) (PRECISE ? (expr) : 0.f)
+    const V ig(p.inv_gamma), ig2(p.inv_gamma2);
+    const V gri = ig * rho_inv;                   // 1/(gamma rho)
+    const V ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
+    const V jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
+    const Lin<V>& H = mm.H;
+    const Lin<V>& L = mm.L;
 #define GLBE_NK(hi, lo) (PRECISE ? (hi) + (lo) : (hi))
     // n_k = f^_k - f^eq,*_k; the rest state contributes -11 rho0 to row 1 and
     // 3 rho0 to row 2 only, so the deviations' moments enter directly
-    const float n1 = GLBE_NK((H.M1 + 11.f * H.drho) - 19.f * jj * gri, GLBE_LO(L.M1 + 11.f * L.drho));
-    const float n2 = GLBE_NK((H.M2 - 3.f * H.drho) + 5.5f * jj * gri, GLBE_LO(L.M2 - 3.f * L.drho));
-    const float n4 = GLBE_NK(H.Qx, GLBE_LO(L.Qx)) + (2.f / 3.f) * jx;
-    const float n6 = GLBE_NK(H.Qy, GLBE_LO(L.Qy)) + (2.f / 3.f) * jy;
-    const float n8 = GLBE_NK(H.Qz, GLBE_LO(L.Qz)) + (2.f / 3.f) * jz;
-    const float e9 = (3.f * jxx - jj) * gri;
-    const float e11 = (jyy - jzz) * gri;
-    const float n9 = GLBE_NK(H.P9 - e9, GLBE_LO(L.P9));
-    const float n10 = GLBE_NK(H.P10 + 0.5f * e9, GLBE_LO(L.P10));
-    const float n11 = GLBE_NK(H.P11 - e11, GLBE_LO(L.P11));
-    const float n12 = GLBE_NK(H.P12 + 0.5f * e11, GLBE_LO(L.P12));
-    const float n13 = GLBE_NK(H.P13 - jx * jy * gri, GLBE_LO(L.P13));
-    const float n14 = GLBE_NK(H.P14 - jy * jz * gri, GLBE_LO(L.P14));
-    const float n15 = GLBE_NK(H.P15 - jx * jz * gri, GLBE_LO(L.P15));
-    const float n16 = GLBE_NK(H.P16, GLBE_LO(L.P16));
-    const float n17 = GLBE_NK(H.P17, GLBE_LO(L.P17));
-    const float n18 = GLBE_NK(H.P18, GLBE_LO(L.P18));
-#undef GLBE_LO
+    const V n1 = GLBE_NK((H.M1 + V(11.f) * H.drho) - V(19.f) * jj * gri, (L.M1 + V(11.f) * L.drho));
+    const V n2 = GLBE_NK((H.M2 - V(3.f) * H.drho) + V(5.5f) * jj * gri, (L.M2 - V(3.f) * L.drho));
+    const V n4 = GLBE_NK(H.Qx, L.Qx) + V(2.f / 3.f) * jx;
+    const V n6 = GLBE_NK(H.Qy, L.Qy) + V(2.f / 3.f) * jy;
+    const V n8 = GLBE_NK(H.Qz, L.Qz) + V(2.f / 3.f) * jz;
+    const V e9 = (V(3.f) * jxx - jj) * gri;
+    const V e11 = (jyy - jzz) * gri;
+    const V n9 = GLBE_NK(H.P9 - e9, L.P9);
+    const V n10 = GLBE_NK(H.P10 + V(0.5f) * e9, L.P10);
+    const V n11 = GLBE_NK(H.P11 - e11, L.P11);
+    const V n12 = GLBE_NK(H.P12 + V(0.5f) * e11, L.P12);
+    const V n13 = GLBE_NK(H.P13 - jx * jy * gri, L.P13);
+    const V n14 = GLBE_NK(H.P14 - jy * jz * gri, L.P14);
+    const V n15 = GLBE_NK(H.P15 - jx * jz * gri, L.P15);
+    const V n16 = GLBE_NK(H.P16, L.P16);
+    const V n17 = GLBE_NK(H.P17, L.P17);
+    const V n18 = GLBE_NK(H.P18, L.P18);
 #undef GLBE_NK
 
     // preconditioned source moments S* = P_S S (App. A, Eq. precondsourceterm)
-    const float Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
-    const float S1 = 38.f * Fu * ig2, S2 = -11.f * Fu * ig2;
-    const float S4 = (-2.f / 3.f) * Fx * ig, S6 = (-2.f / 3.f) * Fy * ig, S8 = (-2.f / 3.f) * Fz * ig;
-    const float S9 = 2.f * (2.f * Fux - Fuy - Fuz) * ig2, S10 = -0.5f * S9;
-    const float S11 = 2.f * (Fuy - Fuz) * ig2, S12 = -0.5f * S11;
-    const float S13 = (Fx * uy + Fy * ux) * ig2;
-    const float S14 = (Fy * uz + Fz * uy) * ig2;
-    const float S15 = (Fx * uz + Fz * ux) * ig2;
+    const V Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
+    const V S1 = V(38.f) * Fu * ig2, S2 = V(-11.f) * Fu * ig2;
+    const V S4 = V(-2.f / 3.f) * Fx * ig, S6 = V(-2.f / 3.f) * Fy * ig, S8 = V(-2.f / 3.f) * Fz * ig;
+    const V S9 = V(2.f) * (V(2.f) * Fux - Fuy - Fuz) * ig2, S10 = V(-0.5f) * S9;
+    const V S11 = V(2.f) * (Fuy - Fuz) * ig2, S12 = V(-0.5f) * S11;
+    const V S13 = (Fx * uy + Fy * ux) * ig2;
+    const V S14 = (Fy * uz + Fz * uy) * ig2;
+    const V S15 = (Fx * uz + Fz * ux) * ig2;
 
     // delta_k = [-s_k n_k + (1 - s_k/2) S*_k] / |row_k|^2; conserved rows:
     // delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
-#define GLBE_DK(k, nk, Sk, inv) (((-p.s[k]) * (nk) + (1.f - 0.5f * p.s[k]) * (Sk)) * (inv))
-    const float q1 = GLBE_DK(1, n1, S1, 1.f / 2394.f);
-    const float q2 = GLBE_DK(2, n2, S2, 1.f / 252.f);
-    const float q3 = Fx * ig * 0.1f, q5 = Fy * ig * 0.1f, q7 = Fz * ig * 0.1f;
-    const float q4 = GLBE_DK(4, n4, S4, 1.f / 40.f);
-    const float q6 = GLBE_DK(6, n6, S6, 1.f / 40.f);
-    const float q8 = GLBE_DK(8, n8, S8, 1.f / 40.f);
-    const float q9 = GLBE_DK(9, n9, S9, 1.f / 36.f);
-    const float q10 = GLBE_DK(10, n10, S10, 1.f / 72.f);
-    const float q11 = GLBE_DK(11, n11, S11, 1.f / 12.f);
-    const float q12 = GLBE_DK(12, n12, S12, 1.f / 24.f);
-    const float q13 = GLBE_DK(13, n13, S13, 0.25f);
-    const float q14 = GLBE_DK(14, n14, S14, 0.25f);
-    const float q15 = GLBE_DK(15, n15, S15, 0.25f);
-    const float q16 = -p.s[16] * n16 * 0.125f;
-    const float q17 = -p.s[17] * n17 * 0.125f;
-    const float q18 = -p.s[18] * n18 * 0.125f;
+#define GLBE_DK(k, nk, Sk, inv) (vfma(V(-p.s[k]), (nk), V(1.f - 0.5f * p.s[k]) * (Sk)) * V(inv))
+    const V q1 = GLBE_DK(1, n1, S1, 1.f / 2394.f);
+    const V q2 = GLBE_DK(2, n2, S2, 1.f / 252.f);
+    const V q3 = Fx * ig * V(0.1f), q5 = Fy * ig * V(0.1f), q7 = Fz * ig * V(0.1f);
+    const V q4 = GLBE_DK(4, n4, S4, 1.f / 40.f);
+    const V q6 = GLBE_DK(6, n6, S6, 1.f / 40.f);
+    const V q8 = GLBE_DK(8, n8, S8, 1.f / 40.f);
+    const V q9 = GLBE_DK(9, n9, S9, 1.f / 36.f);
+    const V q10 = GLBE_DK(10, n10, S10, 1.f / 72.f);
+    const V q11 = GLBE_DK(11, n11, S11, 1.f / 12.f);
+    const V q12 = GLBE_DK(12, n12, S12, 1.f / 24.f);
+    const V q13 = GLBE_DK(13, n13, S13, 0.25f);
+    const V q14 = GLBE_DK(14, n14, S14, 0.25f);
+    const V q15 = GLBE_DK(15, n15, S15, 0.25f);
+    const V q16 = V(-p.s[16] * 0.125f) * n16;
+    const V q17 = V(-p.s[17] * 0.125f) * n17;
+    const V q18 = V(-p.s[18] * 0.125f) * n18;
 #undef GLBE_DK
 
     // om = T^t delta  (columns of T read from the basis polynomials); f~ = f + om
-    om[0] = -30.f * q1 + 12.f * q2;
-    const float A = -11.f * q1 - 4.f * q2;          // axis directions, c^2 = 1
-    const float X9 = 2.f * q9 - 4.f * q10;           // 3c_x^2 - c^2 = 2 on +-x
-    const float Y9 = -q9 + 2.f * q10;                // ... = -1 on +-y, +-z
-    const float W11 = q11 - 2.f * q12;
-    float t = q3 - 4.f * q4;
+    om[0] = V(-30.f) * q1 + V(12.f) * q2;
+    const V A = V(-11.f) * q1 - V(4.f) * q2;          // axis directions, c^2 = 1
+    const V X9 = V(2.f) * q9 - V(4.f) * q10;           // 3c_x^2 - c^2 = 2 on +-x
+    const V Y9 = V(2.f) * q10 - q9;                    // ... = -1 on +-y, +-z
+    const V W11 = q11 - V(2.f) * q12;
+    V t = q3 - V(4.f) * q4;
     om[1] = A + X9 + t;
     om[2] = A + X9 - t;
-    t = q5 - 4.f * q6;
+    t = q5 - V(4.f) * q6;
     om[3] = A + Y9 + W11 + t;
     om[4] = A + Y9 + W11 - t;
-    t = q7 - 4.f * q8;
+    t = q7 - V(4.f) * q8;
     om[5] = A + Y9 - W11 + t;
     om[6] = A + Y9 - W11 - t;
-    const float Dg = 8.f * q1 + q2;                  // diagonal directions, c^2 = 2
-    const float P = q9 + q10, Q = q11 + q12;
+    const V Dg = V(8.f) * q1 + q2;                  // diagonal directions, c^2 = 2
+    const V P = q9 + q10, Q = q11 + q12;
     {   // (+-1, +-1, 0)
-        const float b = Dg + P + Q, ax = q3 + q4 + q16, by = q5 + q6 - q17;
+        const V b = Dg + P + Q, ax = q3 + q4 + q16, by = q5 + q6 - q17;
         om[7] = b + ax + by + q13;
         om[8] = b - ax + by - q13;
         om[9] = b + ax - by - q13;
         om[10] = b - ax - by + q13;
     }
     {   // (+-1, 0, +-1)
-        const float b = Dg + P - Q, ax = q3 + q4 - q16, bz = q7 + q8 + q18;
+        const V b = Dg + P - Q, ax = q3 + q4 - q16, bz = q7 + q8 + q18;
         om[11] = b + ax + bz + q15;
         om[12] = b - ax + bz - q15;
         om[13] = b + ax - bz - q15;
         om[14] = b - ax - bz + q15;
     }
     {   // (0, +-1, +-1)
-        const float b = Dg - 2.f * P, ay = q5 + q6 + q17, bz = q7 + q8 - q18;
+        const V b = Dg - V(2.f) * P, ay = q5 + q6 + q17, bz = q7 + q8 - q18;
         om[15] = b + ay + bz + q14;
         om[16] = b - ay + bz - q14;
         om[17] = b + ay - bz - q14;
         om[18] = b - ay - bz + q14;
     }
+}
+
+// Result of one node's (or pair's) update besides the new populations.
+template <class V>
+struct NodeState {
+    V rho, drho, jx, jy, jz, ux, uy, uz;
+    NodeMacro<V> mac;
+};
+
+// The whole update of a node (pair) from its gathered populations: moments,
+// induction and Lorentz force, velocity, collision changes om (f) and og (g).
+// With collide = false only the macroscopic fields are formed.
+template <class V, int ST, bool MHD>
+__device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19], const V (&dl)[19],
+                                            const V (&q)[21], const V (&ql)[21], V FLpx, V FLpy, V FLpz, V Fx,
+                                            V Fy, V Fz, bool collide, V (&om)[19], V (&og)[21], NodeState<V>& ns)
+{
+    using S = Store<ST>;
+    // moments linear in the populations; density and bare first moment
+    // (Eq. precondhydrofields)
+    constexpr bool PRECISE = (ST == ST_F32 || ST == ST_F32C);
+    NodeMoments<V, PRECISE> mm;
+    if constexpr (PRECISE) {
+        V dh[19], dlo[19];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            split_exact(d[a], dh[a], dlo[a]);
+            if constexpr (S::COMP) dlo[a] += dl[a];
+        }
+        mm.H = linear_moments(dh);
+        mm.L = linear_moments(dlo);
+    } else {
+        mm.H = linear_moments(d);
+    }
+    ns.drho = mm.drho();
+    ns.rho = V(p.rho0) + ns.drho;
+    const V rho_inv = vrcp(ns.rho);
+    const V mxh = mm.H.mx, myh = mm.H.my, mzh = mm.H.mz;
+    const V mxl = PRECISE ? mm.L.mx : V(0.f), myl = PRECISE ? mm.L.my : V(0.f), mzl = PRECISE ? mm.L.mz : V(0.f);
+    ns.mac.Bx = ns.mac.By = ns.mac.Bz = V(0.f);
+    ns.mac.FLx = ns.mac.FLy = ns.mac.FLz = V(0.f);
+    if (MHD) {
+        induction_collide<V, PRECISE, S::COMP>(p, q, ql, og, rho_inv, PRECISE ? mxh + mxl : mxh,
+                                               PRECISE ? myh + myl : myh, PRECISE ? mzh + mzl : mzh, Fx, Fy, Fz,
+                                               FLpx, FLpy, FLpz, ns.mac);
+        Fx += ns.mac.FLx;
+        Fy += ns.mac.FLy;
+        Fz += ns.mac.FLz;
+    }
+    // j = m + F/(2 gamma): in the precise path the high parts and the
+    // half-force are added by an exact two-sum before rounding once
+    const V hg(0.5f * p.inv_gamma);
+    if constexpr (PRECISE) {
+        ns.jx = two_sum_round(mxh, hg * Fx, mxl);
+        ns.jy = two_sum_round(myh, hg * Fy, myl);
+        ns.jz = two_sum_round(mzh, hg * Fz, mzl);
+    } else {
+        ns.jx = mxh + hg * Fx;
+        ns.jy = myh + hg * Fy;
+        ns.jz = mzh + hg * Fz;
+    }
+    ns.ux = ns.jx * rho_inv;
+    ns.uy = ns.jy * rho_inv;
+    ns.uz = ns.jz * rho_inv;
+    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, Fx, Fy, Fz);
 }
 
 template <typename V>
@@ -503,6 +808,31 @@ __device__ __forceinline__ V warp_sum(V v)
     return v;
 }
 
+// Residual sums of a block into partials[k][block]: FP32 per node and per
+// warp (each term is one node's FP32 quantity), FP64 from the block level on
+// -- GB300's FP64 pipe is kept off the per-node path.
+template <int NT>
+__device__ __forceinline__ void block_partials(float (&acc)[7], double* partials)
+{
+    __shared__ double sh[NT / 32][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float v = warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += sh[w][threadIdx.x];
+        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scalar kernel: one node per thread, any geometry
+// ---------------------------------------------------------------------------
 template <int ST, bool MHD, int MODE>
 __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
 {
@@ -519,14 +849,10 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
     if (MODE == MODE_STEP && !fluid) return;
     if (MODE == MODE_FIELDS && !inb) return;
 
-    // residual sums: FP32 per node and per warp (each term is one node's
-    // FP32 quantity), FP64 from the block level on -- GB300's FP64 pipe is
-    // kept off the per-node path
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (fluid) {
-        float d[19], dl[19];
+        float d[19], dl[19], q[21], ql[21];
         load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
-        float q[21], ql[21];
         float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
         if (MHD) {
             load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q, ql);
@@ -534,69 +860,22 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
             FLpy = b.FL[N + n];
             FLpz = b.FL[2 * N + n];
         }
-        // moments linear in the populations; density and bare first moment
-        // (Eq. precondhydrofields)
-        constexpr bool PRECISE = (ST == ST_F32 || ST == ST_F32C);
-        NodeMoments<PRECISE> mm;
-        if constexpr (PRECISE) {
-            float dh[19], dlo[19];
-            split_exact(d, dh, dlo);
-            if constexpr (S::COMP) {
-#pragma unroll
-                for (int a = 0; a < 19; ++a) dlo[a] += dl[a];
-            }
-            mm.H = linear_moments(dh);
-            mm.L = linear_moments(dlo);
-        } else {
-            mm.H = linear_moments(d);
-        }
-        const float drho = mm.drho();
-        const float rho = p.rho0 + drho;
-        const float rho_inv = 1.0f / rho;
-        const float mxh = mm.H.mx, myh = mm.H.my, mzh = mm.H.mz;
-        const float mxl = PRECISE ? mm.L.mx : 0.f, myl = PRECISE ? mm.L.my : 0.f, mzl = PRECISE ? mm.L.mz : 0.f;
-        // external force
         float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
         if (p.force_ncomp >= 1) Fx += __ldg(b.Ffield + n);
         if (p.force_ncomp == 3) {
             Fy += __ldg(b.Ffield + N + n);
             Fz += __ldg(b.Ffield + 2 * N + n);
         }
-        NodeMacro mac;
-        mac.Bx = mac.By = mac.Bz = 0.f;
-        mac.FLx = mac.FLy = mac.FLz = 0.f;
-        float og[21];
-        if (MHD) {
-            induction_collide<PRECISE, S::COMP>(p, q, ql, og, rho_inv, mxh + mxl, myh + myl, mzh + mzl, Fx, Fy, Fz,
-                                                FLpx, FLpy, FLpz, mac);
-            Fx += mac.FLx;
-            Fy += mac.FLy;
-            Fz += mac.FLz;
-        }
-        // j = m + F/(2 gamma): in the precise path the high parts and the
-        // half-force are added by an exact two-sum before rounding once
-        const float hg = 0.5f * p.inv_gamma;
-        float jx, jy, jz;
-        if constexpr (PRECISE) {
-            jx = two_sum_round(mxh, hg * Fx, mxl);
-            jy = two_sum_round(myh, hg * Fy, myl);
-            jz = two_sum_round(mzh, hg * Fz, mzl);
-        } else {
-            jx = mxh + hg * Fx;
-            jy = myh + hg * Fy;
-            jz = mzh + hg * Fz;
-        }
-        const float ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
+        float om[19], og[21];
+        NodeState<float> ns;
+        node_update<float, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, MODE != MODE_FIELDS, om, og, ns);
 
         if (MODE == MODE_FIELDS) {
-            if (fo.rho) fo.rho[n] = rho;
-            if (fo.u) { fo.u[n] = ux; fo.u[N + n] = uy; fo.u[2 * N + n] = uz; }
-            if (MHD && fo.B) { fo.B[n] = mac.Bx; fo.B[N + n] = mac.By; fo.B[2 * N + n] = mac.Bz; }
+            if (fo.rho) fo.rho[n] = ns.rho;
+            if (fo.u) { fo.u[n] = ns.ux; fo.u[N + n] = ns.uy; fo.u[2 * N + n] = ns.uz; }
+            if (MHD && fo.B) { fo.B[n] = ns.mac.Bx; fo.B[N + n] = ns.mac.By; fo.B[2 * N + n] = ns.mac.Bz; }
             return;
         }
-
-        float om[19];
-        flow_collide<PRECISE>(p, mm, om, rho_inv, jx, jy, jz, Fx, Fy, Fz);
         // f~ = f + om, written to the node's own slot of the other buffer
         T* __restrict__ fd = static_cast<T*>(b.fdst);
         if constexpr (S::COMP) {
@@ -610,7 +889,7 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv((d[a] + om[a]) * p.scale);
+            for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, d[a] + om[a]));
         }
         if (MHD) {
             T* __restrict__ gd = static_cast<T*>(b.gdst);
@@ -625,26 +904,26 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
                 }
             } else {
 #pragma unroll
-                for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv((q[a] + og[a]) * p.scale);
+                for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv(toscale<ST>(p, q[a] + og[a]));
             }
-            b.FL[n] = mac.FLx;
-            b.FL[N + n] = mac.FLy;
-            b.FL[2 * N + n] = mac.FLz;
+            b.FL[n] = ns.mac.FLx;
+            b.FL[N + n] = ns.mac.FLy;
+            b.FL[2 * N + n] = ns.mac.FLz;
         }
         if (MODE == MODE_STEP_RESID) {
             if (b.have_snap) {
-                const float dx = ux - b.usnap[n], dy = uy - b.usnap[N + n], dz = uz - b.usnap[2 * N + n];
+                const float dx = ns.ux - b.usnap[n], dy = ns.uy - b.usnap[N + n], dz = ns.uz - b.usnap[2 * N + n];
                 acc[0] = dx * dx + dy * dy + dz * dz;
             }
-            acc[1] = ux * ux + uy * uy + uz * uz;
-            acc[2] = drho;                 // the mass is rho0 * (fluid nodes) + sum drho
-            acc[3] = jx;
-            acc[4] = jy;
-            acc[5] = jz;
-            acc[6] = isfinite(ux + uy + uz) ? 0.f : 1.f;
-            b.usnap[n] = ux;
-            b.usnap[N + n] = uy;
-            b.usnap[2 * N + n] = uz;
+            acc[1] = ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
+            acc[2] = ns.drho;              // the mass is rho0 * (fluid nodes) + sum drho
+            acc[3] = ns.jx;
+            acc[4] = ns.jy;
+            acc[5] = ns.jz;
+            acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
+            b.usnap[n] = ns.ux;
+            b.usnap[N + n] = ns.uy;
+            b.usnap[2 * N + n] = ns.uz;
         }
     } else if (MODE == MODE_FIELDS) {
         if (fo.rho) fo.rho[n] = 0.f;
@@ -652,26 +931,120 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
         if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
         return;
     }
-
-    if (MODE == MODE_STEP_RESID) {
-        __shared__ double sh[STEP_THREADS / 32][7];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const float v = warp_sum(acc[k]);
-            if (lane == 0) sh[warp][k] = (double)v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 7) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < STEP_THREADS / 32; ++w) s += sh[w][threadIdx.x];
-            // structure of arrays: partials[k][block] (coalesced in the finalize)
-            b.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
-        }
-    }
+    if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 
+// ---------------------------------------------------------------------------
+// Paired kernel: two x-adjacent nodes per thread (x periodic, nx even)
+// ---------------------------------------------------------------------------
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParams p, const StepBuffers b)
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    if (b.stop != nullptr && *b.stop) return;
+    const uint32_t npairs = p.N >> 1;
+    const uint32_t i = blockIdx.x * PAIR_THREADS + threadIdx.x;
+    const bool inb = i < npairs;
+    // lanes past the end mirror the last pair so that every lane takes part in
+    // the shuffles; they write nothing
+    const uint32_t n0 = 2u * (inb ? i : npairs - 1u);
+    const GeoP gp = make_geo_pair(p, n0);
+    const Geo& g = gp.g;
+    const bool fluid = inb && !g.solid;
+    const size_t N = p.N;
+
+    F2 d[19], dl[19], q[21], ql[21];
+    load_f_pair<ST>(p, static_cast<const T*>(b.fsrc), gp, d, dl);
+    if (MHD) load_g_pair<ST>(p, static_cast<const T*>(b.gsrc), gp, q, ql);
+
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (fluid) {
+        F2 FLpx(0.f), FLpy(0.f), FLpz(0.f);
+        if (MHD) {
+            FLpx = F2(*reinterpret_cast<const float2*>(b.FL + n0));
+            FLpy = F2(*reinterpret_cast<const float2*>(b.FL + N + n0));
+            FLpz = F2(*reinterpret_cast<const float2*>(b.FL + 2 * N + n0));
+        }
+        F2 Fx(p.F[0]), Fy(p.F[1]), Fz(p.F[2]);
+        if (p.force_ncomp >= 1) Fx += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + n0)));
+        if (p.force_ncomp == 3) {
+            Fy += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + N + n0)));
+            Fz += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + 2 * N + n0)));
+        }
+        F2 om[19], og[21];
+        NodeState<F2> ns;
+        node_update<F2, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, true, om, og, ns);
+
+        T* __restrict__ fd = static_cast<T*>(b.fdst);
+        if constexpr (S::COMP) {
+            __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
+#pragma unroll
+            for (int a = 0; a < 19; ++a) {
+                F2 nh, nl;
+                comp_add(d[a], dl[a], om[a], nh, nl);
+                S::st2(fd + (size_t)a * N + n0, nh);
+                S::st2_lo(fdl + (size_t)a * N + n0, nl);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, d[a] + om[a]));
+        }
+        if (MHD) {
+            T* __restrict__ gd = static_cast<T*>(b.gdst);
+            if constexpr (S::COMP) {
+                __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
+#pragma unroll
+                for (int a = 0; a < 21; ++a) {
+                    F2 nh, nl;
+                    comp_add(q[a], ql[a], og[a], nh, nl);
+                    S::st2(gd + (size_t)a * N + n0, nh);
+                    S::st2_lo(gdl + (size_t)a * N + n0, nl);
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 21; ++a) S::st2(gd + (size_t)a * N + n0, toscale<ST>(p, q[a] + og[a]));
+            }
+            *reinterpret_cast<float2*>(b.FL + n0) = ns.mac.FLx.v;
+            *reinterpret_cast<float2*>(b.FL + N + n0) = ns.mac.FLy.v;
+            *reinterpret_cast<float2*>(b.FL + 2 * N + n0) = ns.mac.FLz.v;
+        }
+        if (MODE == MODE_STEP_RESID) {
+            float2* us = reinterpret_cast<float2*>(b.usnap + n0);
+            float2* vs = reinterpret_cast<float2*>(b.usnap + N + n0);
+            float2* ws = reinterpret_cast<float2*>(b.usnap + 2 * N + n0);
+            if (b.have_snap) {
+                const F2 dx = ns.ux - F2(*us), dy = ns.uy - F2(*vs), dz = ns.uz - F2(*ws);
+                acc[0] = lane_sum(dx * dx + dy * dy + dz * dz);
+            }
+            acc[1] = lane_sum(ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz);
+            acc[2] = lane_sum(ns.drho);
+            acc[3] = lane_sum(ns.jx);
+            acc[4] = lane_sum(ns.jy);
+            acc[5] = lane_sum(ns.jz);
+            acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
+            *us = ns.ux.v;
+            *vs = ns.uy.v;
+            *ws = ns.uz.v;
+        }
+    }
+    if (MODE == MODE_STEP_RESID) block_partials<PAIR_THREADS>(acc, b.partials);
+}
+
+// The paired kernel serves x-periodic grids with an even nx.  The automatic
+// choice keeps the compensated storage on one node per thread (two nodes
+// with their low parts exceed the register file).
+inline bool pair_eligible(const StepParams& p)
+{
+    if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0]) return false;
+    if (p.variant == 1) return false;
+    if (p.variant == 2) return true;
+    return p.storage != ST_F32C;
+}
+
+// ---------------------------------------------------------------------------
+// State transfer (not on the hot path; scalar)
+// ---------------------------------------------------------------------------
 // Pre-collision state (deviations, FP32, C-ABI layout) of every fluid node.
 // The compensated form returns high + low rounded to FP32.
 template <int ST, bool MHD>
@@ -726,7 +1099,7 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
 #define GLBE_STOREF(a, o, src, sol)                                                         \
     {                                                                                       \
         const size_t s_ = GLBE_SLOTF(a, o, src, sol);                                       \
-        fs[s_] = Store<ST>::cv(df[(size_t)(a) * N + i] * p.scale);                          \
+        fs[s_] = Store<ST>::cv(toscale<ST>(p, df[(size_t)(a) * N + i]));                    \
         if (Store<ST>::COMP) fl[s_] = __float2half_rn(0.f);                                 \
     }
         GLBE_STOREF(0, 0, i, false)
@@ -746,7 +1119,7 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
     {                                                                                                \
         const size_t s_ = (sol) ? (size_t)(o) * N + i : (size_t)(a) * N + (src);                     \
         const float v_ = (sol) ? wall - vj[(size_t)(a) * N + i] : vj[(size_t)(a) * N + i];          \
-        bj[s_] = Store<ST>::cv(v_ * p.scale);                                                        \
+        bj[s_] = Store<ST>::cv(toscale<ST>(p, v_));                                                  \
         if (Store<ST>::COMP) blj[s_] = __float2half_rn(0.f);                                         \
     }
             GLBE_STOREG(0, 0, i, false)
@@ -758,21 +1131,37 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
         for (int k = 0; k < 3; ++k) FL[(size_t)k * N + i] = dFL[(size_t)k * N + i];
 }
 
-template <int ST>
-cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuffers& b, const FieldOut& fo,
-                          unsigned grid, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <int ST, bool MHD, int MODE>
+cudaError_t launch_mode(const StepParams& p, const StepBuffers& b, const FieldOut& fo, cudaStream_t st,
+                        unsigned* nblocks)
 {
-    const dim3 blk(STEP_THREADS);
-    if (mhd) {
-        if (mode == MODE_STEP) step_kernel<ST, true, MODE_STEP><<<grid, blk, 0, st>>>(p, b, fo);
-        else if (mode == MODE_STEP_RESID) step_kernel<ST, true, MODE_STEP_RESID><<<grid, blk, 0, st>>>(p, b, fo);
-        else step_kernel<ST, true, MODE_FIELDS><<<grid, blk, 0, st>>>(p, b, fo);
+    if (MODE != MODE_FIELDS && pair_eligible(p)) {
+        const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);
+        step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
+        if (nblocks) *nblocks = grid;
     } else {
-        if (mode == MODE_STEP) step_kernel<ST, false, MODE_STEP><<<grid, blk, 0, st>>>(p, b, fo);
-        else if (mode == MODE_STEP_RESID) step_kernel<ST, false, MODE_STEP_RESID><<<grid, blk, 0, st>>>(p, b, fo);
-        else step_kernel<ST, false, MODE_FIELDS><<<grid, blk, 0, st>>>(p, b, fo);
+        const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
+        step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+        if (nblocks) *nblocks = grid;
     }
     return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                          cudaStream_t st, unsigned* nblocks)
+{
+    if (mhd) {
+        if (mode == MODE_STEP) return launch_mode<ST, true, MODE_STEP>(p, b, fo, st, nblocks);
+        if (mode == MODE_STEP_RESID) return launch_mode<ST, true, MODE_STEP_RESID>(p, b, fo, st, nblocks);
+        return launch_mode<ST, true, MODE_FIELDS>(p, b, fo, st, nblocks);
+    }
+    if (mode == MODE_STEP) return launch_mode<ST, false, MODE_STEP>(p, b, fo, st, nblocks);
+    if (mode == MODE_STEP_RESID) return launch_mode<ST, false, MODE_STEP_RESID>(p, b, fo, st, nblocks);
+    return launch_mode<ST, false, MODE_FIELDS>(p, b, fo, st, nblocks);
 }
 
 template <int ST>

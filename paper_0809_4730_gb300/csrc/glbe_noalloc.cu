@@ -83,6 +83,10 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
     if (!d_src || !d_dst || !d_u || !out) return fail(GLBE_ERR_ARG, "src, dst, u or out is NULL");
     if (d_src == d_dst) return fail(GLBE_ERR_ARG, "src and dst must be different buffers");
     if (p->force_field && !d_force) return fail(GLBE_ERR_ARG, "force_field > 0 needs a force field");
+    // the step moves node pairs as 8-byte vectors: every buffer must be 16-byte aligned
+    auto misaligned = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) != 0; };
+    if (misaligned(d_src) || misaligned(d_dst) || misaligned(d_u) || (d_force && misaligned(d_force)))
+        return fail(GLBE_ERR_ARG, "src, dst, u and force must be 16-byte aligned");
     const size_t N = (size_t)p->nx * p->ny * p->nz;
     if (N > NOALLOC_MAX_NODES)
         return fail(GLBE_ERR_ARG, "grid of %zu nodes exceeds the allocation-free limit of %zu nodes", N,
@@ -102,7 +106,6 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
 
     cudaStream_t stream = static_cast<cudaStream_t>(p->stream);
     const StepParams sp = make_step_params(p);
-    const unsigned grid = (unsigned)((N + STEP_THREADS - 1) / STEP_THREADS);
     StepBuffers b{};
     b.fsrc = d_src;
     b.fdst = d_dst;
@@ -113,14 +116,15 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
     b.stop = nullptr;
     const FieldOut fo{nullptr, nullptr, nullptr};
 
+    unsigned grid = 0;   // blocks of the step launch (at most NOALLOC_MAX_BLOCKS for N within the limit)
     reset_counters<<<1, 1, 0, stream>>>(hist_count, t_dev, tol, stop, (long long)t);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
         switch (p->storage) {
-        case GLBE_F32: e = launch_step_t<ST_F32>(false, MODE_STEP_RESID, sp, b, fo, grid, stream); break;
-        case GLBE_BF16: e = launch_step_t<ST_BF16>(false, MODE_STEP_RESID, sp, b, fo, grid, stream); break;
-        case GLBE_F16: e = launch_step_t<ST_F16>(false, MODE_STEP_RESID, sp, b, fo, grid, stream); break;
-        default: e = launch_step_t<ST_F32C>(false, MODE_STEP_RESID, sp, b, fo, grid, stream); break;
+        case GLBE_F32: e = launch_step_t<ST_F32>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
+        case GLBE_BF16: e = launch_step_t<ST_BF16>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
+        case GLBE_F16: e = launch_step_t<ST_F16>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
+        default: e = launch_step_t<ST_F32C>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         }
     }
     const long long fluid = (long long)(p->nx - p->wall_lo[0] - p->wall_hi[0]) *

@@ -5,7 +5,7 @@
 
 namespace glbe {
 template cudaError_t launch_step_t<ST_F32C>(bool, int, const StepParams&, const StepBuffers&, const FieldOut&,
-                                           unsigned, cudaStream_t);
+                                           cudaStream_t, unsigned*);
 template cudaError_t launch_get_state_t<ST_F32C>(bool, const StepParams&, const void*, const void*, const float*,
                                                 float*, float*, float*, cudaStream_t);
 template cudaError_t launch_set_state_t<ST_F32C>(bool, const StepParams&, void*, void*, float*, const float*,

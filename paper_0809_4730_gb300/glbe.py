@@ -38,6 +38,7 @@ class glbe_params(C.Structure):
         ("B0", C.c_double * 3),
         ("storage", C.c_int), ("storage_scale", C.c_double),
         ("stream", C.c_void_p),
+        ("variant", C.c_int),
     ]
 
 
@@ -96,7 +97,7 @@ def load(build_if_missing: bool = True):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.glbe_abi_version() != 1:
+            if lib.glbe_abi_version() != 2:
                 raise RuntimeError("libglbe ABI version mismatch")
             ps, isz = C.c_size_t(0), C.c_size_t(0)
             lib.glbe_struct_sizes(C.byref(ps), C.byref(isz))
@@ -238,7 +239,7 @@ class Solver:
                     p.s[k] = float(val[k])
             elif key == "storage":
                 p.storage = STORAGE[val] if isinstance(val, str) else int(val)
-            elif key in ("induction", "force_field"):
+            elif key in ("induction", "force_field", "variant"):
                 setattr(p, key, int(val))
             else:
                 setattr(p, key, float(val))

@@ -19,12 +19,12 @@ from gpu_common import (W19, W7, gpu_fields, gpu_state, make_pair, oracle_state_
 pytestmark = pytest.mark.gpu
 
 
-def _cfg(orc, mhd, gamma=0.3, **kw):
+def _cfg(orc, mhd, gamma=0.3, nx=37, ny=11, nz=9, **kw):
     base = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 0), gamma=gamma, nu=0.02, F=(2e-5, -1e-5, 5e-6))
     if mhd:
         base.update(induction=True, gamma_m=gamma, eta=0.03, chi=0.4, mu=1.3, B0=(0.01, 0.03, -0.02))
     base.update(kw)
-    return orc.Config(37, 11, 9, **base)
+    return orc.Config(nx, ny, nz, **base)
 
 
 def _perturb(S, seed, scale=2e-3):
@@ -132,6 +132,45 @@ def test_nonfinite_state_is_reported_as_divergence(orc):
     with pytest.raises(GlbeError) as ei:
         G.residual()
     assert ei.value.status == GLBE_ERR_DIVERGED
+
+
+# The paired kernel (two x-adjacent nodes per thread, packed FP32x2): even nx,
+# x periodic.  nx = 2 and 6 make rows shorter than a warp, so every
+# row-start, row-end and warp-edge case of its lane shuffles occurs; nx = 38
+# leaves a partial last warp.
+@pytest.mark.parametrize("nx", [2, 6, 38])
+@pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2), ("f32c", 3e-5)])
+@pytest.mark.parametrize("mhd", [False, True])
+def test_step_parity_paired_kernel(orc, nx, storage, tol, mhd):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, mhd, gamma=0.4, nx=nx, ny=9, nz=7)
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=nx)
+    S, G = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=2)
+    _perturb(S, 17 + nx)
+    push_oracle_state(S, G)
+    fluid = ~S.solid_mask()
+    if storage != "f32":
+        # start the oracle from the state as rounded into the storage
+        df0, dg0, FL0 = gpu_state(G)
+        S.f[fluid] = (df0[:, fluid].T + W19[None, :] * cfg.rho0)
+        if mhd:
+            B0 = np.asarray(cfg.B0)
+            S.g[fluid] = dg0[:, fluid].T.reshape(-1, 3, 7) + W7[None, None, :] * B0[None, :, None]
+    n = 13
+    S.run(n)
+    G.step(n)
+    df, dg, FL = gpu_state(G)
+    odf, odg, oFL = oracle_state_dev(S)
+    assert rel_linf(df, odf, fluid) < tol
+    if mhd:
+        assert rel_linf(dg, odg, fluid) < tol
+        assert rel_linf(FL, oFL, fluid) < max(tol, 3e-5)
+    # the residual of level 10 was formed by the paired kernel's block sums
+    info = G.residual()
+    h = {row["t"]: row for row in S.hist}
+    assert info.t == 10
+    assert abs(info.r - h[10]["r"]) <= max(1e-3, 30 * tol) * h[10]["r"]
+    assert abs(info.mass - h[10]["mass"]) <= 1e-6 * h[10]["mass"]
 
 
 # ---------------------------------------------------------------------------

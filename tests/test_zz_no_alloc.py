@@ -75,3 +75,8 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     with pytest.raises(glbe.GlbeError) as ei:
         glbe.glbe_step_residual_noalloc(p, x, x[8:], None, x, False, 0)
     assert ei.value.status == glbe.GLBE_ERR_ARG
+    # a buffer that is not 16-byte aligned is refused on the host
+    p.nx, p.ny, p.nz = 4, 4, 4
+    with pytest.raises(glbe.GlbeError) as ei:
+        glbe.glbe_step_residual_noalloc(p, x[1:], x[8:], None, x, False, 0)
+    assert ei.value.status == glbe.GLBE_ERR_ARG
