@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--storage", choices=["bf16", "f16", "f32"], default="bf16")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -233,7 +234,7 @@ def run_glbe(args, rank, ws):
     except (OSError, KeyError, ValueError):
         hbm_peak, peak_src = 6800.0, "fallback"
 
-    G, F_host, fluid = duct_solver(args.storage)
+    G, F_host, fluid = duct_solver(args.storage, variant=args.variant)
     G.step(10 * args.warmup)
     G.residual()
     barrier(ws)
@@ -317,7 +318,7 @@ def run_glbe(args, rank, ws):
 def variants(args, hbm_peak, stream):
     import torch
     out = {}
-    for st, variant in (("f32", 0), ("f16", 0), ("bf16", 0), ("bf16", 1), ("f32", 1)):
+    for st, variant in (("f32", 0), ("f16", 0), ("bf16", 0), ("bf16", 2), ("f32", 2)):
         if st == args.storage and variant == 0:
             continue
         G, _, fluid = duct_solver(st, variant=variant)
@@ -326,7 +327,7 @@ def variants(args, hbm_peak, stream):
         total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
         kern_ms = plain_ms / nplain
         bpn = bytes_per_node(st, False, 1)
-        out[f"duct_{st}" + ("_one_node_per_thread" if variant == 1 else "")] = {
+        out[f"duct_{st}" + ("_paired" if variant == 2 else "")] = {
                              "mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1),
                              "kernel_ms": round(kern_ms, 5), "bytes_per_node": bpn,
                              "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
@@ -334,14 +335,14 @@ def variants(args, hbm_peak, stream):
         del G
         torch.cuda.empty_cache()
     # fused D3Q19 + D3Q7 on the 128^3 Hartmann duct (FP32 and BF16 storage)
-    for st, variant in (("f32", 0), ("f32", 1), ("bf16", 0)):
+    for st, variant in (("f32", 0), ("f32", 2), ("bf16", 0)):
         G, fluid = hartmann_duct_solver(storage=st, variant=variant)
         G.step(30)
         G.sync()
         total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
         kern_ms = plain_ms / nplain
         bpn = bytes_per_node(st, True, 0)
-        key = f"mhd_duct_128_{st}" + ("_one_node_per_thread" if variant == 1 else "")
+        key = f"mhd_duct_128_{st}" + ("_paired" if variant == 2 else "")
         out[key] = {"mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
                     "bytes_per_node": bpn, "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
         G.close()
@@ -361,7 +362,7 @@ def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
 
 def time_to_solution():
     """Wall time to r <= 1e-8 on the 64x64x8 Hartmann duct (Pr_m = 0.01,
-    nu = eta = 0.01, Ha = 5, 10, 20) at gamma = gamma_m = 0.1 and 1, same
+    nu = eta = 0.01, Ha = 5, 10, 20) at gamma = gamma_m = 0.05, 0.1 and 1, same
     GPU, FP32 arithmetic with compensated (F32C) storage, with the error of
     the converged u against the analytic profile."""
     import torch
@@ -372,7 +373,7 @@ def time_to_solution():
         B0 = Ha * math.sqrt(nu * eta) / 31.0
         ua = hartmann_analytic(64, Ha)
         r_ha = {}
-        for gamma in (0.1, 1.0):
+        for gamma in (0.05, 0.1, 1.0):
             G = Solver(64, 64, 8, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
                        induction=1, gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0), storage="f32c")
             torch.cuda.synchronize()
@@ -386,9 +387,11 @@ def time_to_solution():
             r_ha[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r, "wall_s": round(t1 - t0, 4),
                                       "err_vs_analytic": err}
             G.close()
-        a, b = r_ha["gamma_0.1"], r_ha["gamma_1.0"]
-        r_ha["speedup_wall"] = round(b["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
-        r_ha["speedup_steps"] = round(b["steps"] / max(1, a["steps"]), 2)
+        b = r_ha["gamma_1.0"]
+        for g in ("0.1", "0.05"):
+            a = r_ha[f"gamma_{g}"]
+            r_ha[f"speedup_wall_gamma_{g}"] = round(b["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
+            r_ha[f"speedup_steps_gamma_{g}"] = round(b["steps"] / max(1, a["steps"]), 2)
         res[f"Ha_{int(Ha)}"] = r_ha
     return res
 

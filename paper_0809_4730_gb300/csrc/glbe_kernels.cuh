@@ -1031,15 +1031,14 @@ __global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParam
     if (MODE == MODE_STEP_RESID) block_partials<PAIR_THREADS>(acc, b.partials);
 }
 
-// The paired kernel serves x-periodic grids with an even nx.  The automatic
-// choice keeps the compensated storage on one node per thread (two nodes
-// with their low parts exceed the register file).
+// The paired kernel serves x-periodic grids with an even nx when asked for
+// (variant 2).  The automatic choice is one node per thread: measured on
+// GB300 the paired form runs 1.2-1.4x slower (its register footprint halves
+// the resident warps).
 inline bool pair_eligible(const StepParams& p)
 {
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0]) return false;
-    if (p.variant == 1) return false;
-    if (p.variant == 2) return true;
-    return p.storage != ST_F32C;
+    return p.variant == 2;
 }
 
 // ---------------------------------------------------------------------------
