@@ -218,6 +218,75 @@ void glbe_destroy(glbe_ctx* ctx);
 glbe_status glbe_step_residual_noalloc(const glbe_params* p, const void* d_src, void* d_dst, const float* d_force,
                                        float* d_u, int have_prev, long t, glbe_residual_info* out);
 
+/* ------------------------------------------------------------------------ */
+/* Batched steady solves: many independent lattices (own grid, walls, gamma, */
+/* rates, with or without the induction lattice) marched together by one    */
+/* persistent cooperative kernel (one node per thread over a flattened tile  */
+/* list, a bounded grid barrier between steps), launched from a CUDA graph.  */
+/* Every 10 levels each domain's residual is reduced in a fixed order; a     */
+/* domain whose r(t) <= tol leaves the march with its level and the device   */
+/* time since the start of the launch.  Storage F32 or F32C, uniform force.  */
+/* ------------------------------------------------------------------------ */
+#define GLBE_BATCH_MAX_DOMAINS 4096
+
+typedef struct glbe_batch glbe_batch;
+
+typedef struct {
+    int converged;            /* 1: r(t) <= tol was reached                      */
+    long steps;               /* level t of that residual (-1 if not converged) */
+    double r;                 /* last residual of the domain                     */
+    double seconds;           /* device time from the start of the launch to the
+                                 domain's convergence (-1 if not converged)      */
+    int nonfinite;            /* 1: the domain's velocity became NaN/Inf         */
+} glbe_batch_result;
+
+/* Workspace bytes for n domains (each glbe_params as for glbe_init; the
+ * stream field is ignored, force_field must be 0, all domains share one
+ * storage type, F32 or F32C). */
+glbe_status glbe_batch_workspace_bytes(const glbe_params* domains, int n, size_t* bytes);
+
+/* Creates a batch on a caller-owned, 256-byte aligned workspace and sets every
+ * domain to the rest state.  stream: cudaStream_t for all batch work.
+ * Synchronises the stream. */
+glbe_status glbe_batch_init(const glbe_params* domains, int n, void* d_workspace, size_t bytes, void* stream,
+                            glbe_batch** out);
+
+/* Launch shape of the persistent kernel: block_threads 128 or 256 (also the
+ * tile size), blocks_per_sm from 1 to the occupancy limit. */
+glbe_status glbe_batch_set_launch(glbe_batch* b, int block_threads, int blocks_per_sm);
+
+/* Times steps_per_trial steps for every (block_threads, blocks_per_sm)
+ * candidate on the batch itself, keeps the fastest and restores the rest
+ * state.  Outputs may be NULL. */
+glbe_status glbe_batch_autotune(glbe_batch* b, int steps_per_trial, int* block_threads, int* blocks_per_sm,
+                                double* seconds_per_step);
+
+/* Marches all domains from the rest state until each has r(t) <= tol or
+ * max_steps levels have been taken, in one persistent launch (captured in a
+ * CUDA graph when use_graph != 0).  results[n]; *seconds = device time of the
+ * whole launch (may be NULL).  GLBE_ERR_TIMEOUT if some domain did not
+ * converge or the grid barrier timed out, GLBE_ERR_DIVERGED on NaN/Inf,
+ * GLBE_ERR_STATE if the batch was already solved (see glbe_batch_reset).
+ * Synchronises the stream. */
+glbe_status glbe_batch_solve(glbe_batch* b, double tol, long max_steps, int use_graph, glbe_batch_result* results,
+                             double* seconds);
+
+/* Macroscopic fields of domain d after a solve (layout as glbe_fields). */
+glbe_status glbe_batch_fields(glbe_batch* b, int d, float* d_rho, float* d_u, float* d_B);
+
+/* Returns every domain to the rest state for a new solve. */
+glbe_status glbe_batch_reset(glbe_batch* b);
+
+/* Failure detection: every wait of the batch's grid barrier gives up after
+ * spin_limit polls (default 2^26, about 4 s), sets an error flag and ends the
+ * launch (glbe_batch_solve then returns GLBE_ERR_TIMEOUT).  absent_block >= 0
+ * makes that block leave the launch at once so that tests can drive the wait
+ * to its limit without faulting or hanging the GPU; -1 (default) disables it. */
+glbe_status glbe_batch_set_barrier_test(glbe_batch* b, long long spin_limit, int absent_block);
+
+/* Frees the host-side batch (not the workspace). NULL is ignored. */
+void glbe_batch_destroy(glbe_batch* b);
+
 /* ABI version of the loaded library (GLBE_ABI_VERSION). */
 int glbe_abi_version(void);
 

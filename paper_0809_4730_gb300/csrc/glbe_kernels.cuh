@@ -152,6 +152,27 @@ template <> struct Store<ST_F32C> {
     }
 };
 
+// Loads of populations written earlier in the same launch (the persistent
+// batch kernel) must not use the non-coherent read-only path: CG = true reads
+// through L2 (ld.global.cg).
+template <int ST, bool CG>
+__device__ __forceinline__ float ldp(const typename Store<ST>::T* p)
+{
+    if constexpr (CG) {
+        if constexpr (ST == ST_BF16) return __bfloat162float(__ldcg(p));
+        else if constexpr (ST == ST_F16) return __half2float(__ldcg(p));
+        else return __ldcg(p);
+    } else {
+        return Store<ST>::ld(p);
+    }
+}
+template <bool CG>
+__device__ __forceinline__ float ldlo(const __half* p)
+{
+    if constexpr (CG) return __half2float(__ldcg(p)) * LO_INV;
+    else return Store<ST_F32C>::ld_lo(p);
+}
+
 template <int ST>
 __device__ __forceinline__ float unscale(const StepParams& p, float v) { return Store<ST>::SCALED ? v * p.inv_scale : v; }
 template <int ST>
@@ -317,20 +338,20 @@ __device__ __forceinline__ GeoP make_geo_pair(const StepParams& p, uint32_t n0)
 // ---------------------------------------------------------------------------
 // Gathers
 // ---------------------------------------------------------------------------
-template <int ST>
+template <int ST, bool CG = false>
 __device__ __forceinline__ void load_f(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
                                        const Geo& g, float (&d)[19], float (&l)[19])
 {
     const size_t N = p.N;
 #define GLBE_SRCF(a, o, src, sol) ((sol) ? (size_t)(o) * N + g.n : (size_t)(a) * N + (src))
-#define GLBE_LOADF(a, o, src, sol) d[a] = unscale<ST>(p, Store<ST>::ld(fs + GLBE_SRCF(a, o, src, sol)));
-    d[0] = unscale<ST>(p, Store<ST>::ld(fs + g.n));
+#define GLBE_LOADF(a, o, src, sol) d[a] = unscale<ST>(p, ldp<ST, CG>(fs + GLBE_SRCF(a, o, src, sol)));
+    d[0] = unscale<ST>(p, ldp<ST, CG>(fs + g.n));
     GLBE_DIRS(GLBE_LOADF)
 #undef GLBE_LOADF
     if constexpr (Store<ST>::COMP) {
         const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * N);
-#define GLBE_LOADL(a, o, src, sol) l[a] = Store<ST>::ld_lo(fl + GLBE_SRCF(a, o, src, sol));
-        l[0] = Store<ST>::ld_lo(fl + g.n);
+#define GLBE_LOADL(a, o, src, sol) l[a] = ldlo<CG>(fl + GLBE_SRCF(a, o, src, sol));
+        l[0] = ldlo<CG>(fl + g.n);
         GLBE_DIRS(GLBE_LOADL)
 #undef GLBE_LOADL
     }
@@ -341,7 +362,7 @@ __device__ __forceinline__ void load_f(const StepParams& p, const typename Store
 // i.e. for deviations dg_a = -dg~_abar + 2 W_a (B_wall - B0).  In the
 // compensated form the low part is negated with the high part (exact when
 // B_wall = B0, the only case the C-ABI exposes).
-template <int ST>
+template <int ST, bool CG = false>
 __device__ __forceinline__ void load_g(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
                                        const Geo& g, float (&q)[21], float (&ql)[21])
 {
@@ -350,51 +371,55 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     for (int j = 0; j < 3; ++j) {
         const typename Store<ST>::T* __restrict__ b = gs + (size_t)(j * 7) * N;
         const float wall = 0.25f * p.bwall_dev[j];   // 2 W_a (B_wall - B0), W_a = 1/8
-        q[j * 7 + 0] = unscale<ST>(p, Store<ST>::ld(b + g.n));
+        q[j * 7 + 0] = unscale<ST>(p, ldp<ST, CG>(b + g.n));
 #define GLBE_LOADG(a, o, src, sol)                                                               \
-    q[j * 7 + a] = (sol) ? (wall - unscale<ST>(p, Store<ST>::ld(b + (size_t)(o) * N + g.n)))    \
-                         : unscale<ST>(p, Store<ST>::ld(b + (size_t)(a) * N + (src)));
+    q[j * 7 + a] = (sol) ? (wall - unscale<ST>(p, ldp<ST, CG>(b + (size_t)(o) * N + g.n)))      \
+                         : unscale<ST>(p, ldp<ST, CG>(b + (size_t)(a) * N + (src)));
         GLBE_DIRS7(GLBE_LOADG)
 #undef GLBE_LOADG
         if constexpr (Store<ST>::COMP) {
             const __half* __restrict__ bl = reinterpret_cast<const __half*>(gs + 21 * N) + (size_t)(j * 7) * N;
-            ql[j * 7 + 0] = Store<ST>::ld_lo(bl + g.n);
+            ql[j * 7 + 0] = ldlo<CG>(bl + g.n);
 #define GLBE_LOADGL(a, o, src, sol)                                             \
-    ql[j * 7 + a] = (sol) ? -Store<ST>::ld_lo(bl + (size_t)(o) * N + g.n)       \
-                          : Store<ST>::ld_lo(bl + (size_t)(a) * N + (src));
+    ql[j * 7 + a] = (sol) ? -ldlo<CG>(bl + (size_t)(o) * N + g.n)              \
+                          : ldlo<CG>(bl + (size_t)(a) * N + (src));
             GLBE_DIRS7(GLBE_LOADGL)
 #undef GLBE_LOADGL
         }
     }
 }
 
-// One population of a pair: the two sources of direction a with x-shift ex
-// from row `row` (solid: bounce-back from the own row's opposite slot o).
-// ex = 0: one aligned pair.  ex = +1: node x0 needs x0 - 1 (the left lane's
-// pair, or an own load at a warp or row start), node x0 + 1 needs x0.
-// ex = -1: node x0 needs x0 + 1, node x0 + 1 needs x0 + 2 (the right lane's
-// pair, or an own load at a warp or row end).  Every lane executes the
-// shuffles; bounced rows never use them.
-template <class LD2, class LD1>
-__device__ __forceinline__ F2 pair_gather(const GeoP& q, size_t base_a, size_t base_o, uint32_t row, bool sol,
-                                          int ex, LD2 ld2, LD1 ld1)
-{
-    const Geo& g = q.g;
-    const F2 v = sol ? ld2(base_o + g.r00 + (uint32_t)g.x) : ld2(base_a + row + (uint32_t)g.x);
-    if (ex > 0) {
-        const float t = __shfl_up_sync(0xffffffffu, v.v.y, 1);
-        if (sol) return v;
-        const float left = q.left_own ? ld1(base_a + row + (uint32_t)q.xl) : t;
-        return F2(left, v.v.x);
+// Gathers of a pair, in two phases so that every load -- including the edge
+// values a warp's first and last lanes and the lanes at a row start or end
+// fetch for themselves -- is issued before any lane shuffle:
+//   phase A: per direction a (x-shift ex, source row `row`, bounced if sol)
+//     v = the aligned pair at x0 of the source row (or the own row's
+//     opposite slot o when bounced) and, for ex = +1 / -1, the own value at
+//     x0 - 1 / x0 + 2 where the neighbouring lane does not hold it;
+//   phase B: ex = +1: node x0 takes x0 - 1 (left lane's pair or own load),
+//     node x0 + 1 takes x0; ex = -1: node x0 takes x0 + 1, node x0 + 1 takes
+//     x0 + 2 (right lane's pair or own load).  Every lane executes the
+//     shuffles; bounced rows never use them.
+#define GLBE_PAIR_PHASE_A(V, E, a, o, row, sol, ex, LD2, LD1, BASE)                                        \
+    {                                                                                                      \
+        const size_t ia_ = (BASE) + (size_t)(a) * N + (row) + (uint32_t)g.x;                               \
+        const size_t io_ = (BASE) + (size_t)(o) * N + g.r00 + (uint32_t)g.x;                               \
+        V[a] = (sol) ? LD2(io_) : LD2(ia_);                                                                \
+        if ((ex) > 0) E[a] = (!(sol) && q.left_own) ? LD1((BASE) + (size_t)(a) * N + (row) + (uint32_t)q.xl) : 0.f; \
+        if ((ex) < 0) E[a] = (!(sol) && q.right_own) ? LD1((BASE) + (size_t)(a) * N + (row) + (uint32_t)q.xr) : 0.f; \
     }
-    if (ex < 0) {
-        const float t = __shfl_down_sync(0xffffffffu, v.v.x, 1);
-        if (sol) return v;
-        const float right = q.right_own ? ld1(base_a + row + (uint32_t)q.xr) : t;
-        return F2(v.v.y, right);
+#define GLBE_PAIR_PHASE_B(OUT, V, E, a, sol, ex)                                                           \
+    {                                                                                                      \
+        if ((ex) > 0) {                                                                                    \
+            const float t_ = __shfl_up_sync(0xffffffffu, V[a].v.y, 1);                                     \
+            OUT[a] = (sol) ? V[a] : F2(q.left_own ? E[a] : t_, V[a].v.x);                                  \
+        } else if ((ex) < 0) {                                                                             \
+            const float t_ = __shfl_down_sync(0xffffffffu, V[a].v.x, 1);                                   \
+            OUT[a] = (sol) ? V[a] : F2(V[a].v.y, q.right_own ? E[a] : t_);                                 \
+        } else {                                                                                           \
+            OUT[a] = V[a];                                                                                 \
+        }                                                                                                  \
     }
-    return v;
-}
 
 template <int ST>
 __device__ __forceinline__ void load_f_pair(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
@@ -405,19 +430,27 @@ __device__ __forceinline__ void load_f_pair(const StepParams& p, const typename 
     const Geo& g = q.g;
     auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(fs + i)); };
     auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(fs + i)); };
+    float e[19];
     d[0] = ld2((size_t)g.r00 + (uint32_t)g.x);
-#define GLBE_PLOADF(a, o, row, sol, ex) d[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, ld2, ld1);
-    GLBE_PDIRS(GLBE_PLOADF)
-#undef GLBE_PLOADF
+#define GLBE_PA(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(d, e, a, o, row, sol, ex, ld2, ld1, (size_t)0)
+    GLBE_PDIRS(GLBE_PA)
+#undef GLBE_PA
     if constexpr (S::COMP) {
         const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * N);
         auto lo2 = [&](size_t i) { return S::ld2_lo(fl + i); };
         auto lo1 = [&](size_t i) { return S::ld_lo(fl + i); };
+        float el[19];
         l[0] = lo2((size_t)g.r00 + (uint32_t)g.x);
-#define GLBE_PLOADL(a, o, row, sol, ex) l[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, lo2, lo1);
-        GLBE_PDIRS(GLBE_PLOADL)
-#undef GLBE_PLOADL
+#define GLBE_PAL(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(l, el, a, o, row, sol, ex, lo2, lo1, (size_t)0)
+        GLBE_PDIRS(GLBE_PAL)
+#undef GLBE_PAL
+#define GLBE_PBL(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(l, l, el, a, sol, ex)
+        GLBE_PDIRS(GLBE_PBL)
+#undef GLBE_PBL
     }
+#define GLBE_PB(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(d, d, e, a, sol, ex)
+    GLBE_PDIRS(GLBE_PB)
+#undef GLBE_PB
 }
 
 template <int ST>
@@ -429,30 +462,52 @@ __device__ __forceinline__ void load_g_pair(const StepParams& p, const typename 
     const Geo& g = q.g;
     auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(gs + i)); };
     auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(gs + i)); };
+    F2 w[3][7];
+    float e[3][7];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const size_t jb = (size_t)(j * 7) * N;
+        w[j][0] = ld2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PAG(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(w[j], e[j], a, o, row, sol, ex, ld2, ld1, jb)
+        GLBE_PDIRS7(GLBE_PAG)
+#undef GLBE_PAG
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
         const F2 wall(0.25f * p.bwall_dev[j]);
-        v[j * 7] = ld2(jb + g.r00 + (uint32_t)g.x);
-#define GLBE_PLOADG(a, o, row, sol, ex)                                                              \
-    {                                                                                                \
-        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, ld2, ld1); \
-        v[j * 7 + a] = (sol) ? wall - t_ : t_;                                                       \
+        F2 t[7];
+        t[0] = w[j][0];
+#define GLBE_PBG(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(t, w[j], e[j], a, sol, ex)
+        GLBE_PDIRS7(GLBE_PBG)
+#undef GLBE_PBG
+        v[j * 7] = t[0];
+#define GLBE_WALLG(a, o, row, sol, ex) v[j * 7 + a] = (sol) ? wall - t[a] : t[a];
+        GLBE_PDIRS7(GLBE_WALLG)
+#undef GLBE_WALLG
     }
-        GLBE_PDIRS7(GLBE_PLOADG)
-#undef GLBE_PLOADG
-        if constexpr (S::COMP) {
-            const __half* __restrict__ gl = reinterpret_cast<const __half*>(gs + 21 * N);
-            auto lo2 = [&](size_t i) { return S::ld2_lo(gl + i); };
-            auto lo1 = [&](size_t i) { return S::ld_lo(gl + i); };
-            vl[j * 7] = lo2(jb + g.r00 + (uint32_t)g.x);
-#define GLBE_PLOADGL(a, o, row, sol, ex)                                                              \
-    {                                                                                                 \
-        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, lo2, lo1); \
-        vl[j * 7 + a] = (sol) ? -t_ : t_;                                                             \
-    }
-            GLBE_PDIRS7(GLBE_PLOADGL)
-#undef GLBE_PLOADGL
+    if constexpr (S::COMP) {
+        const __half* __restrict__ gl = reinterpret_cast<const __half*>(gs + 21 * N);
+        auto lo2 = [&](size_t i) { return S::ld2_lo(gl + i); };
+        auto lo1 = [&](size_t i) { return S::ld_lo(gl + i); };
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const size_t jb = (size_t)(j * 7) * N;
+            w[j][0] = lo2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PAGL(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(w[j], e[j], a, o, row, sol, ex, lo2, lo1, jb)
+            GLBE_PDIRS7(GLBE_PAGL)
+#undef GLBE_PAGL
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            F2 t[7];
+            t[0] = w[j][0];
+#define GLBE_PBGL(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(t, w[j], e[j], a, sol, ex)
+            GLBE_PDIRS7(GLBE_PBGL)
+#undef GLBE_PBGL
+            vl[j * 7] = t[0];
+#define GLBE_NEGL(a, o, row, sol, ex) vl[j * 7 + a] = (sol) ? -t[a] : t[a];
+            GLBE_PDIRS7(GLBE_NEGL)
+#undef GLBE_NEGL
         }
     }
 }
@@ -833,104 +888,111 @@ __device__ __forceinline__ void block_partials(float (&acc)[7], double* partials
 // ---------------------------------------------------------------------------
 // Scalar kernel: one node per thread, any geometry
 // ---------------------------------------------------------------------------
-template <int ST, bool MHD, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
+// The update of node n (i < N) by one thread; accumulates the residual terms
+// of MODE_STEP_RESID into acc.  Returns without work for solid nodes.
+template <int ST, bool MHD, int MODE, bool CG = false>
+__device__ __forceinline__ void scalar_node_step(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                                                 uint32_t i, float (&acc)[7])
 {
     using S = Store<ST>;
     using T = typename S::T;
-    if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
-    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     const bool inb = i < p.N;
     const uint32_t n = inb ? i : 0u;
     const Geo g = make_geo(p, n);
     const bool fluid = inb && !g.solid;
     const size_t N = p.N;
-
-    if (MODE == MODE_STEP && !fluid) return;
-    if (MODE == MODE_FIELDS && !inb) return;
-
-    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (fluid) {
-        float d[19], dl[19], q[21], ql[21];
-        load_f<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
-        float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
-        if (MHD) {
-            load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q, ql);
-            FLpx = b.FL[n];
-            FLpy = b.FL[N + n];
-            FLpz = b.FL[2 * N + n];
+    if (!fluid) {
+        if (MODE == MODE_FIELDS && inb) {
+            if (fo.rho) fo.rho[n] = 0.f;
+            if (fo.u) { fo.u[n] = 0.f; fo.u[N + n] = 0.f; fo.u[2 * N + n] = 0.f; }
+            if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
         }
-        float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
-        if (p.force_ncomp >= 1) Fx += __ldg(b.Ffield + n);
-        if (p.force_ncomp == 3) {
-            Fy += __ldg(b.Ffield + N + n);
-            Fz += __ldg(b.Ffield + 2 * N + n);
-        }
-        float om[19], og[21];
-        NodeState<float> ns;
-        node_update<float, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, MODE != MODE_FIELDS, om, og, ns);
+        return;
+    }
+    float d[19], dl[19], q[21], ql[21];
+    load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+    float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
+    if (MHD) {
+        load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
+        FLpx = b.FL[n];
+        FLpy = b.FL[N + n];
+        FLpz = b.FL[2 * N + n];
+    }
+    float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
+    if (p.force_ncomp >= 1) Fx += __ldg(b.Ffield + n);
+    if (p.force_ncomp == 3) {
+        Fy += __ldg(b.Ffield + N + n);
+        Fz += __ldg(b.Ffield + 2 * N + n);
+    }
+    float om[19], og[21];
+    NodeState<float> ns;
+    node_update<float, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, MODE != MODE_FIELDS, om, og, ns);
 
-        if (MODE == MODE_FIELDS) {
-            if (fo.rho) fo.rho[n] = ns.rho;
-            if (fo.u) { fo.u[n] = ns.ux; fo.u[N + n] = ns.uy; fo.u[2 * N + n] = ns.uz; }
-            if (MHD && fo.B) { fo.B[n] = ns.mac.Bx; fo.B[N + n] = ns.mac.By; fo.B[2 * N + n] = ns.mac.Bz; }
-            return;
-        }
-        // f~ = f + om, written to the node's own slot of the other buffer
-        T* __restrict__ fd = static_cast<T*>(b.fdst);
-        if constexpr (S::COMP) {
-            __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
+    if (MODE == MODE_FIELDS) {
+        if (fo.rho) fo.rho[n] = ns.rho;
+        if (fo.u) { fo.u[n] = ns.ux; fo.u[N + n] = ns.uy; fo.u[2 * N + n] = ns.uz; }
+        if (MHD && fo.B) { fo.B[n] = ns.mac.Bx; fo.B[N + n] = ns.mac.By; fo.B[2 * N + n] = ns.mac.Bz; }
+        return;
+    }
+    // f~ = f + om, written to the node's own slot of the other buffer
+    T* __restrict__ fd = static_cast<T*>(b.fdst);
+    if constexpr (S::COMP) {
+        __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
 #pragma unroll
-            for (int a = 0; a < 19; ++a) {
+        for (int a = 0; a < 19; ++a) {
+            float nh, nl;
+            comp_add(d[a], dl[a], om[a], nh, nl);
+            fd[(size_t)a * N + n] = nh;
+            fdl[(size_t)a * N + n] = S::cv_lo(nl);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, d[a] + om[a]));
+    }
+    if (MHD) {
+        T* __restrict__ gd = static_cast<T*>(b.gdst);
+        if constexpr (S::COMP) {
+            __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
+#pragma unroll
+            for (int a = 0; a < 21; ++a) {
                 float nh, nl;
-                comp_add(d[a], dl[a], om[a], nh, nl);
-                fd[(size_t)a * N + n] = nh;
-                fdl[(size_t)a * N + n] = S::cv_lo(nl);
+                comp_add(q[a], ql[a], og[a], nh, nl);
+                gd[(size_t)a * N + n] = nh;
+                gdl[(size_t)a * N + n] = S::cv_lo(nl);
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, d[a] + om[a]));
+            for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv(toscale<ST>(p, q[a] + og[a]));
         }
-        if (MHD) {
-            T* __restrict__ gd = static_cast<T*>(b.gdst);
-            if constexpr (S::COMP) {
-                __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
-#pragma unroll
-                for (int a = 0; a < 21; ++a) {
-                    float nh, nl;
-                    comp_add(q[a], ql[a], og[a], nh, nl);
-                    gd[(size_t)a * N + n] = nh;
-                    gdl[(size_t)a * N + n] = S::cv_lo(nl);
-                }
-            } else {
-#pragma unroll
-                for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv(toscale<ST>(p, q[a] + og[a]));
-            }
-            b.FL[n] = ns.mac.FLx;
-            b.FL[N + n] = ns.mac.FLy;
-            b.FL[2 * N + n] = ns.mac.FLz;
-        }
-        if (MODE == MODE_STEP_RESID) {
-            if (b.have_snap) {
-                const float dx = ns.ux - b.usnap[n], dy = ns.uy - b.usnap[N + n], dz = ns.uz - b.usnap[2 * N + n];
-                acc[0] = dx * dx + dy * dy + dz * dz;
-            }
-            acc[1] = ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
-            acc[2] = ns.drho;              // the mass is rho0 * (fluid nodes) + sum drho
-            acc[3] = ns.jx;
-            acc[4] = ns.jy;
-            acc[5] = ns.jz;
-            acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
-            b.usnap[n] = ns.ux;
-            b.usnap[N + n] = ns.uy;
-            b.usnap[2 * N + n] = ns.uz;
-        }
-    } else if (MODE == MODE_FIELDS) {
-        if (fo.rho) fo.rho[n] = 0.f;
-        if (fo.u) { fo.u[n] = 0.f; fo.u[N + n] = 0.f; fo.u[2 * N + n] = 0.f; }
-        if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
-        return;
+        b.FL[n] = ns.mac.FLx;
+        b.FL[N + n] = ns.mac.FLy;
+        b.FL[2 * N + n] = ns.mac.FLz;
     }
+    if (MODE == MODE_STEP_RESID) {
+        if (b.have_snap) {
+            const float dx = ns.ux - b.usnap[n], dy = ns.uy - b.usnap[N + n], dz = ns.uz - b.usnap[2 * N + n];
+            acc[0] = dx * dx + dy * dy + dz * dz;
+        }
+        acc[1] = ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
+        acc[2] = ns.drho;              // the mass is rho0 * (fluid nodes) + sum drho
+        acc[3] = ns.jx;
+        acc[4] = ns.jy;
+        acc[5] = ns.jz;
+        acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
+        b.usnap[n] = ns.ux;
+        b.usnap[N + n] = ns.uy;
+        b.usnap[2 * N + n] = ns.uz;
+    }
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
+    scalar_node_step<ST, MHD, MODE>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 

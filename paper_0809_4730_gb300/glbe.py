@@ -49,6 +49,11 @@ class glbe_residual_info(C.Structure):
     ]
 
 
+class glbe_batch_result(C.Structure):
+    _fields_ = [("converged", C.c_int), ("steps", C.c_long), ("r", C.c_double), ("seconds", C.c_double),
+                ("nonfinite", C.c_int)]
+
+
 # Every symbol include/glbe.h declares, with (restype, argtypes).
 _P = C.POINTER
 _SIGNATURES = {
@@ -70,6 +75,16 @@ _SIGNATURES = {
     "glbe_destroy": (None, [C.c_void_p]),
     "glbe_abi_version": (C.c_int, []),
     "glbe_struct_sizes": (None, [_P(C.c_size_t), _P(C.c_size_t)]),
+    "glbe_batch_workspace_bytes": (C.c_int, [_P(glbe_params), C.c_int, _P(C.c_size_t)]),
+    "glbe_batch_init": (C.c_int, [_P(glbe_params), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, _P(C.c_void_p)]),
+    "glbe_batch_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "glbe_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, _P(C.c_int), _P(C.c_int), _P(C.c_double)]),
+    "glbe_batch_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_long, C.c_int, _P(glbe_batch_result),
+                                   _P(C.c_double)]),
+    "glbe_batch_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "glbe_batch_reset": (C.c_int, [C.c_void_p]),
+    "glbe_batch_set_barrier_test": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int]),
+    "glbe_batch_destroy": (None, [C.c_void_p]),
     "glbe_step_residual_noalloc": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_int, C.c_long, _P(glbe_residual_info)]),
 }
@@ -211,6 +226,98 @@ def glbe_step_residual_noalloc(p: glbe_params, d_src, d_dst, d_force, d_u, have_
 def glbe_destroy(ctx):
     if ctx:
         load().glbe_destroy(ctx)
+
+
+def make_params(nx, ny, nz, **kw) -> glbe_params:
+    """glbe_params from keyword arguments named as its fields (storage may be
+    "f32", "bf16", "f16" or "f32c"; s overrides the 19 rates)."""
+    p = glbe_params_default()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    for key, val in kw.items():
+        if key in ("wall_lo", "wall_hi", "F", "B0"):
+            arr = getattr(p, key)
+            for d in range(3):
+                arr[d] = type(arr[d])(val[d])
+        elif key == "s":
+            for k in range(19):
+                p.s[k] = float(val[k])
+        elif key == "storage":
+            p.storage = STORAGE[val] if isinstance(val, str) else int(val)
+        elif key in ("induction", "force_field", "variant"):
+            setattr(p, key, int(val))
+        else:
+            setattr(p, key, float(val))
+    return p
+
+
+class Batch:
+    """Many independent steady solves in one persistent launch (see
+    glbe_batch_* in include/glbe.h).  domains: list of glbe_params."""
+
+    def __init__(self, domains, *, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = len(domains)
+        self.domains = domains
+        arr = (glbe_params * self.n)(*domains)
+        self._arr = arr
+        nb = C.c_size_t(0)
+        _check(load().glbe_batch_workspace_bytes(arr, self.n, C.byref(nb)), "glbe_batch_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self.ptr = C.c_void_p()
+        _check(load().glbe_batch_init(arr, self.n, _ptr(self.workspace), nb.value,
+                                      C.c_void_p(self.stream.cuda_stream), C.byref(self.ptr)), "glbe_batch_init")
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().glbe_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, block_threads: int, blocks_per_sm: int):
+        _check(load().glbe_batch_set_launch(self.ptr, int(block_threads), int(blocks_per_sm)),
+               "glbe_batch_set_launch")
+
+    def autotune(self, steps_per_trial: int = 20):
+        bt, bps, sps = C.c_int(0), C.c_int(0), C.c_double(0.0)
+        _check(load().glbe_batch_autotune(self.ptr, int(steps_per_trial), C.byref(bt), C.byref(bps), C.byref(sps)),
+               "glbe_batch_autotune")
+        return bt.value, bps.value, sps.value
+
+    def solve(self, tol: float, max_steps: int, use_graph: bool = True):
+        res = (glbe_batch_result * self.n)()
+        sec = C.c_double(0.0)
+        st = load().glbe_batch_solve(self.ptr, float(tol), int(max_steps), int(bool(use_graph)), res,
+                                     C.byref(sec))
+        if st not in (GLBE_OK, GLBE_ERR_TIMEOUT):
+            _check(st, "glbe_batch_solve")
+        out = [dict(converged=bool(r.converged), steps=r.steps, r=r.r, seconds=r.seconds,
+                    nonfinite=bool(r.nonfinite)) for r in res]
+        return st, out, sec.value
+
+    def fields(self, d: int):
+        torch = self.torch
+        p = self.domains[d]
+        N = p.nx * p.ny * p.nz
+        rho = torch.empty(N, dtype=torch.float32, device=self.device)
+        u = torch.empty(3, N, dtype=torch.float32, device=self.device)
+        B = torch.empty(3, N, dtype=torch.float32, device=self.device) if p.induction else None
+        _check(load().glbe_batch_fields(self.ptr, int(d), _ptr(rho), _ptr(u), _ptr(B)), "glbe_batch_fields")
+        return rho, u, B
+
+    def reset(self):
+        _check(load().glbe_batch_reset(self.ptr), "glbe_batch_reset")
+
+    def set_barrier_test(self, spin_limit: int, absent_block: int):
+        _check(load().glbe_batch_set_barrier_test(self.ptr, int(spin_limit), int(absent_block)),
+               "glbe_batch_set_barrier_test")
 
 
 # ---------------------------------------------------------------------------
