@@ -389,37 +389,33 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     }
 }
 
-// Gathers of a pair, in two phases so that every load -- including the edge
-// values a warp's first and last lanes and the lanes at a row start or end
-// fetch for themselves -- is issued before any lane shuffle:
-//   phase A: per direction a (x-shift ex, source row `row`, bounced if sol)
-//     v = the aligned pair at x0 of the source row (or the own row's
-//     opposite slot o when bounced) and, for ex = +1 / -1, the own value at
-//     x0 - 1 / x0 + 2 where the neighbouring lane does not hold it;
-//   phase B: ex = +1: node x0 takes x0 - 1 (left lane's pair or own load),
-//     node x0 + 1 takes x0; ex = -1: node x0 takes x0 + 1, node x0 + 1 takes
-//     x0 + 2 (right lane's pair or own load).  Every lane executes the
-//     shuffles; bounced rows never use them.
-#define GLBE_PAIR_PHASE_A(V, E, a, o, row, sol, ex, LD2, LD1, BASE)                                        \
-    {                                                                                                      \
-        const size_t ia_ = (BASE) + (size_t)(a) * N + (row) + (uint32_t)g.x;                               \
-        const size_t io_ = (BASE) + (size_t)(o) * N + g.r00 + (uint32_t)g.x;                               \
-        V[a] = (sol) ? LD2(io_) : LD2(ia_);                                                                \
-        if ((ex) > 0) E[a] = (!(sol) && q.left_own) ? LD1((BASE) + (size_t)(a) * N + (row) + (uint32_t)q.xl) : 0.f; \
-        if ((ex) < 0) E[a] = (!(sol) && q.right_own) ? LD1((BASE) + (size_t)(a) * N + (row) + (uint32_t)q.xr) : 0.f; \
+// One population of a pair: the two sources of direction a with x-shift ex
+// from row `row` (solid: bounce-back from the own row's opposite slot o).
+// ex = 0: one aligned pair.  ex = +1: node x0 needs x0 - 1 (the left lane's
+// pair, or an own load at a warp or row start), node x0 + 1 needs x0.
+// ex = -1: node x0 needs x0 + 1, node x0 + 1 needs x0 + 2 (the right lane's
+// pair, or an own load at a warp or row end).  Every lane executes the
+// shuffles; bounced rows never use them.
+template <class LD2, class LD1>
+__device__ __forceinline__ F2 pair_gather(const GeoP& q, size_t base_a, size_t base_o, uint32_t row, bool sol,
+                                          int ex, LD2 ld2, LD1 ld1)
+{
+    const Geo& g = q.g;
+    const F2 v = sol ? ld2(base_o + g.r00 + (uint32_t)g.x) : ld2(base_a + row + (uint32_t)g.x);
+    if (ex > 0) {
+        const float t = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+        if (sol) return v;
+        const float left = q.left_own ? ld1(base_a + row + (uint32_t)q.xl) : t;
+        return F2(left, v.v.x);
     }
-#define GLBE_PAIR_PHASE_B(OUT, V, E, a, sol, ex)                                                           \
-    {                                                                                                      \
-        if ((ex) > 0) {                                                                                    \
-            const float t_ = __shfl_up_sync(0xffffffffu, V[a].v.y, 1);                                     \
-            OUT[a] = (sol) ? V[a] : F2(q.left_own ? E[a] : t_, V[a].v.x);                                  \
-        } else if ((ex) < 0) {                                                                             \
-            const float t_ = __shfl_down_sync(0xffffffffu, V[a].v.x, 1);                                   \
-            OUT[a] = (sol) ? V[a] : F2(V[a].v.y, q.right_own ? E[a] : t_);                                 \
-        } else {                                                                                           \
-            OUT[a] = V[a];                                                                                 \
-        }                                                                                                  \
+    if (ex < 0) {
+        const float t = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+        if (sol) return v;
+        const float right = q.right_own ? ld1(base_a + row + (uint32_t)q.xr) : t;
+        return F2(v.v.y, right);
     }
+    return v;
+}
 
 template <int ST>
 __device__ __forceinline__ void load_f_pair(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
@@ -430,27 +426,19 @@ __device__ __forceinline__ void load_f_pair(const StepParams& p, const typename 
     const Geo& g = q.g;
     auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(fs + i)); };
     auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(fs + i)); };
-    float e[19];
     d[0] = ld2((size_t)g.r00 + (uint32_t)g.x);
-#define GLBE_PA(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(d, e, a, o, row, sol, ex, ld2, ld1, (size_t)0)
-    GLBE_PDIRS(GLBE_PA)
-#undef GLBE_PA
+#define GLBE_PLOADF(a, o, row, sol, ex) d[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, ld2, ld1);
+    GLBE_PDIRS(GLBE_PLOADF)
+#undef GLBE_PLOADF
     if constexpr (S::COMP) {
         const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * N);
         auto lo2 = [&](size_t i) { return S::ld2_lo(fl + i); };
         auto lo1 = [&](size_t i) { return S::ld_lo(fl + i); };
-        float el[19];
         l[0] = lo2((size_t)g.r00 + (uint32_t)g.x);
-#define GLBE_PAL(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(l, el, a, o, row, sol, ex, lo2, lo1, (size_t)0)
-        GLBE_PDIRS(GLBE_PAL)
-#undef GLBE_PAL
-#define GLBE_PBL(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(l, l, el, a, sol, ex)
-        GLBE_PDIRS(GLBE_PBL)
-#undef GLBE_PBL
+#define GLBE_PLOADL(a, o, row, sol, ex) l[a] = pair_gather(q, (size_t)(a) * N, (size_t)(o) * N, row, sol, ex, lo2, lo1);
+        GLBE_PDIRS(GLBE_PLOADL)
+#undef GLBE_PLOADL
     }
-#define GLBE_PB(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(d, d, e, a, sol, ex)
-    GLBE_PDIRS(GLBE_PB)
-#undef GLBE_PB
 }
 
 template <int ST>
@@ -462,52 +450,30 @@ __device__ __forceinline__ void load_g_pair(const StepParams& p, const typename 
     const Geo& g = q.g;
     auto ld2 = [&](size_t i) { return unscale<ST>(p, S::ld2(gs + i)); };
     auto ld1 = [&](size_t i) { return unscale<ST>(p, S::ld(gs + i)); };
-    F2 w[3][7];
-    float e[3][7];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const size_t jb = (size_t)(j * 7) * N;
-        w[j][0] = ld2(jb + g.r00 + (uint32_t)g.x);
-#define GLBE_PAG(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(w[j], e[j], a, o, row, sol, ex, ld2, ld1, jb)
-        GLBE_PDIRS7(GLBE_PAG)
-#undef GLBE_PAG
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
         const F2 wall(0.25f * p.bwall_dev[j]);
-        F2 t[7];
-        t[0] = w[j][0];
-#define GLBE_PBG(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(t, w[j], e[j], a, sol, ex)
-        GLBE_PDIRS7(GLBE_PBG)
-#undef GLBE_PBG
-        v[j * 7] = t[0];
-#define GLBE_WALLG(a, o, row, sol, ex) v[j * 7 + a] = (sol) ? wall - t[a] : t[a];
-        GLBE_PDIRS7(GLBE_WALLG)
-#undef GLBE_WALLG
+        v[j * 7] = ld2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADG(a, o, row, sol, ex)                                                              \
+    {                                                                                                \
+        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, ld2, ld1); \
+        v[j * 7 + a] = (sol) ? wall - t_ : t_;                                                       \
     }
-    if constexpr (S::COMP) {
-        const __half* __restrict__ gl = reinterpret_cast<const __half*>(gs + 21 * N);
-        auto lo2 = [&](size_t i) { return S::ld2_lo(gl + i); };
-        auto lo1 = [&](size_t i) { return S::ld_lo(gl + i); };
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const size_t jb = (size_t)(j * 7) * N;
-            w[j][0] = lo2(jb + g.r00 + (uint32_t)g.x);
-#define GLBE_PAGL(a, o, row, sol, ex) GLBE_PAIR_PHASE_A(w[j], e[j], a, o, row, sol, ex, lo2, lo1, jb)
-            GLBE_PDIRS7(GLBE_PAGL)
-#undef GLBE_PAGL
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            F2 t[7];
-            t[0] = w[j][0];
-#define GLBE_PBGL(a, o, row, sol, ex) GLBE_PAIR_PHASE_B(t, w[j], e[j], a, sol, ex)
-            GLBE_PDIRS7(GLBE_PBGL)
-#undef GLBE_PBGL
-            vl[j * 7] = t[0];
-#define GLBE_NEGL(a, o, row, sol, ex) vl[j * 7 + a] = (sol) ? -t[a] : t[a];
-            GLBE_PDIRS7(GLBE_NEGL)
-#undef GLBE_NEGL
+        GLBE_PDIRS7(GLBE_PLOADG)
+#undef GLBE_PLOADG
+        if constexpr (S::COMP) {
+            const __half* __restrict__ gl = reinterpret_cast<const __half*>(gs + 21 * N);
+            auto lo2 = [&](size_t i) { return S::ld2_lo(gl + i); };
+            auto lo1 = [&](size_t i) { return S::ld_lo(gl + i); };
+            vl[j * 7] = lo2(jb + g.r00 + (uint32_t)g.x);
+#define GLBE_PLOADGL(a, o, row, sol, ex)                                                              \
+    {                                                                                                 \
+        const F2 t_ = pair_gather(q, jb + (size_t)(a) * N, jb + (size_t)(o) * N, row, sol, ex, lo2, lo1); \
+        vl[j * 7 + a] = (sol) ? -t_ : t_;                                                             \
+    }
+            GLBE_PDIRS7(GLBE_PLOADGL)
+#undef GLBE_PLOADGL
         }
     }
 }
@@ -1095,8 +1061,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParam
 
 // The paired kernel serves x-periodic grids with an even nx when asked for
 // (variant 2).  The automatic choice is one node per thread: measured on
-// GB300 the paired form runs 1.2-1.4x slower (its register footprint halves
-// the resident warps).
+// GB300 the paired form issues 30 % fewer instructions per node but runs
+// 1.1-1.4x slower -- its register footprint (96-144 registers) leaves too
+// few resident warps to cover the memory latency.
 inline bool pair_eligible(const StepParams& p)
 {
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0]) return false;

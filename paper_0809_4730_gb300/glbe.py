@@ -296,7 +296,7 @@ class Batch:
         sec = C.c_double(0.0)
         st = load().glbe_batch_solve(self.ptr, float(tol), int(max_steps), int(bool(use_graph)), res,
                                      C.byref(sec))
-        if st not in (GLBE_OK, GLBE_ERR_TIMEOUT):
+        if st not in (GLBE_OK, GLBE_ERR_TIMEOUT, GLBE_ERR_DIVERGED):
             _check(st, "glbe_batch_solve")
         out = [dict(converged=bool(r.converged), steps=r.steps, r=r.r, seconds=r.seconds,
                     nonfinite=bool(r.nonfinite)) for r in res]

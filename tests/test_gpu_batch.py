@@ -15,13 +15,14 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 # (nx, ny, nz, gamma, Ha): odd and even sizes, flow-only and coupled domains
-SPECS = [(12, 14, 10, 1.0, 0), (9, 16, 12, 0.1, 5), (16, 12, 12, 0.3, 0), (10, 18, 8, 0.1, 20), (7, 10, 10, 0.5, 5)]
+SPECS = [(12, 14, 10, 1.0, 0), (9, 16, 12, 0.1, 5), (16, 12, 12, 0.3, 0), (10, 18, 8, 0.1, 10), (7, 10, 10, 0.5, 5)]
+# Ha = 20 at gamma = 0.1 on this grid is unstable (the FP64 oracle diverges too)
+UNSTABLE = (10, 18, 8, 0.1, 20)
 
 
-def _params(storage="f32"):
-    from paper_0809_4730_gb300.glbe import make_params
+def _params(storage="f32", specs=SPECS):
     out = []
-    for nx, ny, nz, gamma, Ha in SPECS:
+    for nx, ny, nz, gamma, Ha in specs:
         nu = eta = 0.02
         kw = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=(1e-5, 0, 0), storage=storage)
         if Ha > 0:
@@ -31,9 +32,9 @@ def _params(storage="f32"):
     return out
 
 
-def _batch(storage="f32"):
+def _batch(storage="f32", specs=SPECS):
     from paper_0809_4730_gb300.glbe import Batch, make_params
-    return Batch([make_params(nx, ny, nz, **kw) for nx, ny, nz, kw in _params(storage)])
+    return Batch([make_params(nx, ny, nz, **kw) for nx, ny, nz, kw in _params(storage, specs)])
 
 
 def _rel(a, b):
@@ -119,4 +120,15 @@ def test_batch_barrier_wait_gives_up_and_the_batch_stays_usable():
     B.reset()
     st, res, _ = B.solve(1e-6, 400_000)
     assert st == 0 and all(r["converged"] for r in res)
+    B.close()
+
+
+def test_batch_reports_the_unstable_domain_and_finishes_the_others():
+    from paper_0809_4730_gb300.glbe import GLBE_ERR_DIVERGED
+    specs = SPECS[:3] + [UNSTABLE]
+    B = _batch(specs=specs)
+    st, res, _ = B.solve(1e-6, 400_000)
+    assert st == GLBE_ERR_DIVERGED
+    assert res[3]["nonfinite"] and not res[3]["converged"]
+    assert all(r["converged"] and not r["nonfinite"] for r in res[:3])
     B.close()
