@@ -91,6 +91,8 @@ def lib():
             L.orc_run.argtypes = [C.POINTER(Params), _D, _D, _D, _D, _D, _L,
                                   C.c_long, C.c_long, C.c_double, _D, C.c_long, _L]
             L.orc_run.restype = C.c_long
+            L.orc_node_jacobian.argtypes = [C.POINTER(Params), _D, _D, _D, _D, _D, _D]
+            L.orc_state_jacobians.argtypes = [C.POINTER(Params), _D, _D, _D, _D, _D, _D]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             assert L.orc_params_size() == C.sizeof(Params), "oracle params layout mismatch"
@@ -292,17 +294,21 @@ class Solver:
         return rho, u, B, FLn
 
     def solid_mask(self) -> np.ndarray:
-        c = self.cfg
-        m = np.zeros((c.nz, c.ny, c.nx), dtype=bool)
-        for d, n in zip(range(3), (c.nx, c.ny, c.nz)):
-            sl = [slice(None)] * 3
-            if c.wall_lo[d]:
-                sl[2 - d] = 0
-                m[tuple(sl)] = True
-            if c.wall_hi[d]:
-                sl[2 - d] = n - 1
-                m[tuple(sl)] = True
-        return m.reshape(-1)
+        return solid_mask(self.cfg)
+
+
+def solid_mask(c: Config) -> np.ndarray:
+    """[N] bool: the node lies on a wall plane."""
+    m = np.zeros((c.nz, c.ny, c.nx), dtype=bool)
+    for d, n in zip(range(3), (c.nx, c.ny, c.nz)):
+        sl = [slice(None)] * 3
+        if c.wall_lo[d]:
+            sl[2 - d] = 0
+            m[tuple(sl)] = True
+        if c.wall_hi[d]:
+            sl[2 - d] = n - 1
+            m[tuple(sl)] = True
+    return m.reshape(-1)
 
 
 # ---------------------------------------------------------------------------

@@ -594,6 +594,7 @@ long orc_run(const orc_params* p, double* f, double* g, double* FL, const double
                     mass += rh[n];
                 }
                 double r = den > 0.0 ? sqrt(num/den) : (num > 0.0 ? INFINITY : 0.0);
+                if (!isfinite(num) || !isfinite(den)) r = NAN;   /* a diverged state is never "converged" */
                 if (hist && nh < hist_cap) {
                     double* h = hist + nh*8;
                     h[0] = (double)t; h[1] = r; h[2] = num; h[3] = den; h[4] = mass;
@@ -613,6 +614,96 @@ long orc_run(const orc_params* p, double* f, double* g, double* FL, const double
     if (nhist) *nhist = nh;
     free(fn); free(gn); free(ut); free(rh);
     return t;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Node Jacobians for the gradient checks.  The paper has no adjoint: the  */
+/* derivative of the node update above is taken numerically, by central    */
+/* differences of the unchanged node_collide in FP64.                      */
+/*   inputs  x = (f[19], g[21], F_L of the previous step[3], F_ext[3])     */
+/*   outputs y = (f~[19], g~[21], F_L[3], u[3])                            */
+/* J[i*46 + k] = dy_i/dx_k with step h[k] for input k.  Without induction  */
+/* the g and F_L columns and rows are zero.                                */
+/* ---------------------------------------------------------------------- */
+#define ORC_NJ 46
+
+static void node_outputs(const orc_params* p, const double* s, double tau_m, const double* x, double* y)
+{
+    double ft[19], gt[21];
+    node_macro nm;
+    node_collide(p, s, tau_m, x, p->induction ? x + 19 : NULL, x + 40, x + 43, ft, gt, &nm);
+    for (int i = 0; i < ORC_NJ; ++i) y[i] = 0.0;
+    for (int a = 0; a < 19; ++a) y[a] = ft[a];
+    if (p->induction) {
+        for (int i = 0; i < 21; ++i) y[19 + i] = gt[i];
+        for (int d = 0; d < 3; ++d) y[40 + d] = nm.FL[d];
+    }
+    for (int d = 0; d < 3; ++d) y[43 + d] = nm.u[d];
+}
+
+static void node_jacobian(const orc_params* p, const double* s, double tau_m, const double* x0,
+                          const double* h, double* J)
+{
+    double x[ORC_NJ], yp[ORC_NJ], ym[ORC_NJ];
+    for (int i = 0; i < ORC_NJ * ORC_NJ; ++i) J[i] = 0.0;
+    for (int k = 0; k < ORC_NJ; ++k) {
+        if (!p->induction && k >= 19 && k < 43) continue;
+        for (int i = 0; i < ORC_NJ; ++i) x[i] = x0[i];
+        x[k] = x0[k] + h[k];
+        node_outputs(p, s, tau_m, x, yp);
+        x[k] = x0[k] - h[k];
+        node_outputs(p, s, tau_m, x, ym);
+        for (int i = 0; i < ORC_NJ; ++i) J[i*ORC_NJ + k] = (yp[i] - ym[i]) / (2.0 * h[k]);
+    }
+}
+
+/* One node: f[19], g[21] (may be NULL without induction), FLprev[3],
+ * Fext[3] (the node's total external force). */
+void orc_node_jacobian(const orc_params* p, const double* f, const double* g, const double* FLprev,
+                       const double* Fext, const double* h, double* J)
+{
+    build_tables();
+    double s[19];
+    orc_relaxation_rates(p, s);
+    double tau_m = p->induction ? orc_tau_m(p) : 1.0;
+    double x[ORC_NJ] = {0.0};
+    for (int a = 0; a < 19; ++a) x[a] = f[a];
+    if (p->induction) {
+        for (int i = 0; i < 21; ++i) x[19 + i] = g[i];
+        for (int d = 0; d < 3; ++d) x[40 + d] = FLprev[d];
+    }
+    for (int d = 0; d < 3; ++d) x[43 + d] = Fext[d];
+    node_jacobian(p, s, tau_m, x, h, J);
+}
+
+/* Every node of a state (f, g, FL as in orc_run; Fext the [N][3] field or
+ * NULL): J[n][46][46]; zero for solid nodes. */
+void orc_state_jacobians(const orc_params* p, const double* f, const double* g, const double* FL,
+                         const double* Fext, const double* h, double* J)
+{
+    build_tables();
+    double s[19];
+    orc_relaxation_rates(p, s);
+    double tau_m = p->induction ? orc_tau_m(p) : 1.0;
+    const long N = (long)p->nx * p->ny * p->nz;
+    #pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        double* Jn = J + n * ORC_NJ * ORC_NJ;
+        int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx*p->ny));
+        if (is_solid(p, x, y, z)) {
+            for (int i = 0; i < ORC_NJ * ORC_NJ; ++i) Jn[i] = 0.0;
+            continue;
+        }
+        double xv[ORC_NJ] = {0.0}, Fn[3];
+        for (int a = 0; a < 19; ++a) xv[a] = f[n*19 + a];
+        if (p->induction) {
+            for (int i = 0; i < 21; ++i) xv[19 + i] = g[n*21 + i];
+            for (int d = 0; d < 3; ++d) xv[40 + d] = FL[n*3 + d];
+        }
+        node_force(p, Fext, n, Fn);
+        for (int d = 0; d < 3; ++d) xv[43 + d] = Fn[d];
+        node_jacobian(p, s, tau_m, xv, h, Jn);
+    }
 }
 
 /* ---------------------------------------------------------------------- */
