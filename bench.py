@@ -52,10 +52,19 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch"], default="duct",
-                    help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one launch")
-    ap.add_argument("--batch-storage", choices=["f32", "f32c"], default="f32")
-    ap.add_argument("--batch-max-steps", type=int, default=400_000)
+    ap.add_argument("--workload", choices=["duct", "batch", "adjoint"], default="duct",
+                    help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
+                         "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
+    ap.add_argument("--adjoint-n", type=int, default=128)
+    ap.add_argument("--adjoint-tol", type=float, default=1e-5)
+    ap.add_argument("--adjoint-fwd-tol", type=float, default=1e-7)
+    ap.add_argument("--adjoint-max-steps", type=int, default=300_000)
+    ap.add_argument("--adjoint-unrolled-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-K", type=int, default=100)
+    ap.add_argument("--no-adjoint-fd", action="store_true")
+    ap.add_argument("--batch-storage", choices=["f32", "f32c"], default="f32c",
+                    help="f32c by default: with F32 storage these ducts stall near r = 3e-8 (measured)")
+    ap.add_argument("--batch-max-steps", type=int, default=200_000)
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -183,16 +192,19 @@ def duct_solver(storage: str, device="cuda", variant: int = 0):
     return G, F_host, fluid
 
 
-def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda", storage="f32", variant=0):
+def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda", storage="f32", variant=0, force_field=0,
+                         nu=0.01):
     """Hartmann duct of n^3 nodes: x periodic, walls on y and z, B0 along y,
-    nu = eta = 0.01, chi = 0.01 (Pr_m = 0.01), F_x = 1e-6, FP32."""
+    nu = eta (0.01 by default), chi = 0.01 (Pr_m = 0.01), F_x = 1e-6 uniform
+    (or, with force_field = 3, a per-node field set by the caller), FP32."""
     from paper_0809_4730_gb300.glbe import Solver
-    nu = eta = 0.01
+    eta = nu
     L = (n - 2) / 2
     B0 = Ha * math.sqrt(nu * eta) / L
-    G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=(1e-6, 0, 0), induction=1,
+    F = (0.0, 0.0, 0.0) if force_field else (1e-6, 0, 0)
+    G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=F, induction=1,
                gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0), device=device, storage=storage,
-               variant=variant)
+               variant=variant, force_field=force_field)
     return G, n * (n - 2) * (n - 2)
 
 
@@ -526,6 +538,119 @@ def run_batch(args, rank, ws):
     }
 
 
+ADJ_NU = 0.05   # nu = eta of the adjoint workload (0.01 diverged at gamma = 0.1: u_max 0.04, Re ~ 500)
+
+
+def adjoint_duct(n: int, storage: str = "f32c"):
+    """The adjoint workload: n^3 Hartmann duct (Ha = 10, gamma = 0.1,
+    nu = eta = 0.05, chi = 0.01) driven by the seeded per-node Gaussian force
+    F_x ~ N(F0, (0.2 F0)^2), F_y, F_z ~ N(0, (0.2 F0)^2), F0 = 1e-6 (seed 1).
+    Compensated FP32 storage: with F32 the residual stalls above 1e-8 (storage
+    round-off ~1e-10 against |u| ~ 1e-2)."""
+    import torch
+    from paper_0809_4730_gb300.inputs import gaussian_force
+    G, fluid = hartmann_duct_solver(n, Ha=10.0, gamma=0.1, storage=storage, force_field=3, nu=ADJ_NU)
+    F = torch.tensor(gaussian_force(n, n, n, seed=1).reshape(3, -1), dtype=torch.float32, device="cuda")
+    G.set_force(F)
+    return G, F, fluid
+
+
+def adjoint_bytes_per_node(mhd: bool, storage: str = "f32c") -> int:
+    """Algorithmic bytes of one adjoint step per fluid node: forward gather
+    (19 f + 21 g) x 4 B (F32) or 6 B (F32C), lagged Lorentz force and force
+    field 3 x 4 B each, cotangent gather and store 43 x 4 B each, gradient
+    3 x 4 B."""
+    vb = 6 if storage == "f32c" else 4
+    if mhd:
+        return 40 * vb + 12 + 12 + 43 * 4 * 2 + 12
+    return 19 * vb + 12 + 19 * 4 * 2 + 12
+
+
+def run_adjoint(args, rank, ws):
+    import torch
+    n = args.adjoint_n
+    stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    G, F, fluid = adjoint_duct(n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, steps, r = G.solve(args.adjoint_fwd_tol, args.adjoint_max_steps)
+    e1.record(stream)
+    e1.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1e3
+    print(f"adjoint workload: forward status {st} at level {steps}, r = {r:.3g}, {fwd_s:.2f} s", file=sys.stderr,
+          flush=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        dQ, ast, it, ar = G.adjoint_steady(None, tol=args.adjoint_tol, max_iters=args.adjoint_max_steps)
+        e1.record(stream)
+        e1.synchronize()
+    adj_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws)
+    print(f"steady adjoint: status {ast}, {it} iterations, r = {ar:.3g}, {adj_s:.2f} s", file=sys.stderr, flush=True)
+    per_it = adj_s / max(it, 1)
+    bpn = adjoint_bytes_per_node(True)
+    achieved = bpn * fluid / per_it / 1e9
+    # unrolled transient from rest: 2000 steps, checkpoints every 100
+    H, _, _ = adjoint_duct(n)
+    e0.record(stream)
+    dQu = H.adjoint_unrolled(args.adjoint_unrolled_steps, args.adjoint_K)
+    e1.record(stream)
+    e1.synchronize()
+    unr_s = e0.elapsed_time(e1) / 1e3
+    print(f"unrolled adjoint: {unr_s:.2f} s", file=sys.stderr, flush=True)
+    # full-size property check: directional derivative along a seeded field
+    # against a central difference of two steady solves
+    fd = None
+    if not args.no_adjoint_fd:
+        # a same-sign direction (random signs would cancel below the FP32
+        # resolution of Q): dF_x = 5e-8 U(0.5, 1.5) per node, 5% of F0
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        dF = torch.zeros(3, G.N, device="cuda", dtype=torch.float32)
+        dF[0] = 5e-8 * (0.5 + torch.rand(G.N, generator=gen, device="cuda"))
+        qs = []
+        for sgn in (1.0, -1.0):
+            K2, _, _ = adjoint_duct(n)
+            K2.set_force(F + sgn * dF)
+            K2.solve(args.adjoint_fwd_tol, args.adjoint_max_steps)
+            _, u, _ = K2.fields()      # 0 on solid nodes
+            qs.append(float(u[0].double().sum() / n))
+            K2.close()
+        fd_val = (qs[0] - qs[1]) / 2.0
+        ad_val = float((dQ.double() * dF.double()).sum())
+        fd = {"directional_fd": fd_val, "directional_adjoint": ad_val, "Q": (qs[0] + qs[1]) / 2,
+              "rel_diff": abs(fd_val - ad_val) / max(abs(fd_val), 1e-300),
+              "direction": "dF_x = 5e-8 U(0.5,1.5) per node (seed 7), central difference of two steady solves"}
+    G.close()
+    H.close()
+    mlups = fluid * it / adj_s / 1e6 * ws
+    return {
+        "metric": "steady adjoint throughput (MLUPS of transposed collide-stream steps) and time to dQ/dF",
+        "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": ws, "steps": it, "warmup": 0,
+        "ms_per_step": round(per_it * 1e3, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"adjoint: {n}^3 Hartmann duct Ha=10, gamma=0.1, nu=eta={ADJ_NU}, chi=0.01, "
+                               "per-node Gaussian force (F0=1e-6, sigma=0.2 F0, seed 1), Q=(1/Lx) sum u_x, "
+                               "F32C storage, FP32 cotangents", "inputs_vs_L2": "state > L2 (no flush)"},
+        "forward": {"status": st, "level": steps, "r": r, "tol": args.adjoint_fwd_tol, "seconds": round(fwd_s, 3)},
+        "steady_adjoint": {"status": ast, "iterations": it, "r": ar, "seconds": round(adj_s, 3),
+                           "tol": args.adjoint_tol},
+        "unrolled_adjoint": {"steps": args.adjoint_unrolled_steps, "K": args.adjoint_K, "seconds": round(unr_s, 3),
+                             "max_abs_dQdF": float(dQu.abs().max())},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 3), "traffic": None,
+                     "note": "per iteration of glbe_adjoint_steady (adjoint kernel + finalize every 10 + host "
+                             f"polling), {bpn} B per fluid node, peak of measured"},
+        "full_size_check": fd, "clocks": clk.summary(),
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -536,7 +661,12 @@ def main():
             print(json.dumps(run_reference(args, rank, ws)), flush=True)
         return
     rank, ws = dist_init(args)
-    line = run_batch(args, rank, ws) if args.workload == "batch" else run_glbe(args, rank, ws)
+    if args.workload == "batch":
+        line = run_batch(args, rank, ws)
+    elif args.workload == "adjoint":
+        line = run_adjoint(args, rank, ws)
+    else:
+        line = run_glbe(args, rank, ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -100,7 +100,10 @@ typedef struct {
     void* stream;             /* cudaStream_t owned by the caller                */
     int variant;              /* kernel form: 0 = automatic; 1 = one node per thread; 2 = two x-adjacent
                                  nodes per thread with packed FP32x2 arithmetic (needs an even nx and
-                                 no walls along x, else the one-node form is used) */
+                                 no walls along x, else the one-node form is used); 3 = tiles of 128
+                                 x-nodes whose gathers are staged in shared memory by tensor-memory
+                                 copies (needs no walls along x, nx a multiple of 128, F32, BF16 or
+                                 F16 storage; else the one-node form is used) */
 } glbe_params;
 
 /* Latest residual evaluation (time level t, a multiple of 10). */
@@ -286,6 +289,52 @@ glbe_status glbe_batch_set_barrier_test(glbe_batch* b, long long spin_limit, int
 
 /* Frees the host-side batch (not the workspace). NULL is ignored. */
 void glbe_batch_destroy(glbe_batch* b);
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of a velocity objective with respect to the body force (the     */
+/* paper has no adjoint; this differentiates its time step).                 */
+/*   Q = sum over fluid nodes x of w(x) . u(x), u = j/rho with the half     */
+/*   force (Eq. precondhydrofields).  d_w is [3][N] FP32 or NULL for the    */
+/*   flow rate Q = (1/L_x) sum_fluid u_x (L_x = fluid planes along x).      */
+/*   d_dQdF receives dQ/dF(x), [3][N] FP32, for a force field of three       */
+/*   components added to params.F (0 on solid nodes), whatever the          */
+/*   context's force_field.                                                  */
+/* The state that is differentiated is the pre-collision f, g and the lagged */
+/* Lorentz force, as in glbe_get_state; one adjoint step applies the         */
+/* transposed node update (collision, Lorentz coupling, Secs. 2-4) after the */
+/* transposed streaming (bounce-back / anti-bounce-back walls), one thread   */
+/* per node.  Storage must be GLBE_F32 or GLBE_F32C (GLBE_ERR_ARG else).     */
+/* The caller provides the workspace (glbe_adjoint_workspace_bytes,         */
+/* 256-byte aligned device memory); nothing is allocated.  All work runs on  */
+/* the context's stream.                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes of glbe_adjoint_steady (nsteps = 0) or of
+ * glbe_adjoint_unrolled(nsteps, K): two cotangent buffers of 43N floats plus,
+ * for the unrolled form, ceil(nsteps/K) checkpoints and min(K, nsteps)
+ * recomputed states (each a population buffer pair and the Lorentz force). */
+glbe_status glbe_adjoint_workspace_bytes(const glbe_params* p, long nsteps, long K, size_t* bytes);
+
+/* Steady adjoint at the context's current state, which should be a converged
+ * steady state (glbe_solve): iterates lam <- J^t lam + dQ/ds, J the Jacobian
+ * of one time step there, until the gradient field changes by at most tol
+ * over 10 iterations, r = ||dQdF_k - dQdF_{k-10}|| / ||dQdF_k||, or max_iters
+ * (>= 10) is reached.  Mass is conserved by the step, so lam may drift along
+ * the uniform mode of f; that mode does not enter dQ/dF (the force adds no
+ * mass).  *iters_out = iterations at the last evaluation, *r_out = its r.
+ * GLBE_ERR_TIMEOUT if max_iters came first (d_dQdF then holds the last
+ * iterate), GLBE_ERR_DIVERGED on NaN/Inf.  The state is not changed.
+ * Synchronises the stream. */
+glbe_status glbe_adjoint_steady(glbe_ctx* ctx, const float* d_w, double tol, long max_iters, void* d_work,
+                                size_t bytes, float* d_dQdF, long* iters_out, double* r_out);
+
+/* Unrolled adjoint: marches the context nsteps >= 1 steps from its current
+ * level t0 (as glbe_step_n; the context ends at t0 + nsteps), keeping a
+ * checkpoint every K >= 1 levels, then sweeps backwards segment by segment
+ * (each segment recomputed from its checkpoint) and writes dQ/dF of Q taken
+ * on the final state.  Enqueued asynchronously on the stream. */
+glbe_status glbe_adjoint_unrolled(glbe_ctx* ctx, const float* d_w, long nsteps, long K, void* d_work, size_t bytes,
+                                  float* d_dQdF);
 
 /* ABI version of the loaded library (GLBE_ABI_VERSION). */
 int glbe_abi_version(void);

@@ -116,7 +116,7 @@ glbe_status glbe::validate_params(const glbe_params* p)
     }
     if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16 && p->storage != GLBE_F32C)
         return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16 or GLBE_F32C");
-    if (p->variant < 0 || p->variant > 2) return fail(GLBE_ERR_ARG, "variant must be 0, 1 or 2");
+    if (p->variant < 0 || p->variant > 3) return fail(GLBE_ERR_ARG, "variant must be 0, 1, 2 or 3");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
     return GLBE_OK;
@@ -160,6 +160,22 @@ StepParams glbe::make_step_params(const glbe_params* p)
     s.inv_scale = (float)(1.0 / scale);
     s.variant = p->variant;
     s.storage = p->storage;
+    // interior nodes: on each axis lo = 1 + wall_lo, hi = n - 2 - wall_hi
+    // (neighbours neither on a wall plane nor across the periodic seam)
+    s.interior_ok = 1;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; ++d) {
+        const int lo = 1 + p->wall_lo[d], hi = n[d] - 2 - p->wall_hi[d];
+        if (hi < lo) s.interior_ok = 0;
+        s.ilo[d] = (uint32_t)lo;
+        s.ispan[d] = hi >= lo ? (uint32_t)(hi - lo) : 0u;
+    }
+    // D3Q19 directions in the order of include/glbe.h
+    static const int E[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                 {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1},
+                                 {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
+    const long long Nn = (long long)p->nx * p->ny * p->nz, sx = 1, sy = p->nx, sz = (long long)p->nx * p->ny;
+    for (int a = 0; a < 19; ++a) s.doff[a] = a * Nn - (E[a][0] * sx + E[a][1] * sy + E[a][2] * sz);
     return s;
 }
 
@@ -316,6 +332,26 @@ glbe_status enqueue_step(glbe_ctx* c, cudaStream_t st, const int* stop)
 }  // namespace
 
 namespace glbe {
+size_t storage_value_bytes(int storage) { return storage_bytes(storage); }
+
+glbe_status ctx_view(glbe_ctx* c, CtxView* v)
+{
+    if (!c || !v) return fail(GLBE_ERR_ARG, "ctx or view is NULL");
+    const int s = (int)(c->t & 1);
+    v->prm = c->prm;
+    v->sp = c->sp;
+    v->N = c->N;
+    v->t = c->t;
+    v->fsrc = c->f[s];
+    v->gsrc = c->prm.induction ? c->g[s] : nullptr;
+    v->FL = c->FL;
+    v->Ffield = c->Ffield;
+    v->f_bytes = 19 * c->N * storage_bytes(c->prm.storage);
+    v->g_bytes = c->prm.induction ? 21 * c->N * storage_bytes(c->prm.storage) : 0;
+    v->stream = c->stream;
+    return GLBE_OK;
+}
+
 cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mass0, long long* t_dev, double* record,
                             double* hist, unsigned long long* hist_count, unsigned hist_cap, int* stop,
                             const double* tol, cudaStream_t st)
@@ -477,6 +513,14 @@ glbe_status glbe_sync(glbe_ctx* c)
 {
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     GLBE_CUDA(cudaStreamSynchronize(c->stream), "glbe_sync");
+    int waited_out = 0;
+    switch (c->prm.storage) {
+    case GLBE_F32: waited_out = tile_wait_error_t<ST_F32>(); break;
+    case GLBE_BF16: waited_out = tile_wait_error_t<ST_BF16>(); break;
+    case GLBE_F16: waited_out = tile_wait_error_t<ST_F16>(); break;
+    default: break;
+    }
+    if (waited_out) return fail(GLBE_ERR_TIMEOUT, "a pipeline wait of the TMA-staged step kernel ran out");
     return GLBE_OK;
 }
 

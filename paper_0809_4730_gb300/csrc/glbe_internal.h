@@ -47,8 +47,13 @@ struct StepParams {
     float bwall_dev[3];   // B_wall - B0 (0: insulating walls at the applied field)
     // storage of deviations
     float scale, inv_scale;
-    int variant;          // 0 automatic, 1 one node per thread, 2 two nodes per thread
+    int variant;          // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 TMA-staged tiles
     int storage;          // Storage of the buffers (for the automatic choice)
+    // interior nodes (no solid node among the 18 neighbours, no periodic wrap):
+    // x - ilo[0] <= ispan[0] (unsigned) and likewise y, z; interior_ok = 0 if none
+    int interior_ok;
+    uint32_t ilo[3], ispan[3];
+    long long doff[19];   // a N - (e_ax + e_ay nx + e_az nx ny): offset of the source of direction a
 };
 
 // Buffers of one launch.  Populations are deviations in the storage type,
@@ -90,6 +95,10 @@ cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuf
 template <int ST>
 cudaError_t launch_get_state_t(bool mhd, const StepParams& p, const void* fsrc, const void* gsrc, const float* FL,
                                float* df, float* dg, float* dFL, cudaStream_t st);
+// 1 if a bounded wait of the TMA-staged step kernel (variant 3) ran out since
+// the last call (the flag is then cleared); one flag per storage type.
+template <int ST>
+int tile_wait_error_t();
 template <int ST>
 cudaError_t launch_set_state_t(bool mhd, const StepParams& p, void* fsrc, void* gsrc, float* FL, const float* df,
                                const float* dg, const float* dFL, cudaStream_t st);
@@ -109,5 +118,24 @@ cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mas
 glbe_status fail(glbe_status s, const char* fmt, ...);       // sets the thread-local message
 glbe_status validate_params(const glbe_params* p);
 StepParams make_step_params(const glbe_params* p);
+
+// What another translation unit (the adjoint) needs of a context: its
+// parameters and the buffers of the current time level t (the populations the
+// next step gathers from, the lagged Lorentz force, the force field).
+struct CtxView {
+    glbe_params prm;
+    StepParams sp;
+    size_t N;
+    long t;
+    void* fsrc;           // population deviations entering the step from t (storage type)
+    void* gsrc;           // null without induction
+    float* FL;            // [3][N] Lorentz force of the step that led to t (null without induction)
+    const float* Ffield;  // [force_field][N] or null
+    size_t f_bytes;       // bytes of one f buffer (19N values, F32C: plus the 19N low parts)
+    size_t g_bytes;       // bytes of one g buffer (0 without induction)
+    cudaStream_t stream;
+};
+glbe_status ctx_view(glbe_ctx* c, CtxView* v);
+size_t storage_value_bytes(int storage);   // bytes per population value (F32C: 4 + 2)
 
 }  // namespace glbe

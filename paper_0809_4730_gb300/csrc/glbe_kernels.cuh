@@ -389,6 +389,52 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
     }
 }
 
+// Interior nodes: the node and its 18 neighbours are fluid and no neighbour
+// wraps around a periodic axis, so the source of direction a is the fixed
+// offset p.doff[a] = a N - (e_ax + e_ay nx + e_az nx ny) from the node, the
+// same for every such node (no geometry, no bounce-back choice).
+__device__ __forceinline__ bool is_interior(const StepParams& p, uint32_t n)
+{
+    if (!p.interior_ok) return false;
+    const uint32_t zy = fdiv(n, p.div_nx);
+    const uint32_t z = fdiv(n, p.div_nxy);
+    const uint32_t x = n - zy * (uint32_t)p.nx;
+    const uint32_t y = zy - z * (uint32_t)p.ny;
+    return (x - p.ilo[0]) <= p.ispan[0] && (y - p.ilo[1]) <= p.ispan[1] && (z - p.ilo[2]) <= p.ispan[2];
+}
+
+template <int ST, bool CG = false>
+__device__ __forceinline__ void load_f_interior(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
+                                                uint32_t n, float (&d)[19], float (&l)[19])
+{
+    const typename Store<ST>::T* __restrict__ fn = fs + n;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) d[a] = unscale<ST>(p, ldp<ST, CG>(fn + p.doff[a]));
+    if constexpr (Store<ST>::COMP) {
+        const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * (size_t)p.N) + n;
+#pragma unroll
+        for (int a = 0; a < 19; ++a) l[a] = ldlo<CG>(fl + p.doff[a]);
+    }
+}
+
+template <int ST, bool CG = false>
+__device__ __forceinline__ void load_g_interior(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
+                                                uint32_t n, float (&q)[21], float (&ql)[21])
+{
+    const size_t N = p.N;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const typename Store<ST>::T* __restrict__ b = gs + (size_t)(j * 7) * N + n;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) q[j * 7 + a] = unscale<ST>(p, ldp<ST, CG>(b + p.doff[a]));
+        if constexpr (Store<ST>::COMP) {
+            const __half* __restrict__ bl = reinterpret_cast<const __half*>(gs + 21 * N) + (size_t)(j * 7) * N + n;
+#pragma unroll
+            for (int a = 0; a < 7; ++a) ql[j * 7 + a] = ldlo<CG>(bl + p.doff[a]);
+        }
+    }
+}
+
 // One population of a pair: the two sources of direction a with x-shift ex
 // from row `row` (solid: bounce-back from the own row's opposite slot o).
 // ex = 0: one aligned pair.  ex = +1: node x0 needs x0 - 1 (the left lane's
@@ -851,6 +897,11 @@ __device__ __forceinline__ void block_partials(float (&acc)[7], double* partials
     }
 }
 
+template <int ST, bool MHD, int MODE>
+__device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                                                  uint32_t n, const float (&d)[19], const float (&dl)[19],
+                                                  const float (&q)[21], const float (&ql)[21], float (&acc)[7]);
+
 // ---------------------------------------------------------------------------
 // Scalar kernel: one node per thread, any geometry
 // ---------------------------------------------------------------------------
@@ -864,22 +915,43 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
     using T = typename S::T;
     const bool inb = i < p.N;
     const uint32_t n = inb ? i : 0u;
-    const Geo g = make_geo(p, n);
-    const bool fluid = inb && !g.solid;
     const size_t N = p.N;
-    if (!fluid) {
-        if (MODE == MODE_FIELDS && inb) {
-            if (fo.rho) fo.rho[n] = 0.f;
-            if (fo.u) { fo.u[n] = 0.f; fo.u[N + n] = 0.f; fo.u[2 * N + n] = 0.f; }
-            if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
-        }
-        return;
-    }
     float d[19], dl[19], q[21], ql[21];
-    load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+    if (inb && is_interior(p, n)) {
+        // no solid node and no periodic wrap around: every source at a fixed offset
+        load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, d, dl);
+        if (MHD) load_g_interior<ST, CG>(p, static_cast<const T*>(b.gsrc), n, q, ql);
+    } else {
+        const Geo g = make_geo(p, n);
+        if (!inb || g.solid) {
+            if (MODE == MODE_FIELDS && inb) {
+                if (fo.rho) fo.rho[n] = 0.f;
+                if (fo.u) { fo.u[n] = 0.f; fo.u[N + n] = 0.f; fo.u[2 * N + n] = 0.f; }
+                if (MHD && fo.B) { fo.B[n] = 0.f; fo.B[N + n] = 0.f; fo.B[2 * N + n] = 0.f; }
+            }
+            return;
+        }
+        load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+        if (MHD) load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
+    }
+    node_from_sources<ST, MHD, MODE>(p, b, fo, n, d, dl, q, ql, acc);
+}
+
+// The update of fluid node n from its gathered pre-collision populations
+// (d, dl: f and, for F32C, its low parts; q, ql: g): reads the lagged Lorentz
+// force and the force field, collides, writes the node's own slots of the
+// destination buffers (or the fields in MODE_FIELDS) and adds the residual
+// terms of MODE_STEP_RESID to acc.
+template <int ST, bool MHD, int MODE>
+__device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
+                                                  uint32_t n, const float (&d)[19], const float (&dl)[19],
+                                                  const float (&q)[21], const float (&ql)[21], float (&acc)[7])
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    const size_t N = p.N;
     float FLpx = 0.f, FLpy = 0.f, FLpz = 0.f;
     if (MHD) {
-        load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
         FLpx = b.FL[n];
         FLpy = b.FL[N + n];
         FLpz = b.FL[2 * N + n];
@@ -937,14 +1009,14 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
     if (MODE == MODE_STEP_RESID) {
         if (b.have_snap) {
             const float dx = ns.ux - b.usnap[n], dy = ns.uy - b.usnap[N + n], dz = ns.uz - b.usnap[2 * N + n];
-            acc[0] = dx * dx + dy * dy + dz * dz;
+            acc[0] += dx * dx + dy * dy + dz * dz;
         }
-        acc[1] = ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
-        acc[2] = ns.drho;              // the mass is rho0 * (fluid nodes) + sum drho
-        acc[3] = ns.jx;
-        acc[4] = ns.jy;
-        acc[5] = ns.jz;
-        acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
+        acc[1] += ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
+        acc[2] += ns.drho;             // the mass is rho0 * (fluid nodes) + sum drho
+        acc[3] += ns.jx;
+        acc[4] += ns.jy;
+        acc[5] += ns.jz;
+        acc[6] += vnonfinite(ns.ux + ns.uy + ns.uz);
         b.usnap[n] = ns.ux;
         b.usnap[N + n] = ns.uy;
         b.usnap[2 * N + n] = ns.uz;
@@ -1162,10 +1234,17 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+}  // namespace glbe
+#include "glbe_tile.cuh"
+namespace glbe {
+
 template <int ST, bool MHD, int MODE>
 cudaError_t launch_mode(const StepParams& p, const StepBuffers& b, const FieldOut& fo, cudaStream_t st,
                         unsigned* nblocks)
 {
+    if constexpr (ST != ST_F32C && MODE != MODE_FIELDS) {
+        if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE>(p, b, st, nblocks);
+    }
     if (MODE != MODE_FIELDS && pair_eligible(p)) {
         const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);
         step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
@@ -1190,6 +1269,12 @@ cudaError_t launch_step_t(bool mhd, int mode, const StepParams& p, const StepBuf
     if (mode == MODE_STEP) return launch_mode<ST, false, MODE_STEP>(p, b, fo, st, nblocks);
     if (mode == MODE_STEP_RESID) return launch_mode<ST, false, MODE_STEP_RESID>(p, b, fo, st, nblocks);
     return launch_mode<ST, false, MODE_FIELDS>(p, b, fo, st, nblocks);
+}
+
+template <int ST>
+int tile_wait_error_t()
+{
+    return tile_wait_error_read();
 }
 
 template <int ST>

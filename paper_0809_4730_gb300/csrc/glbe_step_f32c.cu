@@ -10,4 +10,5 @@ template cudaError_t launch_get_state_t<ST_F32C>(bool, const StepParams&, const 
                                                 float*, float*, float*, cudaStream_t);
 template cudaError_t launch_set_state_t<ST_F32C>(bool, const StepParams&, void*, void*, float*, const float*,
                                                 const float*, const float*, cudaStream_t);
+template int tile_wait_error_t<ST_F32C>();
 }  // namespace glbe

@@ -1,0 +1,395 @@
+// glbe_tile.cuh -- the fused step with TMA-staged gathers (sm_100+ tensor
+// memory accelerator, mbarrier pipeline), for x-periodic grids with nx a
+// multiple of 128 and FP32 / BF16 / FP16 storage.
+//
+// The arithmetic is the one of glbe_kernels.cuh (node_from_sources); only the
+// gather changes.  A persistent block holds one producer warp and four
+// consumer warps.  Work is cut into tiles of 128 consecutive x nodes of one
+// fluid (y, z) row.  For a tile the producer thread issues one 2-D tensor copy
+// per population array (19 for f, 21 more for g): the row the direction
+// streams from, (y - e_y, z - e_z), over x in [x0 - 8, x0 + 136), into a
+// stage of shared memory, all completing on the stage's mbarrier.  Where that
+// row is a wall plane, the link is bounced and the copy takes instead the
+// node row's own opposite population (the half-way bounce-back source).  The
+// consumer thread of node x reads its 19 (+21) values at x - e_x from the
+// stage, releases the stage, and runs the node update.  Four stages per block
+// keep the copies of the next tiles in flight while the current one is
+// computed, so the compute warps do not wait on DRAM latency.
+//
+// Periodic wrap in x: the copies read zeros outside [0, nx); the one thread at
+// x = 0 (x = nx - 1) takes its sources from x = nx - 1 (x = 0) with plain
+// loads.  Every mbarrier wait is bounded in time; a wait that runs out records
+// an error flag (reported by glbe_sync) and the block leaves its loop.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace glbe {
+
+constexpr int TILE_W = 128;                          // nodes per tile (one per consumer thread)
+constexpr int TILE_HALO = 8;                         // copied halo on each side (16-byte aligned start)
+constexpr int TILE_BOX = TILE_W + 2 * TILE_HALO;     // elements per row copy
+// Pipeline depth: four stages for the flow lattice; two when the 21 D3Q7
+// rows are staged as well (a stage then holds 40 rows).
+template <bool MHD>
+constexpr int tile_stages() { return MHD ? 2 : 4; }
+constexpr int TILE_CONSUMER_WARPS = TILE_W / 32;
+constexpr int TILE_THREADS = 32 * (TILE_CONSUMER_WARPS + 1);
+constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;   // 2 s per wait at most
+
+// Tile decomposition of the fluid rows of a grid.
+struct TileGeom {
+    uint32_t ntiles;     // xtiles * nyf * nzf
+    uint32_t xtiles;     // nx / TILE_W
+    uint32_t y0, nyf;    // fluid rows y in [y0, y0 + nyf)
+    uint32_t z0, nzf;
+    uint32_t plane;      // ny * nz: rows of one population array
+};
+
+// Set when a bounded wait of the tile kernel ran out (one flag per
+// translation unit; read through tile_wait_error_t).
+static __device__ int g_tile_wait_error;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long tile_clock_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of the given parity; false (and the error flag set)
+// when TILE_WAIT_NS passed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = tile_clock_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (tile_clock_ns() - t0 > TILE_WAIT_NS) {
+            atomicExch(&g_tile_wait_error, 1);
+            return false;
+        }
+    }
+}
+
+// 2-D tensor copy global -> shared, completing on bar.
+__device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, int x, int row, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(row), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <int ST>
+__device__ __forceinline__ float smem_pop(const typename Store<ST>::T* p)
+{
+    if constexpr (ST == ST_BF16) return __bfloat162float(*p);
+    else if constexpr (ST == ST_F16) return __half2float(*p);
+    else return *p;
+}
+
+// Shared-memory row pitch (elements): each row copy starts 128-byte aligned.
+template <int ST>
+constexpr int tile_pitch()
+{
+    return (int)(((TILE_BOX * sizeof(typename Store<ST>::T) + 127) / 128) * 128 / sizeof(typename Store<ST>::T));
+}
+
+template <int ST, bool MHD>
+constexpr size_t tile_smem_bytes()
+{
+    return 128 + (size_t)tile_stages<MHD>() * (MHD ? 40 : 19) * tile_pitch<ST>() * sizeof(typename Store<ST>::T);
+}
+
+// (e_x, e_y, e_z) and opposite of the D3Q19 directions (ordering of glbe.h).
+__device__ __forceinline__ void dir19(int a, int& ex, int& ey, int& ez)
+{
+    constexpr int E[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1},
+                              {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
+    ex = E[a][0];
+    ey = E[a][1];
+    ez = E[a][2];
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, const StepBuffers b,
+                                                            const TileGeom tg,
+                                                            const __grid_constant__ CUtensorMap tmf,
+                                                            const __grid_constant__ CUtensorMap tmg)
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    constexpr int Q = MHD ? 40 : 19;
+    constexpr int RP = tile_pitch<ST>();
+    constexpr uint32_t TILE_STAGES = (uint32_t)tile_stages<MHD>();
+    constexpr uint32_t STAGE_TX = (uint32_t)(Q * TILE_BOX * sizeof(T));
+    // direction tables: opposite of each D3Q19 direction
+    constexpr int OPP[19] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
+    if (b.stop != nullptr && *b.stop) return;
+
+    extern __shared__ __align__(128) unsigned char tile_smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(tile_smem);
+    uint64_t* empty = full + TILE_STAGES;
+    T* stages = reinterpret_cast<T*>(tile_smem + 128);
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < TILE_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TILE_CONSUMER_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int ny = p.ny, nz = p.nz;
+
+    if (warp == TILE_CONSUMER_WARPS) {
+        // ---------------- producer: one thread issues the row copies ----------
+        if (lane == 0) {
+            uint32_t k = 0;
+            bool ok = true;
+            for (uint32_t tile = blockIdx.x; tile < tg.ntiles && ok; tile += gridDim.x, ++k) {
+                const uint32_t s = k % TILE_STAGES;
+                const uint32_t par = (k / TILE_STAGES) & 1u;
+                if (!mbar_wait(&empty[s], par ^ 1u)) { ok = false; break; }
+                const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+                const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+                const int xs = (int)(xt * TILE_W) - TILE_HALO;
+                mbar_arrive_expect_tx(&full[s], STAGE_TX);
+                T* st = stages + (size_t)s * Q * RP;
+                for (int a = 0; a < 19; ++a) {
+                    int ex, ey, ez;
+                    dir19(a, ex, ey, ez);
+                    const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
+                    const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
+                    const bool sol = plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
+                    const int row = sol ? OPP[a] * (int)tg.plane + z * ny + y : a * (int)tg.plane + zs * ny + ys;
+                    tma_load_row(st + a * RP, &tmf, xs, row, &full[s]);
+                }
+                if (MHD) {
+                    for (int j = 0; j < 3; ++j)
+                        for (int a = 0; a < 7; ++a) {
+                            int ex, ey, ez;
+                            dir19(a, ex, ey, ez);
+                            const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
+                            const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
+                            const bool sol =
+                                plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
+                            const int row = sol ? (j * 7 + OPP[a]) * (int)tg.plane + z * ny + y
+                                                : (j * 7 + a) * (int)tg.plane + zs * ny + ys;
+                            tma_load_row(st + (19 + j * 7 + a) * RP, &tmg, xs, row, &full[s]);
+                        }
+                }
+            }
+            if (!ok) {
+                // leave no copy in flight: wait (bounded) for the stages already issued
+                const uint32_t issued = k;
+                const uint32_t first = issued > TILE_STAGES ? issued - TILE_STAGES : 0u;
+                for (uint32_t kk = first; kk < issued; ++kk)
+                    mbar_wait(&full[kk % TILE_STAGES], (kk / TILE_STAGES) & 1u);
+            }
+        }
+    } else {
+        // ---------------- consumers: one node per thread ----------------------
+        const int t = threadIdx.x;
+        const size_t N = p.N;
+        const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
+        const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
+        uint32_t k = 0;
+        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
+            const uint32_t s = k % TILE_STAGES;
+            const uint32_t par = (k / TILE_STAGES) & 1u;
+            if (!mbar_wait(&full[s], par)) break;
+            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+            const int x = (int)(xt * TILE_W) + t;
+            const uint32_t n = ((uint32_t)z * (uint32_t)ny + (uint32_t)y) * (uint32_t)p.nx + (uint32_t)x;
+            const T* st = stages + (size_t)s * Q * RP;
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+            const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
+            const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
+            const bool wrap_lo = x == 0, wrap_hi = x == p.nx - 1;
+            float d[19], dl[19], q[21], ql[21];
+#pragma unroll
+            for (int a = 0; a < 19; ++a) {
+                int ex, ey, ez;
+                dir19(a, ex, ey, ez);
+                const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
+                const int idx = TILE_HALO + t - (sol ? 0 : ex);
+                d[a] = unscale<ST>(p, smem_pop<ST>(st + a * RP + idx));
+                if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                    const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+                    const int xw = ex > 0 ? p.nx - 1 : 0;
+                    const size_t src = ((size_t)zs * ny + ys) * p.nx + xw;
+                    d[a] = unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + src));
+                }
+            }
+            if (MHD) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float wall = 0.25f * p.bwall_dev[j];
+#pragma unroll
+                    for (int a = 0; a < 7; ++a) {
+                        int ex, ey, ez;
+                        dir19(a, ex, ey, ez);
+                        const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
+                        const int idx = TILE_HALO + t - (sol ? 0 : ex);
+                        float v = unscale<ST>(p, smem_pop<ST>(st + (19 + j * 7 + a) * RP + idx));
+                        if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                            const int xw = ex > 0 ? p.nx - 1 : 0;
+                            const size_t src = ((size_t)z * ny + y) * p.nx + xw;
+                            v = unscale<ST>(p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + src));
+                        }
+                        q[j * 7 + a] = sol ? wall - v : v;
+                    }
+                }
+            }
+            // the stage is no longer needed: hand it back to the producer
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            node_from_sources<ST, MHD, MODE>(p, b, FieldOut{nullptr, nullptr, nullptr}, n, d, dl, q, ql, acc);
+        }
+    }
+    if (MODE == MODE_STEP_RESID) block_partials<TILE_THREADS>(acc, b.partials);
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+inline bool tile_eligible(const StepParams& p, int mode)
+{
+    if (mode == MODE_FIELDS) return false;
+    if (p.storage != ST_F32 && p.storage != ST_BF16 && p.storage != ST_F16) return false;
+    if (p.wlo[0] || p.whi[0]) return false;                 // x periodic
+    if (p.nx % TILE_W != 0) return false;
+    if (p.ny - p.wlo[1] - p.whi[1] < 1 || p.nz - p.wlo[2] - p.whi[2] < 1) return false;
+    const unsigned long long rows = 21ull * (unsigned long long)p.ny * (unsigned long long)p.nz;
+    return rows < (1ull << 31);
+}
+
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// Row-copy tensor map over a population buffer: dims (nx, rows), one row
+// per copy of TILE_BOX elements.
+template <int ST>
+inline bool make_row_map(CUtensorMap* map, const void* base, int nx, unsigned long long rows)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = ST == ST_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : (ST == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const size_t es = sizeof(typename Store<ST>::T);
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * es};
+    const cuuint32_t box[2] = {(cuuint32_t)TILE_BOX, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int ST, bool MHD, int MODE>
+cudaError_t launch_tile(const StepParams& p, const StepBuffers& b, cudaStream_t st, unsigned* nblocks)
+{
+    static int max_blocks = 0;   // resident blocks for the whole GPU (per instantiation, first device used)
+    constexpr size_t smem = tile_smem_bytes<ST, MHD>();
+    if (max_blocks == 0) {
+        cudaError_t e = cudaFuncSetAttribute(tile_kernel<ST, MHD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel<ST, MHD, MODE>, TILE_THREADS, smem);
+        if (e != cudaSuccess) return e;
+        max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    TileGeom tg;
+    tg.xtiles = (uint32_t)(p.nx / TILE_W);
+    tg.y0 = (uint32_t)p.wlo[1];
+    tg.nyf = (uint32_t)(p.ny - p.wlo[1] - p.whi[1]);
+    tg.z0 = (uint32_t)p.wlo[2];
+    tg.nzf = (uint32_t)(p.nz - p.wlo[2] - p.whi[2]);
+    tg.ntiles = tg.xtiles * tg.nyf * tg.nzf;
+    tg.plane = (uint32_t)(p.ny * p.nz);
+    CUtensorMap mf, mg;
+    if (!make_row_map<ST>(&mf, b.fsrc, p.nx, 19ull * tg.plane)) return cudaErrorInvalidValue;
+    if (MHD) {
+        if (!make_row_map<ST>(&mg, b.gsrc, p.nx, 21ull * tg.plane)) return cudaErrorInvalidValue;
+    } else {
+        mg = mf;
+    }
+    // at most one block per tile, per resident slot, and per residual partial
+    // the context holds (one per 256 nodes)
+    unsigned grid = (unsigned)(tg.ntiles < (uint32_t)max_blocks ? tg.ntiles : (uint32_t)max_blocks);
+    const unsigned partial_cap = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
+    if (grid > partial_cap) grid = partial_cap;
+    tile_kernel<ST, MHD, MODE><<<grid, TILE_THREADS, smem, st>>>(p, b, tg, mf, mg);
+    if (nblocks) *nblocks = grid;
+    return cudaGetLastError();
+}
+
+// Reads and clears this translation unit's wait-error flag.
+inline int tile_wait_error_read()
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tile_wait_error, sizeof v) != cudaSuccess) return 0;
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tile_wait_error, &zero, sizeof zero);
+    }
+    return v;
+}
+
+}  // namespace glbe

@@ -87,6 +87,11 @@ _SIGNATURES = {
     "glbe_batch_destroy": (None, [C.c_void_p]),
     "glbe_step_residual_noalloc": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_int, C.c_long, _P(glbe_residual_info)]),
+    "glbe_adjoint_workspace_bytes": (C.c_int, [_P(glbe_params), C.c_long, C.c_long, _P(C.c_size_t)]),
+    "glbe_adjoint_steady": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_long, C.c_void_p, C.c_size_t,
+                                      C.c_void_p, _P(C.c_long), _P(C.c_double)]),
+    "glbe_adjoint_unrolled": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_long, C.c_void_p, C.c_size_t,
+                                        C.c_void_p]),
 }
 
 _lib = None
@@ -226,6 +231,30 @@ def glbe_step_residual_noalloc(p: glbe_params, d_src, d_dst, d_force, d_u, have_
 def glbe_destroy(ctx):
     if ctx:
         load().glbe_destroy(ctx)
+
+
+def glbe_adjoint_workspace_bytes(p: glbe_params, nsteps: int = 0, K: int = 1) -> int:
+    n = C.c_size_t(0)
+    _check(load().glbe_adjoint_workspace_bytes(C.byref(p), int(nsteps), int(K), C.byref(n)),
+           "glbe_adjoint_workspace_bytes")
+    return n.value
+
+
+def glbe_adjoint_steady(ctx, d_w, tol: float, max_iters: int, work, d_dQdF):
+    """Returns (status, iterations, r); status GLBE_OK or GLBE_ERR_TIMEOUT."""
+    it = C.c_long(0)
+    r = C.c_double(0.0)
+    st = load().glbe_adjoint_steady(ctx, _ptr(d_w), float(tol), int(max_iters), _ptr(work),
+                                    work.numel() * work.element_size(), _ptr(d_dQdF), C.byref(it), C.byref(r))
+    if st not in (GLBE_OK, GLBE_ERR_TIMEOUT):
+        _check(st, "glbe_adjoint_steady")
+    return st, it.value, r.value
+
+
+def glbe_adjoint_unrolled(ctx, d_w, nsteps: int, K: int, work, d_dQdF):
+    _check(load().glbe_adjoint_unrolled(ctx, _ptr(d_w), int(nsteps), int(K), _ptr(work),
+                                        work.numel() * work.element_size(), _ptr(d_dQdF)),
+           "glbe_adjoint_unrolled")
 
 
 def make_params(nx, ny, nz, **kw) -> glbe_params:
@@ -415,3 +444,73 @@ class Solver:
 
     def sync(self):
         glbe_sync(self.ctx)
+
+    # -- gradients of Q = sum w . u with respect to the force field ----------
+    def _adjoint_work(self, nsteps: int, K: int):
+        nbytes = glbe_adjoint_workspace_bytes(self.params, nsteps, K)
+        key = (nsteps, K)
+        if getattr(self, "_adj_key", None) != key:
+            self._adj_work = None
+            self._adj_work = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+            self._adj_key = key
+        return self._adj_work
+
+    def adjoint_steady(self, w=None, tol: float = 1e-6, max_iters: int = 1_000_000):
+        """dQ/dF [3, N] at the current (steady) state; w [3, N] or None for the
+        flow rate (1/L_x) sum u_x.  Returns (dQdF, status, iterations, r)."""
+        dQdF = self.torch.empty(3, self.N, dtype=self.torch.float32, device=self.device)
+        st, it, r = glbe_adjoint_steady(self.ctx, None if w is None else w.contiguous(), tol, max_iters,
+                                        self._adjoint_work(0, 1), dQdF)
+        return dQdF, st, it, r
+
+    def adjoint_unrolled(self, nsteps: int, K: int, w=None):
+        """Marches nsteps steps (checkpoint every K) and returns dQ/dF [3, N] of
+        Q on the final state."""
+        dQdF = self.torch.empty(3, self.N, dtype=self.torch.float32, device=self.device)
+        glbe_adjoint_unrolled(self.ctx, None if w is None else w.contiguous(), nsteps, K,
+                              self._adjoint_work(nsteps, K), dQdF)
+        return dQdF
+
+
+class SteadyVelocity:
+    """torch.autograd.Function factory: the steady velocity field as a
+    differentiable function of the body-force field.
+
+    ``SteadyVelocity(solver, tol, adj_tol)(F)`` with F [3, N] (FP32, on the
+    solver's device) sets the force, solves to r <= tol (glbe_solve from the
+    current state) and returns u [3, N].  Its backward takes dL/du as the
+    objective weights w and returns dL/dF from the steady adjoint
+    (glbe_adjoint_steady) at that state.  The solver must have been created
+    with force_field = 3."""
+
+    def __init__(self, solver: "Solver", tol: float = 1e-8, max_steps: int = 10_000_000,
+                 adj_tol: float = 1e-6, max_iters: int = 10_000_000):
+        import torch
+        self.solver, self.tol, self.max_steps = solver, tol, max_steps
+        self.adj_tol, self.max_iters = adj_tol, max_iters
+        outer = self
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, F):
+                S = outer.solver
+                S.set_force(F.detach().to(torch.float32).contiguous())
+                st, steps, r = S.solve(outer.tol, outer.max_steps)
+                if st != GLBE_OK:
+                    raise GlbeError(st, "SteadyVelocity forward", f"no steady state (r = {r:g} after {steps})")
+                _, u, _ = S.fields()
+                return u
+
+            @staticmethod
+            def backward(ctx, grad_u):
+                S = outer.solver
+                dF, st, it, r = S.adjoint_steady(grad_u.detach().to(torch.float32).contiguous(), outer.adj_tol,
+                                                 outer.max_iters)
+                if st != GLBE_OK:
+                    raise GlbeError(st, "SteadyVelocity backward", f"adjoint r = {r:g} after {it} iterations")
+                return dF
+
+        self._fn = _Fn
+
+    def __call__(self, F):
+        return self._fn.apply(F)

@@ -173,6 +173,62 @@ def test_step_parity_paired_kernel(orc, nx, storage, tol, mhd):
     assert abs(info.mass - h[10]["mass"]) <= 1e-6 * h[10]["mass"]
 
 
+# The TMA-staged tile kernel (variant 3): x periodic, nx a multiple of 128.
+# It gathers the same values as the one-node kernel and runs the same node
+# update, so the states must agree bit for bit; ny = 9 with walls on both
+# y planes and nz = 7 with one z wall leave fluid rows next to walls, rows
+# that wrap around z, and the x seam at x = 0 / nx - 1.
+@pytest.mark.parametrize("nx", [128, 256])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("mhd", [False, True])
+def test_tile_kernel_matches_one_node_kernel_bitwise(orc, nx, storage, mhd):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, mhd, gamma=0.4, nx=nx, ny=9, nz=7)
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=nx)
+    S, G1 = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=1)
+    _, G3 = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=3)
+    _perturb(S, 23 + nx)
+    push_oracle_state(S, G1)
+    push_oracle_state(S, G3)
+    G1.step(21)
+    G3.step(21)
+    for a, b in zip(gpu_state(G1), gpu_state(G3)):
+        if a is not None:
+            assert np.array_equal(a, b)
+    r1, r3 = G1.residual(), G3.residual()
+    assert r1.t == r3.t == 20
+    assert abs(r1.r - r3.r) <= 1e-5 * r1.r        # block sums in another order
+    assert abs(r1.mass - r3.mass) <= 1e-9 * r1.mass
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2)])
+@pytest.mark.parametrize("mhd", [False, True])
+def test_step_parity_tile_kernel(orc, storage, tol, mhd):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, mhd, gamma=0.4, nx=128, ny=9, nz=7)
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=5)
+    S, G = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=3)
+    _perturb(S, 41)
+    push_oracle_state(S, G)
+    fluid = ~S.solid_mask()
+    if storage != "f32":
+        df0, dg0, FL0 = gpu_state(G)
+        S.f[fluid] = (df0[:, fluid].T + W19[None, :] * cfg.rho0)
+        if mhd:
+            B0 = np.asarray(cfg.B0)
+            S.g[fluid] = dg0[:, fluid].T.reshape(-1, 3, 7) + W7[None, None, :] * B0[None, :, None]
+    n = 13
+    S.run(n)
+    G.step(n)
+    df, dg, FL = gpu_state(G)
+    odf, odg, oFL = oracle_state_dev(S)
+    assert rel_linf(df, odf, fluid) < tol
+    if mhd:
+        assert rel_linf(dg, odg, fluid) < tol
+        assert rel_linf(FL, oFL, fluid) < max(tol, 3e-5)
+    G.sync()
+
+
 # ---------------------------------------------------------------------------
 # Steady state: plane channel 4x32x4 (walls at y = 0, 31), F_x = 1e-6,
 # tau = 0.8 on the stress moments, gamma = 0.1.  The oracle runs the x/z-
