@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-adjoint-fd", action="store_true")
     ap.add_argument("--batch-storage", choices=["f32", "f32c"], default="f32c",
                     help="f32c by default: with F32 storage these ducts stall near r = 3e-8 (measured)")
-    ap.add_argument("--batch-max-steps", type=int, default=200_000)
+    ap.add_argument("--batch-max-steps", type=int, default=50_000)
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)

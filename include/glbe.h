@@ -103,7 +103,8 @@ typedef struct {
                                  no walls along x, else the one-node form is used); 3 = tiles of 128
                                  x-nodes whose gathers are staged in shared memory by tensor-memory
                                  copies (needs no walls along x, nx a multiple of 128, F32, BF16 or
-                                 F16 storage; else the one-node form is used) */
+                                 F16 storage; else the one-node form is used); 4 = the same tiles with
+                                 two x-adjacent nodes per thread in packed FP32x2 arithmetic */
 } glbe_params;
 
 /* Latest residual evaluation (time level t, a multiple of 10). */

@@ -23,8 +23,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "glbe_oracle.c")
-_BUILD_DIR = os.path.join(_HERE, "_build")
+# GLBE_ORACLE_SOURCE / GLBE_ORACLE_BUILD_DIR let the mutation tests build a
+# deliberately broken copy of the source elsewhere (test use only).
+_SRC = os.environ.get("GLBE_ORACLE_SOURCE") or os.path.join(_HERE, "glbe_oracle.c")
+_BUILD_DIR = os.environ.get("GLBE_ORACLE_BUILD_DIR") or os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None

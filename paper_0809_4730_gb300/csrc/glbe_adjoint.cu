@@ -41,6 +41,10 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr unsigned HIST_CAP = 64;
+// One node per thread; 128-thread blocks held to 128 registers (4 resident
+// blocks per SM; the reverse step needs ~160 registers unconstrained, which
+// leaves one 256-thread block per SM).
+constexpr int ADJ_THREADS = 128;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 // Buffers of one adjoint step.
@@ -67,12 +71,12 @@ struct AdjArgs {
 };
 
 template <int ST, bool MHD, bool RESID>
-__global__ void __launch_bounds__(STEP_THREADS) adjoint_kernel(const StepParams p, const AdjArgs a)
+__global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParams p, const AdjArgs a)
 {
     using S = Store<ST>;
     using T = typename S::T;
     if (a.stop != nullptr && *a.stop) return;
-    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    const uint32_t i = blockIdx.x * ADJ_THREADS + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t N = p.N;
     const bool inb = i < p.N;
@@ -161,6 +165,13 @@ __global__ void __launch_bounds__(STEP_THREADS) adjoint_kernel(const StepParams 
                 wu[2] = a.w_uniform[2];
             }
         }
+        // values this thread reads back are loaded before any store (a load
+        // after the stores waits for their completion)
+        float acc_in[3] = {0.f, 0.f, 0.f}, snap[3] = {0.f, 0.f, 0.f};
+        if (a.accumulate)
+            for (int k = 0; k < 3; ++k) acc_in[k] = a.dQdF[(size_t)k * N + n];
+        if (RESID && a.have_snap)
+            for (int k = 0; k < 3; ++k) snap[k] = a.dsnap[(size_t)k * N + n];
         NodeAdjoint r;
         node_reverse<MHD>(p, d, q, FLp, Fext, vf, vg, vFL, wu, r);
 #pragma unroll
@@ -170,13 +181,10 @@ __global__ void __launch_bounds__(STEP_THREADS) adjoint_kernel(const StepParams 
             for (int k = 0; k < 21; ++k) og[(size_t)k * N + n] = r.q[k];
             for (int k = 0; k < 3; ++k) ok[(size_t)k * N + n] = r.FLp[k];
         }
-        for (int k = 0; k < 3; ++k) {
-            const size_t o = (size_t)k * N + n;
-            a.dQdF[o] = a.accumulate ? a.dQdF[o] + r.F[k] : r.F[k];
-        }
+        for (int k = 0; k < 3; ++k) a.dQdF[(size_t)k * N + n] = a.accumulate ? acc_in[k] + r.F[k] : r.F[k];
         if (RESID) {
             if (a.have_snap) {
-                const float e0 = r.F[0] - a.dsnap[n], e1 = r.F[1] - a.dsnap[N + n], e2 = r.F[2] - a.dsnap[2 * N + n];
+                const float e0 = r.F[0] - snap[0], e1 = r.F[1] - snap[1], e2 = r.F[2] - snap[2];
                 acc[0] = e0 * e0 + e1 * e1 + e2 * e2;
             }
             acc[1] = r.F[0] * r.F[0] + r.F[1] * r.F[1] + r.F[2] * r.F[2];
@@ -186,15 +194,15 @@ __global__ void __launch_bounds__(STEP_THREADS) adjoint_kernel(const StepParams 
             a.dsnap[2 * N + n] = r.F[2];
         }
     }
-    if (RESID) block_partials<STEP_THREADS>(acc, a.partials);
+    if (RESID) block_partials<ADJ_THREADS>(acc, a.partials);
 }
 
 template <int ST, bool MHD>
 cudaError_t launch_adj2(bool resid, const StepParams& p, const AdjArgs& a, cudaStream_t st, unsigned* nblocks)
 {
-    const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
-    if (resid) adjoint_kernel<ST, MHD, true><<<grid, STEP_THREADS, 0, st>>>(p, a);
-    else adjoint_kernel<ST, MHD, false><<<grid, STEP_THREADS, 0, st>>>(p, a);
+    const unsigned grid = (unsigned)(((size_t)p.N + ADJ_THREADS - 1) / ADJ_THREADS);
+    if (resid) adjoint_kernel<ST, MHD, true><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+    else adjoint_kernel<ST, MHD, false><<<grid, ADJ_THREADS, 0, st>>>(p, a);
     if (nblocks) *nblocks = grid;
     return cudaGetLastError();
 }
@@ -237,7 +245,7 @@ AdjLayout adj_layout(const glbe_params* p, long nsteps, long K)
 {
     AdjLayout L{};
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    const size_t grid = (N + STEP_THREADS - 1) / STEP_THREADS;
+    const size_t grid = (N + ADJ_THREADS - 1) / ADJ_THREADS;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     L.lam[0] = take(43 * N * sizeof(float));

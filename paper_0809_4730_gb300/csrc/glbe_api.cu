@@ -116,7 +116,7 @@ glbe_status glbe::validate_params(const glbe_params* p)
     }
     if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16 && p->storage != GLBE_F32C)
         return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16 or GLBE_F32C");
-    if (p->variant < 0 || p->variant > 3) return fail(GLBE_ERR_ARG, "variant must be 0, 1, 2 or 3");
+    if (p->variant < 0 || p->variant > 4) return fail(GLBE_ERR_ARG, "variant must be 0 ... 4");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
     return GLBE_OK;
@@ -227,6 +227,36 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(const double* __r
         *hist_count = c + 1;
         *t_dev = t + 10;
         if ((*tol > 0.0 && r <= *tol) || rec[8] > 0.0 || !isfinite(r)) *stop = 1;
+    }
+}
+
+// First stage of the residual reduction for large grids: block b sums the
+// partials of blocks [b*chunk, (b+1)*chunk) of the step (fixed order) into
+// row 7 of the partials, which the step leaves unused: out[k][b].
+constexpr int RED_THREADS = 256;
+
+__global__ void __launch_bounds__(RED_THREADS) partial_reduce_kernel(const double* __restrict__ partials,
+                                                                     unsigned nblocks, unsigned fb, double* out,
+                                                                     const int* stop)
+{
+    if (*stop) return;
+    __shared__ double sh[RED_THREADS / 32];
+    const unsigned chunk = (nblocks + fb - 1) / fb;
+    const unsigned b0 = blockIdx.x * chunk, b1 = b0 + chunk < nblocks ? b0 + chunk : nblocks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 7; ++k) {
+        const double* pk = partials + (size_t)k * nblocks;
+        double s = 0.0;
+        for (unsigned b = b0 + threadIdx.x; b < b1; b += RED_THREADS) s += pk[b];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) t += sh[w];
+            out[(size_t)k * fb + blockIdx.x] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -356,8 +386,21 @@ cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mas
                             double* hist, unsigned long long* hist_count, unsigned hist_cap, int* stop,
                             const double* tol, cudaStream_t st)
 {
-    finalize_kernel<<<1, FIN_THREADS, 0, st>>>(partials, nblocks, mass0, t_dev, record, hist, hist_count, hist_cap,
-                                               stop, tol);
+    // large grids: a first stage over many blocks (one SM alone reads the
+    // 7 x nblocks partials at a fraction of the HBM bandwidth), its results
+    // in the unused row 7 of the partials; then the one-block finalize
+    constexpr unsigned PER_BLOCK = 512;
+    if (nblocks >= 2 * PER_BLOCK) {
+        unsigned fb = nblocks / PER_BLOCK;
+        if (7 * fb > nblocks) fb = nblocks / 7;
+        double* row7 = const_cast<double*>(partials) + (size_t)7 * nblocks;
+        partial_reduce_kernel<<<fb, RED_THREADS, 0, st>>>(partials, nblocks, fb, row7, stop);
+        finalize_kernel<<<1, FIN_THREADS, 0, st>>>(row7, fb, mass0, t_dev, record, hist, hist_count, hist_cap, stop,
+                                                   tol);
+    } else {
+        finalize_kernel<<<1, FIN_THREADS, 0, st>>>(partials, nblocks, mass0, t_dev, record, hist, hist_count,
+                                                   hist_cap, stop, tol);
+    }
     return cudaGetLastError();
 }
 }  // namespace glbe

@@ -76,7 +76,8 @@ enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
 
 constexpr int STEP_THREADS = 256;   // scalar kernel: one node per thread
 constexpr int PAIR_THREADS = 128;   // paired kernel: two nodes per thread (the same 256 nodes per block)
-constexpr int PARTIAL_STRIDE = 8;   // per block: num, den, sum drho, Mx, My, Mz, nonfinite, pad; stored [k][block]
+constexpr int PARTIAL_STRIDE = 8;   // per block: num, den, sum drho, Mx, My, Mz, nonfinite, and a row the
+                                    // finalize uses for its first-stage sums; stored [k][block]
 
 // Outputs of MODE_FIELDS.
 struct FieldOut {

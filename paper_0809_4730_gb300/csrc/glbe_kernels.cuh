@@ -875,25 +875,25 @@ __device__ __forceinline__ V warp_sum(V v)
     return v;
 }
 
-// Residual sums of a block into partials[k][block]: FP32 per node and per
-// warp (each term is one node's FP32 quantity), FP64 from the block level on
-// -- GB300's FP64 pipe is kept off the per-node path.
+// Residual sums of a block into partials[k][block]: FP32 per node, warp and
+// block (at most 256 terms, all of one node's FP32 quantities), FP64 from the
+// partials on -- GB300's FP64 pipe is kept off the step kernel.
 template <int NT>
 __device__ __forceinline__ void block_partials(float (&acc)[7], double* partials)
 {
-    __shared__ double sh[NT / 32][7];
+    __shared__ float sh[NT / 32][7];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         const float v = warp_sum(acc[k]);
-        if (lane == 0) sh[warp][k] = (double)v;
+        if (lane == 0) sh[warp][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
-        double s = 0.0;
+        float s = 0.f;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) s += sh[w][threadIdx.x];
-        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+        partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = (double)s;
     }
 }
 
@@ -962,6 +962,15 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
         Fy += __ldg(b.Ffield + N + n);
         Fz += __ldg(b.Ffield + 2 * N + n);
     }
+    // the previous snapshot is read here, with the other loads: read after the
+    // population stores it waits on their completion (measured: the residual
+    // step took 5.3 ms instead of 1.3 ms on the 512 x 256 x 256 duct)
+    float us0 = 0.f, us1 = 0.f, us2 = 0.f;
+    if (MODE == MODE_STEP_RESID && b.have_snap) {
+        us0 = b.usnap[n];
+        us1 = b.usnap[N + n];
+        us2 = b.usnap[2 * N + n];
+    }
     float om[19], og[21];
     NodeState<float> ns;
     node_update<float, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, MODE != MODE_FIELDS, om, og, ns);
@@ -1008,7 +1017,7 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     }
     if (MODE == MODE_STEP_RESID) {
         if (b.have_snap) {
-            const float dx = ns.ux - b.usnap[n], dy = ns.uy - b.usnap[N + n], dz = ns.uz - b.usnap[2 * N + n];
+            const float dx = ns.ux - us0, dy = ns.uy - us1, dz = ns.uz - us2;
             acc[0] += dx * dx + dy * dy + dz * dz;
         }
         acc[1] += ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
@@ -1032,6 +1041,93 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
     scalar_node_step<ST, MHD, MODE>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
+}
+
+// The update of the fluid node pair (n0, n0 + 1) from its gathered
+// pre-collision populations (packed FP32x2): the counterpart of
+// node_from_sources for two nodes; adds the pair's residual terms to acc.
+template <int ST, bool MHD, int MODE>
+__device__ __forceinline__ void pair_from_sources(const StepParams& p, const StepBuffers& b, uint32_t n0,
+                                                  const F2 (&d)[19], const F2 (&dl)[19], const F2 (&q)[21],
+                                                  const F2 (&ql)[21], float (&acc)[7])
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    const size_t N = p.N;
+    F2 FLpx(0.f), FLpy(0.f), FLpz(0.f);
+    if (MHD) {
+        FLpx = F2(*reinterpret_cast<const float2*>(b.FL + n0));
+        FLpy = F2(*reinterpret_cast<const float2*>(b.FL + N + n0));
+        FLpz = F2(*reinterpret_cast<const float2*>(b.FL + 2 * N + n0));
+    }
+    F2 Fx(p.F[0]), Fy(p.F[1]), Fz(p.F[2]);
+    if (p.force_ncomp >= 1) Fx += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + n0)));
+    if (p.force_ncomp == 3) {
+        Fy += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + N + n0)));
+        Fz += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + 2 * N + n0)));
+    }
+    F2 om[19], og[21];
+    // previous snapshot read before the stores (see node_from_sources)
+    F2 us0(0.f), us1(0.f), us2(0.f);
+    if (MODE == MODE_STEP_RESID && b.have_snap) {
+        us0 = F2(*reinterpret_cast<const float2*>(b.usnap + n0));
+        us1 = F2(*reinterpret_cast<const float2*>(b.usnap + N + n0));
+        us2 = F2(*reinterpret_cast<const float2*>(b.usnap + 2 * N + n0));
+    }
+    NodeState<F2> ns;
+    node_update<F2, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, true, om, og, ns);
+
+    T* __restrict__ fd = static_cast<T*>(b.fdst);
+    if constexpr (S::COMP) {
+        __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            F2 nh, nl;
+            comp_add(d[a], dl[a], om[a], nh, nl);
+            S::st2(fd + (size_t)a * N + n0, nh);
+            S::st2_lo(fdl + (size_t)a * N + n0, nl);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, d[a] + om[a]));
+    }
+    if (MHD) {
+        T* __restrict__ gd = static_cast<T*>(b.gdst);
+        if constexpr (S::COMP) {
+            __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
+#pragma unroll
+            for (int a = 0; a < 21; ++a) {
+                F2 nh, nl;
+                comp_add(q[a], ql[a], og[a], nh, nl);
+                S::st2(gd + (size_t)a * N + n0, nh);
+                S::st2_lo(gdl + (size_t)a * N + n0, nl);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 21; ++a) S::st2(gd + (size_t)a * N + n0, toscale<ST>(p, q[a] + og[a]));
+        }
+        *reinterpret_cast<float2*>(b.FL + n0) = ns.mac.FLx.v;
+        *reinterpret_cast<float2*>(b.FL + N + n0) = ns.mac.FLy.v;
+        *reinterpret_cast<float2*>(b.FL + 2 * N + n0) = ns.mac.FLz.v;
+    }
+    if (MODE == MODE_STEP_RESID) {
+        float2* us = reinterpret_cast<float2*>(b.usnap + n0);
+        float2* vs = reinterpret_cast<float2*>(b.usnap + N + n0);
+        float2* ws = reinterpret_cast<float2*>(b.usnap + 2 * N + n0);
+        if (b.have_snap) {
+            const F2 dx = ns.ux - us0, dy = ns.uy - us1, dz = ns.uz - us2;
+            acc[0] += lane_sum(dx * dx + dy * dy + dz * dz);
+        }
+        acc[1] += lane_sum(ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz);
+        acc[2] += lane_sum(ns.drho);
+        acc[3] += lane_sum(ns.jx);
+        acc[4] += lane_sum(ns.jy);
+        acc[5] += lane_sum(ns.jz);
+        acc[6] += vnonfinite(ns.ux + ns.uy + ns.uz);
+        *us = ns.ux.v;
+        *vs = ns.uy.v;
+        *ws = ns.uz.v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1059,75 +1155,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParam
     if (MHD) load_g_pair<ST>(p, static_cast<const T*>(b.gsrc), gp, q, ql);
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (fluid) {
-        F2 FLpx(0.f), FLpy(0.f), FLpz(0.f);
-        if (MHD) {
-            FLpx = F2(*reinterpret_cast<const float2*>(b.FL + n0));
-            FLpy = F2(*reinterpret_cast<const float2*>(b.FL + N + n0));
-            FLpz = F2(*reinterpret_cast<const float2*>(b.FL + 2 * N + n0));
-        }
-        F2 Fx(p.F[0]), Fy(p.F[1]), Fz(p.F[2]);
-        if (p.force_ncomp >= 1) Fx += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + n0)));
-        if (p.force_ncomp == 3) {
-            Fy += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + N + n0)));
-            Fz += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + 2 * N + n0)));
-        }
-        F2 om[19], og[21];
-        NodeState<F2> ns;
-        node_update<F2, ST, MHD>(p, d, dl, q, ql, FLpx, FLpy, FLpz, Fx, Fy, Fz, true, om, og, ns);
-
-        T* __restrict__ fd = static_cast<T*>(b.fdst);
-        if constexpr (S::COMP) {
-            __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
-#pragma unroll
-            for (int a = 0; a < 19; ++a) {
-                F2 nh, nl;
-                comp_add(d[a], dl[a], om[a], nh, nl);
-                S::st2(fd + (size_t)a * N + n0, nh);
-                S::st2_lo(fdl + (size_t)a * N + n0, nl);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, d[a] + om[a]));
-        }
-        if (MHD) {
-            T* __restrict__ gd = static_cast<T*>(b.gdst);
-            if constexpr (S::COMP) {
-                __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
-#pragma unroll
-                for (int a = 0; a < 21; ++a) {
-                    F2 nh, nl;
-                    comp_add(q[a], ql[a], og[a], nh, nl);
-                    S::st2(gd + (size_t)a * N + n0, nh);
-                    S::st2_lo(gdl + (size_t)a * N + n0, nl);
-                }
-            } else {
-#pragma unroll
-                for (int a = 0; a < 21; ++a) S::st2(gd + (size_t)a * N + n0, toscale<ST>(p, q[a] + og[a]));
-            }
-            *reinterpret_cast<float2*>(b.FL + n0) = ns.mac.FLx.v;
-            *reinterpret_cast<float2*>(b.FL + N + n0) = ns.mac.FLy.v;
-            *reinterpret_cast<float2*>(b.FL + 2 * N + n0) = ns.mac.FLz.v;
-        }
-        if (MODE == MODE_STEP_RESID) {
-            float2* us = reinterpret_cast<float2*>(b.usnap + n0);
-            float2* vs = reinterpret_cast<float2*>(b.usnap + N + n0);
-            float2* ws = reinterpret_cast<float2*>(b.usnap + 2 * N + n0);
-            if (b.have_snap) {
-                const F2 dx = ns.ux - F2(*us), dy = ns.uy - F2(*vs), dz = ns.uz - F2(*ws);
-                acc[0] = lane_sum(dx * dx + dy * dy + dz * dz);
-            }
-            acc[1] = lane_sum(ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz);
-            acc[2] = lane_sum(ns.drho);
-            acc[3] = lane_sum(ns.jx);
-            acc[4] = lane_sum(ns.jy);
-            acc[5] = lane_sum(ns.jz);
-            acc[6] = vnonfinite(ns.ux + ns.uy + ns.uz);
-            *us = ns.ux.v;
-            *vs = ns.uy.v;
-            *ws = ns.uz.v;
-        }
-    }
+    if (fluid) pair_from_sources<ST, MHD, MODE>(p, b, n0, d, dl, q, ql, acc);
     if (MODE == MODE_STEP_RESID) block_partials<PAIR_THREADS>(acc, b.partials);
 }
 
@@ -1243,7 +1271,8 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b, const FieldOu
                         unsigned* nblocks)
 {
     if constexpr (ST != ST_F32C && MODE != MODE_FIELDS) {
-        if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE>(p, b, st, nblocks);
+        if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
+        if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);
     }
     if (MODE != MODE_FIELDS && pair_eligible(p)) {
         const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);

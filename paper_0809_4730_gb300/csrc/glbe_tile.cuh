@@ -5,8 +5,9 @@
 // The arithmetic is the one of glbe_kernels.cuh (node_from_sources); only the
 // gather changes.  A persistent block holds one producer warp and four
 // consumer warps.  Work is cut into tiles of 128 consecutive x nodes of one
-// fluid (y, z) row.  For a tile the producer thread issues one 2-D tensor copy
-// per population array (19 for f, 21 more for g): the row the direction
+// fluid (y, z) row.  For a tile the producer warp issues one 2-D tensor copy
+// per population array (19 for f, 21 more for g; lane r takes array r and
+// r + 32): the row the direction
 // streams from, (y - e_y, z - e_z), over x in [x0 - 8, x0 + 136), into a
 // stage of shared memory, all completing on the stage's mbarrier.  Where that
 // row is a wall plane, the link is bounced and the copy takes instead the
@@ -33,9 +34,17 @@ constexpr int TILE_BOX = TILE_W + 2 * TILE_HALO;     // elements per row copy
 // rows are staged as well (a stage then holds 40 rows).
 template <bool MHD>
 constexpr int tile_stages() { return MHD ? 2 : 4; }
-constexpr int TILE_CONSUMER_WARPS = TILE_W / 32;
-constexpr int TILE_THREADS = 32 * (TILE_CONSUMER_WARPS + 1);
+// Consumer warps per block: one node per thread (4 warps), or two x-adjacent
+// nodes per thread with packed FP32x2 arithmetic (2 warps); plus the producer.
+template <bool PAIR>
+constexpr int tile_consumer_warps() { return PAIR ? TILE_W / 64 : TILE_W / 32; }
+template <bool PAIR>
+constexpr int tile_threads() { return 32 * (tile_consumer_warps<PAIR>() + 1); }
 constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;   // 2 s per wait at most
+// Hint for the time a waiting thread may be suspended inside one try_wait
+// (it resumes when the phase completes): waiting warps then take no issue
+// slots from the working ones.
+constexpr uint32_t TILE_SUSPEND_NS = 100000u;
 
 // Tile decomposition of the fluid rows of a grid.
 struct TileGeom {
@@ -76,10 +85,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(TILE_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -98,7 +107,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = tile_clock_ns();
     for (;;) {
-        for (int k = 0; k < 64; ++k)
+        for (int k = 0; k < 4; ++k)
             if (mbar_try_wait(bar, parity)) return true;
         if (tile_clock_ns() - t0 > TILE_WAIT_NS) {
             atomicExch(&g_tile_wait_error, 1);
@@ -107,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     }
 }
 
-// 2-D tensor copy global -> shared, completing on bar.
+// 2-D tensor copy global -> shared, completing on bar (any lane may issue).
 __device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, int x, int row, uint64_t* bar)
 {
     asm volatile(
@@ -122,6 +131,19 @@ __device__ __forceinline__ float smem_pop(const typename Store<ST>::T* p)
     if constexpr (ST == ST_BF16) return __bfloat162float(*p);
     else if constexpr (ST == ST_F16) return __half2float(*p);
     else return *p;
+}
+
+// Elements i and i + 1 of a staged row as two FP32 lanes (raw stored values).
+// i even: one aligned 4- or 8-byte load; i odd: two element loads.
+template <int ST>
+__device__ __forceinline__ F2 smem_pair(const typename Store<ST>::T* row, int i, bool aligned)
+{
+    if (aligned) {
+        if constexpr (ST == ST_BF16) return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + i)));
+        else if constexpr (ST == ST_F16) return F2(__half22float2(*reinterpret_cast<const __half2*>(row + i)));
+        else return F2(*reinterpret_cast<const float2*>(row + i));
+    }
+    return F2(smem_pop<ST>(row + i), smem_pop<ST>(row + i + 1));
 }
 
 // Shared-memory row pitch (elements): each row copy starts 128-byte aligned.
@@ -148,8 +170,14 @@ __device__ __forceinline__ void dir19(int a, int& ex, int& ey, int& ez)
     ez = E[a][2];
 }
 
-template <int ST, bool MHD, int MODE>
-__global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, const StepBuffers b,
+// The same tables for run-time indices (the producer lanes): e_y, e_z and
+// the opposite direction.
+static __constant__ int c_tile_ey[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+static __constant__ int c_tile_ez[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+static __constant__ int c_tile_opp[19] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
+
+template <int ST, bool MHD, int MODE, bool PAIR>
+__global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepParams p, const StepBuffers b,
                                                             const TileGeom tg,
                                                             const __grid_constant__ CUtensorMap tmf,
                                                             const __grid_constant__ CUtensorMap tmg)
@@ -160,8 +188,8 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, 
     constexpr int RP = tile_pitch<ST>();
     constexpr uint32_t TILE_STAGES = (uint32_t)tile_stages<MHD>();
     constexpr uint32_t STAGE_TX = (uint32_t)(Q * TILE_BOX * sizeof(T));
-    // direction tables: opposite of each D3Q19 direction
-    constexpr int OPP[19] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
+    constexpr int TILE_CONSUMER_WARPS = tile_consumer_warps<PAIR>();
+    constexpr int TILE_THREADS = tile_threads<PAIR>();
     if (b.stop != nullptr && *b.stop) return;
 
     extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -182,50 +210,148 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, 
     const int ny = p.ny, nz = p.nz;
 
     if (warp == TILE_CONSUMER_WARPS) {
-        // ---------------- producer: one thread issues the row copies ----------
-        if (lane == 0) {
-            uint32_t k = 0;
-            bool ok = true;
-            for (uint32_t tile = blockIdx.x; tile < tg.ntiles && ok; tile += gridDim.x, ++k) {
-                const uint32_t s = k % TILE_STAGES;
-                const uint32_t par = (k / TILE_STAGES) & 1u;
-                if (!mbar_wait(&empty[s], par ^ 1u)) { ok = false; break; }
-                const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
-                const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
-                const int xs = (int)(xt * TILE_W) - TILE_HALO;
-                mbar_arrive_expect_tx(&full[s], STAGE_TX);
-                T* st = stages + (size_t)s * Q * RP;
+        // ---------------- producer warp: lane r issues row copy r (and r + 32) --
+        uint32_t k = 0;
+        bool ok = true;
+        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
+            const uint32_t s = k % TILE_STAGES;
+            const uint32_t par = (k / TILE_STAGES) & 1u;
+            int got = 0;
+            if (lane == 0) got = mbar_wait(&empty[s], par ^ 1u) ? 1 : 0;
+            if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], STAGE_TX);
+            __syncwarp();
+            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+            const int xs = (int)(xt * TILE_W) - TILE_HALO;
+            T* st = stages + (size_t)s * Q * RP;
+            for (int rr = lane; rr < Q; rr += 32) {
+                // row rr of the stage: f direction rr, or g component j, direction a
+                const int a = rr < 19 ? rr : (rr - 19) % 7;
+                const int arr = rr < 19 ? rr : rr - 19;   // population array index within f or g
+                const int ey = c_tile_ey[a], ez = c_tile_ez[a];
+                const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
+                const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
+                const bool sol = plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
+                const int src_arr = sol ? arr - a + c_tile_opp[a] : arr;   // bounced: the opposite population
+                const int row = sol ? src_arr * (int)tg.plane + z * ny + y : src_arr * (int)tg.plane + zs * ny + ys;
+                tma_load_row(st + rr * RP, rr < 19 ? &tmf : &tmg, xs, row, &full[s]);
+            }
+        }
+        if (!ok && lane == 0) {
+            // leave no copy in flight: wait (bounded) for the stages already issued
+            const uint32_t issued = k;
+            const uint32_t first = issued > TILE_STAGES ? issued - TILE_STAGES : 0u;
+            for (uint32_t kk = first; kk < issued; ++kk)
+                mbar_wait(&full[kk % TILE_STAGES], (kk / TILE_STAGES) & 1u);
+        }
+    } else if constexpr (PAIR) {
+        // ---------------- consumers: two x-adjacent nodes per thread ----------
+        const int t = threadIdx.x;    // nodes x0 + 2t, x0 + 2t + 1
+        const size_t N = p.N;
+        const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
+        const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
+        uint32_t k = 0;
+        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
+            const uint32_t s = k % TILE_STAGES;
+            const uint32_t par = (k / TILE_STAGES) & 1u;
+            if (!mbar_wait(&full[s], par)) break;
+            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+            const int x = (int)(xt * TILE_W) + 2 * t;
+            const uint32_t n0 = ((uint32_t)z * (uint32_t)ny + (uint32_t)y) * (uint32_t)p.nx + (uint32_t)x;
+            const T* st = stages + (size_t)s * Q * RP;
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+            const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
+            const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
+            const bool wrap_lo = x == 0, wrap_hi = x + 1 == p.nx - 1;
+            const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
+            F2 d[19], dl[19], q[21], ql[21];
+            if (!wall_row) {
+                // no bounced link: every source pair at its x-shift in the stage
+#pragma unroll
                 for (int a = 0; a < 19; ++a) {
                     int ex, ey, ez;
                     dir19(a, ex, ey, ez);
-                    const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
-                    const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
-                    const bool sol = plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
-                    const int row = sol ? OPP[a] * (int)tg.plane + z * ny + y : a * (int)tg.plane + zs * ny + ys;
-                    tma_load_row(st + a * RP, &tmf, xs, row, &full[s]);
+                    d[a] = unscale<ST>(p, smem_pair<ST>(st + a * RP, TILE_HALO + 2 * t - ex, ex == 0));
                 }
                 if (MHD) {
+#pragma unroll
                     for (int j = 0; j < 3; ++j)
+#pragma unroll
                         for (int a = 0; a < 7; ++a) {
                             int ex, ey, ez;
                             dir19(a, ex, ey, ez);
-                            const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
-                            const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
-                            const bool sol =
-                                plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
-                            const int row = sol ? (j * 7 + OPP[a]) * (int)tg.plane + z * ny + y
-                                                : (j * 7 + a) * (int)tg.plane + zs * ny + ys;
-                            tma_load_row(st + (19 + j * 7 + a) * RP, &tmg, xs, row, &full[s]);
+                            q[j * 7 + a] =
+                                unscale<ST>(p, smem_pair<ST>(st + (19 + j * 7 + a) * RP, TILE_HALO + 2 * t - ex, ex == 0));
                         }
                 }
+                if (wrap_lo || wrap_hi) {
+                    // the pair at the periodic seam: one lane's x-shifted sources lie across it
+                    const int xw = wrap_lo ? p.nx - 1 : 0, sgn = wrap_lo ? 1 : -1;
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) {
+                        int ex, ey, ez;
+                        dir19(a, ex, ey, ez);
+                        if (ex != sgn) continue;
+                        const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+                        const float w =
+                            unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw));
+                        if (wrap_lo) d[a].v.x = w; else d[a].v.y = w;
+                    }
+                    if (MHD) {
+                        const int a = wrap_lo ? 1 : 2;
+                        for (int j = 0; j < 3; ++j) {
+                            const float w = unscale<ST>(
+                                p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw));
+                            if (wrap_lo) q[j * 7 + a].v.x = w; else q[j * 7 + a].v.y = w;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+            for (int a = 0; a < 19; ++a) {
+                int ex, ey, ez;
+                dir19(a, ex, ey, ez);
+                const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
+                const bool shifted = !sol && ex != 0;
+                F2 v = smem_pair<ST>(st + a * RP, TILE_HALO + 2 * t - (shifted ? ex : 0), !shifted);
+                if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                    const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+                    const int xw = ex > 0 ? p.nx - 1 : 0;
+                    const float w = Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw);
+                    if (ex > 0) v.v.x = w; else v.v.y = w;
+                }
+                d[a] = unscale<ST>(p, v);
             }
-            if (!ok) {
-                // leave no copy in flight: wait (bounded) for the stages already issued
-                const uint32_t issued = k;
-                const uint32_t first = issued > TILE_STAGES ? issued - TILE_STAGES : 0u;
-                for (uint32_t kk = first; kk < issued; ++kk)
-                    mbar_wait(&full[kk % TILE_STAGES], (kk / TILE_STAGES) & 1u);
+            if (MHD) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const F2 wall(0.25f * p.bwall_dev[j]);
+#pragma unroll
+                    for (int a = 0; a < 7; ++a) {
+                        int ex, ey, ez;
+                        dir19(a, ex, ey, ez);
+                        const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
+                        const bool shifted = !sol && ex != 0;
+                        F2 v = smem_pair<ST>(st + (19 + j * 7 + a) * RP, TILE_HALO + 2 * t - (shifted ? ex : 0),
+                                             !shifted);
+                        if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                            const int xw = ex > 0 ? p.nx - 1 : 0;
+                            const float w =
+                                Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw);
+                            if (ex > 0) v.v.x = w; else v.v.y = w;
+                        }
+                        v = unscale<ST>(p, v);
+                        q[j * 7 + a] = sol ? wall - v : v;
+                    }
+                }
             }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            pair_from_sources<ST, MHD, MODE>(p, b, n0, d, dl, q, ql, acc);
         }
     } else {
         // ---------------- consumers: one node per thread ----------------------
@@ -248,7 +374,45 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, 
             const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
             const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
             const bool wrap_lo = x == 0, wrap_hi = x == p.nx - 1;
+            const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
             float d[19], dl[19], q[21], ql[21];
+            if (!wall_row) {
+                // no bounced link: every source at its x-shift in the stage
+#pragma unroll
+                for (int a = 0; a < 19; ++a) {
+                    int ex, ey, ez;
+                    dir19(a, ex, ey, ez);
+                    d[a] = unscale<ST>(p, smem_pop<ST>(st + a * RP + TILE_HALO + t - ex));
+                }
+                if (MHD) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) {
+                            int ex, ey, ez;
+                            dir19(a, ex, ey, ez);
+                            q[j * 7 + a] = unscale<ST>(p, smem_pop<ST>(st + (19 + j * 7 + a) * RP + TILE_HALO + t - ex));
+                        }
+                }
+                if (wrap_lo || wrap_hi) {
+                    // the thread at the periodic seam: its x-shifted sources lie across it
+                    const int xw = wrap_lo ? p.nx - 1 : 0, sgn = wrap_lo ? 1 : -1;
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) {
+                        int ex, ey, ez;
+                        dir19(a, ex, ey, ez);
+                        if (ex != sgn) continue;
+                        const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+                        d[a] = unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw));
+                    }
+                    if (MHD) {
+                        const int a = wrap_lo ? 1 : 2;
+                        for (int j = 0; j < 3; ++j)
+                            q[j * 7 + a] = unscale<ST>(
+                                p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw));
+                    }
+                }
+            } else {
 #pragma unroll
             for (int a = 0; a < 19; ++a) {
                 int ex, ey, ez;
@@ -282,6 +446,7 @@ __global__ void __launch_bounds__(TILE_THREADS) tile_kernel(const StepParams p, 
                         q[j * 7 + a] = sol ? wall - v : v;
                     }
                 }
+            }
             }
             // the stage is no longer needed: hand it back to the producer
             __syncwarp();
@@ -339,19 +504,20 @@ inline bool make_row_map(CUtensorMap* map, const void* base, int nx, unsigned lo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int ST, bool MHD, int MODE>
+template <int ST, bool MHD, int MODE, bool PAIR>
 cudaError_t launch_tile(const StepParams& p, const StepBuffers& b, cudaStream_t st, unsigned* nblocks)
 {
+    constexpr int TILE_THREADS = tile_threads<PAIR>();
     static int max_blocks = 0;   // resident blocks for the whole GPU (per instantiation, first device used)
     constexpr size_t smem = tile_smem_bytes<ST, MHD>();
     if (max_blocks == 0) {
-        cudaError_t e = cudaFuncSetAttribute(tile_kernel<ST, MHD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(tile_kernel<ST, MHD, MODE, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel<ST, MHD, MODE>, TILE_THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel<ST, MHD, MODE, PAIR>, TILE_THREADS, smem);
         if (e != cudaSuccess) return e;
         max_blocks = sms * (per_sm > 0 ? per_sm : 1);
     }
@@ -375,7 +541,7 @@ cudaError_t launch_tile(const StepParams& p, const StepBuffers& b, cudaStream_t 
     unsigned grid = (unsigned)(tg.ntiles < (uint32_t)max_blocks ? tg.ntiles : (uint32_t)max_blocks);
     const unsigned partial_cap = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
     if (grid > partial_cap) grid = partial_cap;
-    tile_kernel<ST, MHD, MODE><<<grid, TILE_THREADS, smem, st>>>(p, b, tg, mf, mg);
+    tile_kernel<ST, MHD, MODE, PAIR><<<grid, TILE_THREADS, smem, st>>>(p, b, tg, mf, mg);
     if (nblocks) *nblocks = grid;
     return cudaGetLastError();
 }
