@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--batch-storage", choices=["f32", "f32c"], default="f32c",
                     help="f32c by default: with F32 storage these ducts stall near r = 3e-8 (measured)")
     ap.add_argument("--batch-max-steps", type=int, default=50_000)
+    ap.add_argument("--batch-tol", type=float, default=3e-8,
+                    help="3e-8 by default: these ducts (nu = 0.1, |u| ~ 1e-3) settle at r = 1.2-3.6e-8 in FP32 "
+                         "arithmetic (measured with F32 and F32C storage), below which 1e-8 is not reached")
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -507,7 +510,7 @@ def run_batch(args, rank, ws):
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        st, res, sec = B.solve(1e-8, args.batch_max_steps, use_graph=True)
+        st, res, sec = B.solve(args.batch_tol, args.batch_max_steps, use_graph=True)
     sec = max_over_ranks(sec, ws)
     # node updates: each domain marched to its convergence level + 1 (or the cap)
     updates = 0
@@ -526,7 +529,8 @@ def run_batch(args, rank, ws):
                    if any(x is not None for x in v) else None} for k, v in by.items()}
     B.close()
     return {
-        "metric": "aggregate MLUPS of the batched steady solve (64 ducts, one persistent launch) to r <= 1e-8",
+        "metric": f"aggregate MLUPS of the batched steady solve (64 ducts, one persistent launch) to r <= "
+                  f"{args.batch_tol:g}",
         "value": round(updates / sec / 1e6 * ws, 1), "unit": "MLUPS", "n_gpus": ws, "steps": 1, "warmup": 0,
         "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
@@ -534,7 +538,9 @@ def run_batch(args, rank, ws):
                                "round-robin after seeded shuffle, nu=eta=0.1, chi=0.01, Fx=1e-6, "
                                + args.batch_storage + " storage", "nodes": sum(m["n"] ** 3 for m in meta),
                    "launch": {"block_threads": bt, "blocks_per_sm": bps, "autotune_s_per_step": sps}},
-        "status": st, "per_gamma": summary, "domains": per, "clocks": clk.summary(),
+        "status": st, "tol": args.batch_tol, "max_steps": args.batch_max_steps, "per_gamma": summary,
+        "converged": sum(1 for r in res if r["converged"]), "diverged": sum(1 for r in res if r["nonfinite"]),
+        "domains": per, "clocks": clk.summary(),
     }
 
 

@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 namespace glbe {
 
 constexpr int TILE_W = 128;                          // nodes per tile (one per consumer thread)
@@ -33,13 +35,18 @@ constexpr int TILE_BOX = TILE_W + 2 * TILE_HALO;     // elements per row copy
 // Pipeline depth: four stages for the flow lattice; two when the 21 D3Q7
 // rows are staged as well (a stage then holds 40 rows).
 template <bool MHD>
-constexpr int tile_stages() { return MHD ? 2 : 4; }
-// Consumer warps per block: one node per thread (4 warps), or two x-adjacent
-// nodes per thread with packed FP32x2 arithmetic (2 warps); plus the producer.
+constexpr int tile_stages() { return MHD ? 2 : 3; }
+// Warps per block: one node per thread (4 warps), or two x-adjacent nodes per
+// thread with packed FP32x2 arithmetic (2 warps).
 template <bool PAIR>
 constexpr int tile_consumer_warps() { return PAIR ? TILE_W / 64 : TILE_W / 32; }
 template <bool PAIR>
-constexpr int tile_threads() { return 32 * (tile_consumer_warps<PAIR>() + 1); }
+constexpr int tile_threads() { return 32 * tile_consumer_warps<PAIR>(); }
+// Resident blocks the register allocation is held to: the paired flow-only
+// form fits 96 registers (10 blocks of 64 threads per SM); the other forms
+// are left to the compiler.
+template <bool PAIR, bool MHD>
+constexpr int tile_min_blocks() { return PAIR && !MHD ? 10 : 1; }
 constexpr unsigned long long TILE_WAIT_NS = 2000000000ull;   // 2 s per wait at most
 // Hint for the time a waiting thread may be suspended inside one try_wait
 // (it resumes when the phase completes): waiting warps then take no issue
@@ -177,10 +184,9 @@ static __constant__ int c_tile_ez[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1,
 static __constant__ int c_tile_opp[19] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
 
 template <int ST, bool MHD, int MODE, bool PAIR>
-__global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepParams p, const StepBuffers b,
-                                                            const TileGeom tg,
-                                                            const __grid_constant__ CUtensorMap tmf,
-                                                            const __grid_constant__ CUtensorMap tmg)
+__global__ void __launch_bounds__(tile_threads<PAIR>(), tile_min_blocks<PAIR, MHD>())
+    tile_kernel(const StepParams p, const StepBuffers b, const TileGeom tg, const __grid_constant__ CUtensorMap tmf,
+                const __grid_constant__ CUtensorMap tmg)
 {
     using S = Store<ST>;
     using T = typename S::T;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepPa
     constexpr int RP = tile_pitch<ST>();
     constexpr uint32_t TILE_STAGES = (uint32_t)tile_stages<MHD>();
     constexpr uint32_t STAGE_TX = (uint32_t)(Q * TILE_BOX * sizeof(T));
-    constexpr int TILE_CONSUMER_WARPS = tile_consumer_warps<PAIR>();
+    constexpr int TILE_WARPS = tile_consumer_warps<PAIR>();
     constexpr int TILE_THREADS = tile_threads<PAIR>();
     if (b.stop != nullptr && *b.stop) return;
 
@@ -199,75 +205,76 @@ __global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepPa
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < TILE_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TILE_CONSUMER_WARPS);
+            mbar_init(&empty[s], TILE_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int t = threadIdx.x;
     const int ny = p.ny, nz = p.nz;
+    const size_t N = p.N;
+    const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
+    const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
-    if (warp == TILE_CONSUMER_WARPS) {
-        // ---------------- producer warp: lane r issues row copy r (and r + 32) --
-        uint32_t k = 0;
-        bool ok = true;
-        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
-            const uint32_t s = k % TILE_STAGES;
-            const uint32_t par = (k / TILE_STAGES) & 1u;
-            int got = 0;
-            if (lane == 0) got = mbar_wait(&empty[s], par ^ 1u) ? 1 : 0;
-            if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], STAGE_TX);
-            __syncwarp();
-            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
-            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
-            const int xs = (int)(xt * TILE_W) - TILE_HALO;
-            T* st = stages + (size_t)s * Q * RP;
-            for (int rr = lane; rr < Q; rr += 32) {
-                // row rr of the stage: f direction rr, or g component j, direction a
-                const int a = rr < 19 ? rr : (rr - 19) % 7;
-                const int arr = rr < 19 ? rr : rr - 19;   // population array index within f or g
-                const int ey = c_tile_ey[a], ez = c_tile_ez[a];
-                const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
-                const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
-                const bool sol = plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
-                const int src_arr = sol ? arr - a + c_tile_opp[a] : arr;   // bounced: the opposite population
-                const int row = sol ? src_arr * (int)tg.plane + z * ny + y : src_arr * (int)tg.plane + zs * ny + ys;
-                tma_load_row(st + rr * RP, rr < 19 ? &tmf : &tmg, xs, row, &full[s]);
-            }
+    // Warp 0 fills a stage with the rows of a tile: lane r issues row copy r
+    // (and r + 32), all completing on the stage's full barrier.
+    auto issue = [&](uint32_t tile, uint32_t s) {
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], STAGE_TX);
+        __syncwarp();
+        const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+        const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+        const int xs = (int)(xt * TILE_W) - TILE_HALO;
+        T* st = stages + (size_t)s * Q * RP;
+        for (int rr = lane; rr < Q; rr += 32) {
+            // row rr of the stage: f direction rr, or g component j, direction a
+            const int a = rr < 19 ? rr : (rr - 19) % 7;
+            const int arr = rr < 19 ? rr : rr - 19;   // population array index within f or g
+            const int ey = c_tile_ey[a], ez = c_tile_ez[a];
+            const int ys = y - ey < 0 ? ny - 1 : (y - ey >= ny ? 0 : y - ey);
+            const int zs = z - ez < 0 ? nz - 1 : (z - ez >= nz ? 0 : z - ez);
+            const bool sol = plane_solid(ys, ny, p.wlo[1], p.whi[1]) || plane_solid(zs, nz, p.wlo[2], p.whi[2]);
+            const int src_arr = sol ? arr - a + c_tile_opp[a] : arr;   // bounced: the opposite population
+            const int row = sol ? src_arr * (int)tg.plane + z * ny + y : src_arr * (int)tg.plane + zs * ny + ys;
+            tma_load_row(st + rr * RP, rr < 19 ? &tmf : &tmg, xs, row, &full[s]);
         }
-        if (!ok && lane == 0) {
-            // leave no copy in flight: wait (bounded) for the stages already issued
-            const uint32_t issued = k;
-            const uint32_t first = issued > TILE_STAGES ? issued - TILE_STAGES : 0u;
-            for (uint32_t kk = first; kk < issued; ++kk)
-                mbar_wait(&full[kk % TILE_STAGES], (kk / TILE_STAGES) & 1u);
+    };
+
+    uint32_t issued = 0;   // tiles issued by warp 0
+    if (warp == 0) {
+        for (uint32_t j = 0; j < TILE_STAGES; ++j) {
+            const uint32_t tile = blockIdx.x + j * gridDim.x;
+            if (tile >= tg.ntiles) break;
+            issue(tile, j);
+            ++issued;
         }
-    } else if constexpr (PAIR) {
-        // ---------------- consumers: two x-adjacent nodes per thread ----------
-        const int t = threadIdx.x;    // nodes x0 + 2t, x0 + 2t + 1
-        const size_t N = p.N;
-        const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
-        const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
-        uint32_t k = 0;
-        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
-            const uint32_t s = k % TILE_STAGES;
-            const uint32_t par = (k / TILE_STAGES) & 1u;
-            if (!mbar_wait(&full[s], par)) break;
-            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
-            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
-            const int x = (int)(xt * TILE_W) + 2 * t;
-            const uint32_t n0 = ((uint32_t)z * (uint32_t)ny + (uint32_t)y) * (uint32_t)p.nx + (uint32_t)x;
-            const T* st = stages + (size_t)s * Q * RP;
-            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-            const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-            const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
-            const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
+    }
+    bool ok = true;
+    uint32_t k = 0;
+    for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
+        const uint32_t s = k % TILE_STAGES;
+        const uint32_t par = (k / TILE_STAGES) & 1u;
+        const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
+        const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
+        const int x = (int)(xt * TILE_W) + (PAIR ? 2 * t : t);
+        const uint32_t n = ((uint32_t)z * (uint32_t)ny + (uint32_t)y) * (uint32_t)p.nx + (uint32_t)x;
+        using V = typename std::conditional<PAIR, F2, float>::type;
+        // the node's other inputs, loaded while the stage may still be in flight
+        NodeIn<V> in;
+        if constexpr (PAIR) in = pair_inputs<MHD, MODE>(p, b, n);
+        else in = node_inputs<MHD, MODE>(p, b, n);
+        if (!mbar_wait(&full[s], par)) { ok = false; break; }
+        const T* st = stages + (size_t)s * Q * RP;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
+        const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
+        V d[19], dl[19], q[21], ql[21];
+        if constexpr (PAIR) {
             const bool wrap_lo = x == 0, wrap_hi = x + 1 == p.nx - 1;
             const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
-            F2 d[19], dl[19], q[21], ql[21];
             if (!wall_row) {
                 // no bounced link: every source pair at its x-shift in the stage
 #pragma unroll
@@ -349,33 +356,9 @@ __global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepPa
                 }
             }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-            pair_from_sources<ST, MHD, MODE>(p, b, n0, d, dl, q, ql, acc);
-        }
-    } else {
-        // ---------------- consumers: one node per thread ----------------------
-        const int t = threadIdx.x;
-        const size_t N = p.N;
-        const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
-        const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
-        uint32_t k = 0;
-        for (uint32_t tile = blockIdx.x; tile < tg.ntiles; tile += gridDim.x, ++k) {
-            const uint32_t s = k % TILE_STAGES;
-            const uint32_t par = (k / TILE_STAGES) & 1u;
-            if (!mbar_wait(&full[s], par)) break;
-            const uint32_t xt = tile % tg.xtiles, r = tile / tg.xtiles;
-            const int y = (int)(tg.y0 + r % tg.nyf), z = (int)(tg.z0 + r / tg.nyf);
-            const int x = (int)(xt * TILE_W) + t;
-            const uint32_t n = ((uint32_t)z * (uint32_t)ny + (uint32_t)y) * (uint32_t)p.nx + (uint32_t)x;
-            const T* st = stages + (size_t)s * Q * RP;
-            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-            const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-            const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
-            const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
+        } else {
             const bool wrap_lo = x == 0, wrap_hi = x == p.nx - 1;
             const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
-            float d[19], dl[19], q[21], ql[21];
             if (!wall_row) {
                 // no bounced link: every source at its x-shift in the stage
 #pragma unroll
@@ -448,11 +431,27 @@ __global__ void __launch_bounds__(tile_threads<PAIR>()) tile_kernel(const StepPa
                 }
             }
             }
-            // the stage is no longer needed: hand it back to the producer
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-            node_from_sources<ST, MHD, MODE>(p, b, FieldOut{nullptr, nullptr, nullptr}, n, d, dl, q, ql, acc);
         }
+        // the stage is no longer needed: release it; warp 0 refills it with
+        // the tile TILE_STAGES ahead once every warp has released it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (warp == 0) {
+            const uint32_t next = tile + TILE_STAGES * gridDim.x;
+            if (next < tg.ntiles) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait(&empty[s], par) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
+                issue(next, s);
+                ++issued;
+            }
+        }
+        if constexpr (PAIR) pair_from_sources<ST, MHD, MODE>(p, b, n, d, dl, q, ql, in, acc);
+        else node_from_sources<ST, MHD, MODE>(p, b, FieldOut{nullptr, nullptr, nullptr}, n, d, dl, q, ql, in, acc);
+    }
+    if (!ok && warp == 0 && lane == 0) {
+        // leave no copy in flight: wait (bounded) for the tiles issued but not consumed
+        for (uint32_t kk = k; kk < issued; ++kk) mbar_wait(&full[kk % TILE_STAGES], (kk / TILE_STAGES) & 1u);
     }
     if (MODE == MODE_STEP_RESID) block_partials<TILE_THREADS>(acc, b.partials);
 }
