@@ -41,6 +41,15 @@ W19 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
 
 DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 
+# DRAM bytes (read + write) per fluid node of one plain step of the default
+# (one-node) kernel, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# on the 256x128x128 duct (4,064,256 fluid nodes; profiles/step_kernel_bf16_duct.md),
+# scaled here by the fluid nodes of the timed duct: the traffic of a step is
+# proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
+# part of the written data is still in L2 when the kernel ends.
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": 285263872 / 4064256, "f16": 284678400 / 4064256,
+                                 "f32": 588947712 / 4064256}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -299,7 +308,9 @@ def run_glbe(args, rank, ws):
             "peak": hbm_peak,
             "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4),
-            "traffic": None,
+            "traffic": (round(STEP_TRAFFIC_B_PER_FLUID_NODE[args.storage] * fluid)
+                        if args.variant in (0, 1) and args.storage in STEP_TRAFFIC_B_PER_FLUID_NODE else None),
+            "traffic_note": "bytes per launch, ncu capture on the 256x128x128 duct scaled by fluid nodes",
             "kernel": "step_kernel (plain fused collide+stream)",
             "bytes_per_node": bpn,
             "kernel_ms": round(kern_ms, 5),
@@ -523,10 +534,16 @@ def run_batch(args, rank, ws):
     by = {}
     for q in per:
         key = f"gamma_{q['gamma']}"
-        by.setdefault(key, []).append(q["seconds"] if q["converged"] else None)
+        by.setdefault(key, []).append((q["seconds"], q["steps"]) if q["converged"] else None)
+
+    def median(xs):
+        xs = sorted(xs)
+        return xs[len(xs) // 2] if xs else None
+    # per-solve time: device seconds from the launch start to the domain's
+    # convergence (all domains share the launch), and its level count
     summary = {k: {"converged": sum(x is not None for x in v), "of": len(v),
-                   "median_s": sorted(x for x in v if x is not None)[len([x for x in v if x is not None]) // 2]
-                   if any(x is not None for x in v) else None} for k, v in by.items()}
+                   "median_s": median([x[0] for x in v if x is not None]),
+                   "median_steps": median([x[1] for x in v if x is not None])} for k, v in by.items()}
     B.close()
     return {
         "metric": f"aggregate MLUPS of the batched steady solve (64 ducts, one persistent launch) to r <= "

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define GLBE_ABI_VERSION 2
+#define GLBE_ABI_VERSION 3
 
 typedef struct glbe_ctx glbe_ctx;
 
@@ -178,6 +178,20 @@ glbe_status glbe_get_state(glbe_ctx* ctx, float* d_df, float* d_dg, float* d_FL)
  * level t >= 0.  Clears the residual snapshot, the residual record and a
  * divergence stop left by an earlier non-finite residual. */
 glbe_status glbe_set_state(glbe_ctx* ctx, const float* d_df, const float* d_dg, const float* d_FL, long t);
+
+/* Checkpoint / resume (the paper has no counterpart; a service of the
+ * library).  A checkpoint is one host buffer holding the raw state of the
+ * context: the populations in the storage type, the lagged Lorentz force,
+ * the force field, the velocity snapshot of the residual, the residual record,
+ * the time level and the residual counters.  Loading it into a context with
+ * the same grid, storage, coupling and force_field makes the following march
+ * bit for bit the one the saved context would have made (the residual history
+ * restarts empty).  Both calls synchronise the stream; the buffer is plain
+ * (pageable or pinned) host memory owned by the caller.  glbe_checkpoint_load
+ * returns GLBE_ERR_ARG for a buffer of another shape or library version. */
+glbe_status glbe_checkpoint_bytes(const glbe_ctx* ctx, size_t* bytes);
+glbe_status glbe_checkpoint_save(glbe_ctx* ctx, void* h_buf, size_t bytes);
+glbe_status glbe_checkpoint_load(glbe_ctx* ctx, const void* h_buf, size_t bytes);
 
 /* Current time level. */
 glbe_status glbe_time(const glbe_ctx* ctx, long* t);

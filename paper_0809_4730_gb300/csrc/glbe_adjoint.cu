@@ -358,6 +358,7 @@ glbe_status glbe_adjoint_workspace_bytes(const glbe_params* p, long nsteps, long
 glbe_status glbe_adjoint_steady(glbe_ctx* ctx, const float* d_w, double tol, long max_iters, void* d_work,
                                 size_t bytes, float* d_dQdF, long* iters_out, double* r_out)
 {
+    NvtxRange range_("glbe_adjoint_steady");
     CtxView v;
     glbe_status s = ctx_view(ctx, &v);
     if (s != GLBE_OK) return s;
@@ -457,6 +458,7 @@ glbe_status glbe_adjoint_steady(glbe_ctx* ctx, const float* d_w, double tol, lon
 glbe_status glbe_adjoint_unrolled(glbe_ctx* ctx, const float* d_w, long nsteps, long K, void* d_work, size_t bytes,
                                   float* d_dQdF)
 {
+    NvtxRange range_("glbe_adjoint_unrolled");
     CtxView v;
     glbe_status s = ctx_view(ctx, &v);
     if (s != GLBE_OK) return s;

@@ -543,6 +543,7 @@ glbe_status glbe_set_force_host(glbe_ctx* c, const float* h_F)
 
 glbe_status glbe_step_n(glbe_ctx* c, long n)
 {
+    NvtxRange range_("glbe_step_n");
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     if (n < 0) return fail(GLBE_ERR_ARG, "n must be >= 0");
     for (long k = 0; k < n; ++k) {
@@ -618,6 +619,7 @@ glbe_status glbe_history(glbe_ctx* c, glbe_residual_info* out, long cap, long* n
 
 glbe_status glbe_residual(glbe_ctx* c, glbe_residual_info* out)
 {
+    NvtxRange range_("glbe_residual");
     if (!c || !out) return fail(GLBE_ERR_ARG, "ctx or out is NULL");
     return read_record(c, out);
 }
@@ -655,6 +657,7 @@ static glbe_status build_chunk(glbe_ctx* c)
 
 glbe_status glbe_solve(glbe_ctx* c, double tol, long max_steps, long* steps_out, double* r_out)
 {
+    NvtxRange range_("glbe_solve");
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     if (!(tol > 0.0)) return fail(GLBE_ERR_ARG, "tol must be > 0");
     if (max_steps < 0) return fail(GLBE_ERR_ARG, "max_steps must be >= 0");
@@ -706,6 +709,7 @@ glbe_status glbe_solve(glbe_ctx* c, double tol, long max_steps, long* steps_out,
 
 glbe_status glbe_fields(glbe_ctx* c, float* d_rho, float* d_u, float* d_B)
 {
+    NvtxRange range_("glbe_fields");
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     StepBuffers b = buffers_for(c, c->t);
     const FieldOut fo{d_rho, d_u, c->prm.induction ? d_B : nullptr};
@@ -751,6 +755,136 @@ glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, co
     c->t_snap = -1;
     return GLBE_OK;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the raw state (populations in the storage type, the
+// lagged Lorentz force, the force field, the velocity snapshot, the residual
+// record and counters) in one host buffer, so that a resumed march is bit for
+// bit the uninterrupted one.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+    char magic[8];                 // "GLBECKP1"
+    uint32_t version, header_bytes;
+    int32_t nx, ny, nz, storage, induction, force_field;
+    int64_t t, t_snap, t_dev;
+    uint64_t N, f_bytes, g_bytes, total;
+    uint64_t reserved[4];
+};
+
+size_t ckpt_total(const glbe_ctx* c)
+{
+    const size_t fb = 19 * c->N * storage_bytes(c->prm.storage);
+    const size_t gb = c->prm.induction ? 21 * c->N * storage_bytes(c->prm.storage) : 0;
+    return sizeof(CkptHeader) + fb + gb + (c->prm.induction ? 3 * c->N * sizeof(float) : 0) +
+           (size_t)c->prm.force_field * c->N * sizeof(float) + 3 * c->N * sizeof(float) +
+           RECORD_STRIDE * sizeof(double);
+}
+
+}  // namespace
+
+extern "C" glbe_status glbe_checkpoint_bytes(const glbe_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(GLBE_ERR_ARG, "ctx or bytes is NULL");
+    *bytes = ckpt_total(c);
+    return GLBE_OK;
+}
+
+extern "C" glbe_status glbe_checkpoint_save(glbe_ctx* c, void* h_buf, size_t bytes)
+{
+    if (!c || !h_buf) return fail(GLBE_ERR_ARG, "ctx or buffer is NULL");
+    const size_t total = ckpt_total(c);
+    if (bytes < total) return fail(GLBE_ERR_ARG, "checkpoint buffer of %zu bytes is smaller than %zu", bytes, total);
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "checkpoint sync");
+    CkptHeader h{};
+    std::memcpy(h.magic, "GLBECKP1", 8);
+    h.version = 1;
+    h.header_bytes = sizeof(CkptHeader);
+    h.nx = c->prm.nx;
+    h.ny = c->prm.ny;
+    h.nz = c->prm.nz;
+    h.storage = c->prm.storage;
+    h.induction = c->prm.induction;
+    h.force_field = c->prm.force_field;
+    h.t = c->t;
+    h.t_snap = c->t_snap;
+    long long tdev = 0;
+    GLBE_CUDA(cudaMemcpy(&tdev, c->t_dev, sizeof tdev, cudaMemcpyDeviceToHost), "checkpoint t");
+    h.t_dev = tdev;
+    h.N = c->N;
+    h.f_bytes = 19 * c->N * storage_bytes(c->prm.storage);
+    h.g_bytes = c->prm.induction ? 21 * c->N * storage_bytes(c->prm.storage) : 0;
+    h.total = total;
+    char* o = static_cast<char*>(h_buf);
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const int s = (int)(c->t & 1);
+    GLBE_CUDA(cudaMemcpy(o, c->f[s], h.f_bytes, cudaMemcpyDeviceToHost), "checkpoint f");
+    o += h.f_bytes;
+    if (c->prm.induction) {
+        GLBE_CUDA(cudaMemcpy(o, c->g[s], h.g_bytes, cudaMemcpyDeviceToHost), "checkpoint g");
+        o += h.g_bytes;
+        GLBE_CUDA(cudaMemcpy(o, c->FL, 3 * c->N * sizeof(float), cudaMemcpyDeviceToHost), "checkpoint F_L");
+        o += 3 * c->N * sizeof(float);
+    }
+    if (c->prm.force_field) {
+        const size_t fb = (size_t)c->prm.force_field * c->N * sizeof(float);
+        GLBE_CUDA(cudaMemcpy(o, c->Ffield, fb, cudaMemcpyDeviceToHost), "checkpoint force");
+        o += fb;
+    }
+    GLBE_CUDA(cudaMemcpy(o, c->usnap, 3 * c->N * sizeof(float), cudaMemcpyDeviceToHost), "checkpoint snapshot");
+    o += 3 * c->N * sizeof(float);
+    GLBE_CUDA(cudaMemcpy(o, c->record, RECORD_STRIDE * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint record");
+    return GLBE_OK;
+}
+
+extern "C" glbe_status glbe_checkpoint_load(glbe_ctx* c, const void* h_buf, size_t bytes)
+{
+    if (!c || !h_buf) return fail(GLBE_ERR_ARG, "ctx or buffer is NULL");
+    CkptHeader h;
+    if (bytes < sizeof h) return fail(GLBE_ERR_ARG, "checkpoint buffer too small");
+    std::memcpy(&h, h_buf, sizeof h);
+    if (std::memcmp(h.magic, "GLBECKP1", 8) != 0 || h.version != 1 || h.header_bytes != sizeof h)
+        return fail(GLBE_ERR_ARG, "not a checkpoint of this library version");
+    if (h.nx != c->prm.nx || h.ny != c->prm.ny || h.nz != c->prm.nz || h.storage != c->prm.storage ||
+        h.induction != c->prm.induction || h.force_field != c->prm.force_field)
+        return fail(GLBE_ERR_ARG, "checkpoint of another grid, storage or coupling");
+    if (h.total != ckpt_total(c) || bytes < h.total) return fail(GLBE_ERR_ARG, "checkpoint size mismatch");
+    if (h.t < 0) return fail(GLBE_ERR_ARG, "checkpoint time level < 0");
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "restore sync");
+    const char* in = static_cast<const char*>(h_buf) + sizeof h;
+    const int s = (int)(h.t & 1);
+    GLBE_CUDA(cudaMemcpy(c->f[s], in, h.f_bytes, cudaMemcpyHostToDevice), "restore f");
+    in += h.f_bytes;
+    if (c->prm.induction) {
+        GLBE_CUDA(cudaMemcpy(c->g[s], in, h.g_bytes, cudaMemcpyHostToDevice), "restore g");
+        in += h.g_bytes;
+        GLBE_CUDA(cudaMemcpy(c->FL, in, 3 * c->N * sizeof(float), cudaMemcpyHostToDevice), "restore F_L");
+        in += 3 * c->N * sizeof(float);
+    }
+    if (c->prm.force_field) {
+        const size_t fb = (size_t)c->prm.force_field * c->N * sizeof(float);
+        GLBE_CUDA(cudaMemcpy(c->Ffield, in, fb, cudaMemcpyHostToDevice), "restore force");
+        in += fb;
+    }
+    GLBE_CUDA(cudaMemcpy(c->usnap, in, 3 * c->N * sizeof(float), cudaMemcpyHostToDevice), "restore snapshot");
+    in += 3 * c->N * sizeof(float);
+    GLBE_CUDA(cudaMemcpy(c->record, in, RECORD_STRIDE * sizeof(double), cudaMemcpyHostToDevice), "restore record");
+    // residual level counter as saved; a fresh history; no pending stop
+    misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, (long long)h.t_dev, c->stop_dev, 0, c->tol_dev, 0.0, nullptr,
+                                            nullptr, 0);
+    GLBE_CUDA(cudaGetLastError(), "restore counters");
+    GLBE_CUDA(cudaMemsetAsync(c->hist_count, 0, sizeof(unsigned long long), c->stream), "restore history");
+    GLBE_CUDA(cudaStreamSynchronize(c->stream), "restore sync");
+    c->t = (long)h.t;
+    c->t_snap = (long)h.t_snap;
+    return GLBE_OK;
+}
+
+extern "C" {
 
 glbe_status glbe_time(const glbe_ctx* c, long* t)
 {

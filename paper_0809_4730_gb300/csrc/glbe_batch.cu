@@ -100,10 +100,8 @@ __device__ bool grid_barrier(BatchState* st, long long spin_limit)
     return ok;
 }
 
-// WIDE: the register budget of a launch with at most 256 threads per SM (no
-// spills); otherwise 128 registers per thread for up to 512 threads per SM.
-template <int ST, int BT, bool WIDE>
-__global__ void __launch_bounds__(BT, (WIDE ? 256 : 512) / BT) batch_kernel(const BatchDomain* __restrict__ doms, int ndom,
+template <int ST, int BT>
+__global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* __restrict__ doms, int ndom,
                                                    const uint32_t* __restrict__ tile_start, uint32_t ntiles,
                                                    double* __restrict__ partials, BatchState* st,
                                                    BatchDomainState* ds, long long t0, long long nsteps,
@@ -348,32 +346,22 @@ uint32_t total_tiles(const glbe_batch* b)
     return acc;
 }
 
-template <int ST, int BT, bool WIDE>
+template <int ST, int BT>
 void* kernel_ptr()
 {
-    return reinterpret_cast<void*>(&batch_kernel<ST, BT, WIDE>);
+    return reinterpret_cast<void*>(&batch_kernel<ST, BT>);
 }
 
-// The kernel for a launch of bt threads per block and bps blocks per SM: the
-// wide-register form when at most 256 threads per SM are resident.
-void* batch_kernel_for(int storage, int bt, int bps)
+void* batch_kernel_for(int storage, int bt)
 {
-    const bool wide = bt * bps <= 256;
-    if (storage == GLBE_F32) {
-        if (bt == 128) return wide ? kernel_ptr<ST_F32, 128, true>() : kernel_ptr<ST_F32, 128, false>();
-        return wide ? kernel_ptr<ST_F32, 256, true>() : kernel_ptr<ST_F32, 256, false>();
-    }
-    if (bt == 128) return wide ? kernel_ptr<ST_F32C, 128, true>() : kernel_ptr<ST_F32C, 128, false>();
-    return wide ? kernel_ptr<ST_F32C, 256, true>() : kernel_ptr<ST_F32C, 256, false>();
+    if (storage == GLBE_F32) return bt == 128 ? kernel_ptr<ST_F32, 128>() : kernel_ptr<ST_F32, 256>();
+    return bt == 128 ? kernel_ptr<ST_F32C, 128>() : kernel_ptr<ST_F32C, 256>();
 }
 
-// Most blocks of bt threads per SM (of the 128-register form, the one used
-// above 256 threads per SM).
 glbe_status max_blocks_per_sm(glbe_batch* b, int bt, int* out)
 {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_for(b->storage, bt, 512 / bt), bt,
-                                                                  0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_for(b->storage, bt), bt, 0);
     if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
     *out = nb;
     return GLBE_OK;
@@ -394,7 +382,7 @@ glbe_status launch_batch(glbe_batch* b, long long nsteps, double tol, cudaStream
     int absent = b->absent_block;
     void* args[] = {&b->d_doms, &b->n, &b->d_tile_start, (void*)&ntiles, &b->d_partials, &b->d_state, &b->d_dstate,
                     &t0, &nsteps, &snap, &tol, &spin, &absent};
-    cudaError_t e = cudaLaunchCooperativeKernel(batch_kernel_for(b->storage, b->block_threads, bps), dim3(grid),
+    cudaError_t e = cudaLaunchCooperativeKernel(batch_kernel_for(b->storage, b->block_threads), dim3(grid),
                                                 dim3(b->block_threads), args, 0, stream);
     if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "cooperative batch launch: %s", cudaGetErrorString(e));
     return GLBE_OK;
@@ -591,6 +579,7 @@ glbe_status glbe_batch_autotune(glbe_batch* b, int steps_per_trial, int* block_t
 glbe_status glbe_batch_solve(glbe_batch* b, double tol, long max_steps, int use_graph, glbe_batch_result* res,
                              double* seconds_out)
 {
+    NvtxRange range_("glbe_batch_solve");
     if (!b || !res) return fail(GLBE_ERR_ARG, "batch or results is NULL");
     if (!(tol > 0.0) || max_steps < 1) return fail(GLBE_ERR_ARG, "tol must be > 0 and max_steps >= 1");
     if (b->t != 0) return fail(GLBE_ERR_STATE, "a batch solves once from the rest state: call glbe_batch_reset");

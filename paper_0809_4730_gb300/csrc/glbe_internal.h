@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "glbe.h"
 
@@ -137,6 +138,15 @@ struct CtxView {
     cudaStream_t stream;
 };
 glbe_status ctx_view(glbe_ctx* c, CtxView* v);
+
+// NVTX range around a C-ABI call (visible in Nsight tools; header-only NVTX 3,
+// a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 size_t storage_value_bytes(int storage);   // bytes per population value (F32C: 4 + 2)
 
 }  // namespace glbe

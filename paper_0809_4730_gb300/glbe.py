@@ -87,6 +87,9 @@ _SIGNATURES = {
     "glbe_batch_destroy": (None, [C.c_void_p]),
     "glbe_step_residual_noalloc": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_int, C.c_long, _P(glbe_residual_info)]),
+    "glbe_checkpoint_bytes": (C.c_int, [C.c_void_p, _P(C.c_size_t)]),
+    "glbe_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "glbe_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "glbe_adjoint_workspace_bytes": (C.c_int, [_P(glbe_params), C.c_long, C.c_long, _P(C.c_size_t)]),
     "glbe_adjoint_steady": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_long, C.c_void_p, C.c_size_t,
                                       C.c_void_p, _P(C.c_long), _P(C.c_double)]),
@@ -117,7 +120,7 @@ def load(build_if_missing: bool = True):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.glbe_abi_version() != 2:
+            if lib.glbe_abi_version() != 3:
                 raise RuntimeError("libglbe ABI version mismatch")
             ps, isz = C.c_size_t(0), C.c_size_t(0)
             lib.glbe_struct_sizes(C.byref(ps), C.byref(isz))
@@ -231,6 +234,25 @@ def glbe_step_residual_noalloc(p: glbe_params, d_src, d_dst, d_force, d_u, have_
 def glbe_destroy(ctx):
     if ctx:
         load().glbe_destroy(ctx)
+
+
+def glbe_checkpoint_bytes(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(load().glbe_checkpoint_bytes(ctx, C.byref(n)), "glbe_checkpoint_bytes")
+    return n.value
+
+
+def glbe_checkpoint_save(ctx) -> bytes:
+    """The context's raw state as a bytes object (see include/glbe.h)."""
+    n = glbe_checkpoint_bytes(ctx)
+    buf = C.create_string_buffer(n)
+    _check(load().glbe_checkpoint_save(ctx, buf, n), "glbe_checkpoint_save")
+    return buf.raw
+
+
+def glbe_checkpoint_load(ctx, data: bytes):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(load().glbe_checkpoint_load(ctx, buf, len(data)), "glbe_checkpoint_load")
 
 
 def glbe_adjoint_workspace_bytes(p: glbe_params, nsteps: int = 0, K: int = 1) -> int:
@@ -444,6 +466,13 @@ class Solver:
 
     def sync(self):
         glbe_sync(self.ctx)
+
+    def checkpoint(self) -> bytes:
+        """Raw state for a bit-exact resume (glbe_checkpoint_save)."""
+        return glbe_checkpoint_save(self.ctx)
+
+    def restore(self, data: bytes):
+        glbe_checkpoint_load(self.ctx, data)
 
     # -- gradients of Q = sum w . u with respect to the force field ----------
     def _adjoint_work(self, nsteps: int, K: int):
