@@ -480,3 +480,64 @@ def test_residual_definition(orc):
         du = snaps[t][fluid] - snaps[t - 10][fluid]
         r = np.sqrt((du ** 2).sum() / (snaps[t][fluid] ** 2).sum())
         assert abs(h[t]["r"] - r) <= 1e-12 * r
+
+
+# ---------------------------------------------------------------------------
+# Three statements of the paper's discussion, reproduced by the oracle.
+# ---------------------------------------------------------------------------
+def test_poiseuille_centre_error_is_linear_in_nu_over_gamma(orc):
+    """Sec. 5 (figure of the Poiseuille error): the relative error of the
+    centre velocity is linear in nu/gamma.  With the paper's rates only
+    s_nu* depends on nu/gamma, and the bounce-back error of the MRT scheme is
+    affine in (1/s_nu* - 1/2) = 3 nu/gamma: a straight line to round-off."""
+    nu = 0.05
+    xs = np.array([0.05, 0.1, 0.2, 0.3, 0.5])
+    es = []
+    for x in xs:
+        _, u, a = _poiseuille(orc, nu / x, nu, 18, 1e-6, False, 1e-12)
+        c = len(u) // 2
+        es.append((u[c] - a[c]) / a[c])
+    es = np.array(es)
+    slope, icpt = np.polyfit(xs, es, 1)
+    assert np.abs(es - (slope * xs + icpt)).max() < 1e-5 * np.abs(es).max()
+    assert abs(slope * (xs[-1] - xs[0])) > 0.1 * np.abs(es).max()     # a real dependence
+
+
+def test_equal_preconditioning_of_both_lattices_converges_fastest(orc):
+    """Sec. 5 (Hartmann flow): with the GLBE at gamma = 0.1, the induction
+    lattice reaches the steady state in the fewest steps at gamma_m = gamma;
+    gamma_m = 1 is the slowest and gamma_m < gamma is slower again."""
+    def steps(gm, Ha=5, ny=34, nu=0.01):
+        L = (ny - 2) / 2
+        cfg = orc.Config(1, ny, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=0.1, nu=nu, F=(1e-6, 0, 0),
+                         induction=True, gamma_m=gm, eta=nu, chi=0.01, mu=1.0, B0=(0, Ha * nu / L, 0))
+        S = orc.Solver(cfg)
+        S.run(3_000_000, tol=1e-9)
+        assert S.hist[-1]["r"] <= 1e-9
+        return S.t
+    n = {gm: steps(gm) for gm in (1.0, 0.5, 0.1, 0.05)}
+    assert n[0.1] < n[0.05] < n[0.5] < n[1.0], n
+
+
+def test_induction_stays_solenoidal(orc):
+    """Sec. 4: the induction remains divergence free when it starts so.  A
+    periodic box with a smooth three-component force and an oblique applied
+    field: after 2000 steps the central-difference divergence of B is below
+    1e-4 of its largest derivative."""
+    n = 16
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    k = 2 * np.pi / n
+    F = np.stack([np.sin(k * z), np.sin(k * x), np.sin(k * y)], 0) * 2e-5
+    cfg = orc.Config(n, n, n, gamma=0.5, nu=0.05, induction=True, gamma_m=0.5, eta=0.05, chi=0.5, mu=1.0,
+                     B0=(0.01, 0.03, -0.02))
+    S = orc.Solver(cfg, np.ascontiguousarray(F.reshape(3, -1).T))
+    S.run(2000)
+    _, _, B, _ = S.fields()
+    Bf = B.reshape(n, n, n, 3)
+
+    def d(A, ax):
+        return (np.roll(A, -1, axis=ax) - np.roll(A, 1, axis=ax)) / 2
+    div = d(Bf[..., 0], 2) + d(Bf[..., 1], 1) + d(Bf[..., 2], 0)
+    grad = max(np.abs(d(Bf[..., c], ax)).max() for c in range(3) for ax in range(3))
+    assert grad > 1e-5
+    assert np.abs(div).max() < 1e-4 * grad
