@@ -7,7 +7,7 @@ error stays below n * 30 u * D.  For the 23-step cases that is 4e-5 D; the
 tests use 3e-5 D, the tail of a random walk being far below the worst case.
 BF16 storage rounds every population once per step to 8 bits (u = 2^-9 =
 2e-3 relative); FP16 with the default scale 4096 to 11 bits (u = 2.4e-4).
-At steady state the bar is the spec one: velocity L-infinity relative
+At steady state the bar is the stated one: velocity L-infinity relative
 error <= 1e-5 against the converged FP64 oracle.
 """
 import numpy as np
