@@ -145,6 +145,20 @@ StepParams glbe::make_step_params(const glbe_params* p)
     const double snu = 1.0 / (3.0 * p->nu / p->gamma + 0.5);
     for (int k = 0; k < 19; ++k) s.s[k] = (float)p->s[k];
     s.s[9] = s.s[11] = s.s[13] = s.s[14] = s.s[15] = (float)snu;
+    {
+        // folded relaxation per row (App. A tables): |row_k|^2, P_S,k and the
+        // constant c_k of S_k = c_k R_k
+        static const double norm2[19] = {19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8};
+        const double ig = 1.0 / p->gamma, ig2 = ig * ig;
+        const double ps[19] = {1, ig2, ig2, ig, ig, ig, ig, ig, ig, ig2, ig2, ig2, ig2, ig2, ig2, ig2, 1, 1, 1};
+        const double ck[19] = {0, 38, -11, 0, -2.0 / 3.0, 0, -2.0 / 3.0, 0, -2.0 / 3.0, 2, -1, 2, -1, 1, 1, 1, 0, 0, 0};
+        for (int k = 0; k < 19; ++k) {
+            const double sk = (k == 9 || k == 11 || k == 13 || k == 14 || k == 15) ? snu : p->s[k];
+            s.rl_a[k] = (float)(-sk / norm2[k]);
+            s.rl_b[k] = (float)((1.0 - 0.5 * sk) * ps[k] * ck[k] / norm2[k]);
+        }
+        s.rl_cons = (float)(ig / 10.0);
+    }
     s.force_ncomp = p->force_field;
     if (p->induction) {
         // tau_m* = eta / (gamma_m theta_m) + 1/2 (Eq. mrelaxationtime)

@@ -38,6 +38,11 @@ struct StepParams {
     float inv_gamma;      // 1/gamma
     float inv_gamma2;     // 1/gamma^2
     float s[19];          // Lambda* diagonal
+    // relaxation folded per moment row k (host, FP64 -> FP32): the collision
+    // change of row k is rl_a[k] n_k + rl_b[k] R_k (see flow_collide)
+    float rl_a[19];       // -s_k / |row_k|^2
+    float rl_b[19];       // (1 - s_k/2) P_S,k c_k / |row_k|^2
+    float rl_cons;        // 1 / (10 gamma): rows 3, 5, 7
     float F[3];           // uniform force
     int force_ncomp;      // 0, 1 (F_x field), 3
     // D3Q7 vector lattice

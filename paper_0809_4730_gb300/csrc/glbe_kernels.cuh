@@ -731,35 +731,32 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     const V n18 = GLBE_NK(H.P18, L.P18);
 #undef GLBE_NK
 
-    // preconditioned source moments S* = P_S S (App. A, Eq. precondsourceterm)
+    // delta_k = [-s_k n_k + (1 - s_k/2) S*_k] / |row_k|^2 with the
+    // preconditioned source moments S* = P_S S (App. A, Eq. precondsourceterm).
+    // Per row the host folds -s_k/|row_k|^2 into p.rl_a[k] and
+    // (1 - s_k/2) P_S,k c_k/|row_k|^2 into p.rl_b[k], where S_k = c_k R_k with
+    // R_k one of the force-velocity products below (c_k: 38 and -11 on rows 1,
+    // 2; -2/3 on 4, 6, 8; 2 and -1 on 9, 10 and 11, 12; 1 on 13-15).
+    // Conserved rows: delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
     const V Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
-    const V S1 = V(38.f) * Fu * ig2, S2 = V(-11.f) * Fu * ig2;
-    const V S4 = V(-2.f / 3.f) * Fx * ig, S6 = V(-2.f / 3.f) * Fy * ig, S8 = V(-2.f / 3.f) * Fz * ig;
-    const V S9 = V(2.f) * (V(2.f) * Fux - Fuy - Fuz) * ig2, S10 = V(-0.5f) * S9;
-    const V S11 = V(2.f) * (Fuy - Fuz) * ig2, S12 = V(-0.5f) * S11;
-    const V S13 = (Fx * uy + Fy * ux) * ig2;
-    const V S14 = (Fy * uz + Fz * uy) * ig2;
-    const V S15 = (Fx * uz + Fz * ux) * ig2;
-
-    // delta_k = [-s_k n_k + (1 - s_k/2) S*_k] / |row_k|^2; conserved rows:
-    // delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
-#define GLBE_DK(k, nk, Sk, inv) (vfma(V(-p.s[k]), (nk), V(1.f - 0.5f * p.s[k]) * (Sk)) * V(inv))
-    const V q1 = GLBE_DK(1, n1, S1, 1.f / 2394.f);
-    const V q2 = GLBE_DK(2, n2, S2, 1.f / 252.f);
-    const V q3 = Fx * ig * V(0.1f), q5 = Fy * ig * V(0.1f), q7 = Fz * ig * V(0.1f);
-    const V q4 = GLBE_DK(4, n4, S4, 1.f / 40.f);
-    const V q6 = GLBE_DK(6, n6, S6, 1.f / 40.f);
-    const V q8 = GLBE_DK(8, n8, S8, 1.f / 40.f);
-    const V q9 = GLBE_DK(9, n9, S9, 1.f / 36.f);
-    const V q10 = GLBE_DK(10, n10, S10, 1.f / 72.f);
-    const V q11 = GLBE_DK(11, n11, S11, 1.f / 12.f);
-    const V q12 = GLBE_DK(12, n12, S12, 1.f / 24.f);
-    const V q13 = GLBE_DK(13, n13, S13, 0.25f);
-    const V q14 = GLBE_DK(14, n14, S14, 0.25f);
-    const V q15 = GLBE_DK(15, n15, S15, 0.25f);
-    const V q16 = V(-p.s[16] * 0.125f) * n16;
-    const V q17 = V(-p.s[17] * 0.125f) * n17;
-    const V q18 = V(-p.s[18] * 0.125f) * n18;
+    const V R9 = V(2.f) * Fux - Fuy - Fuz, R11 = Fuy - Fuz;
+#define GLBE_DK(k, nk, Rk) vfma(V(p.rl_a[k]), (nk), V(p.rl_b[k]) * (Rk))
+    const V q1 = GLBE_DK(1, n1, Fu);
+    const V q2 = GLBE_DK(2, n2, Fu);
+    const V q3 = Fx * V(p.rl_cons), q5 = Fy * V(p.rl_cons), q7 = Fz * V(p.rl_cons);
+    const V q4 = GLBE_DK(4, n4, Fx);
+    const V q6 = GLBE_DK(6, n6, Fy);
+    const V q8 = GLBE_DK(8, n8, Fz);
+    const V q9 = GLBE_DK(9, n9, R9);
+    const V q10 = GLBE_DK(10, n10, R9);
+    const V q11 = GLBE_DK(11, n11, R11);
+    const V q12 = GLBE_DK(12, n12, R11);
+    const V q13 = GLBE_DK(13, n13, Fx * uy + Fy * ux);
+    const V q14 = GLBE_DK(14, n14, Fy * uz + Fz * uy);
+    const V q15 = GLBE_DK(15, n15, Fx * uz + Fz * ux);
+    const V q16 = V(p.rl_a[16]) * n16;
+    const V q17 = V(p.rl_a[17]) * n17;
+    const V q18 = V(p.rl_a[18]) * n18;
 #undef GLBE_DK
 
     // om = T^t delta  (columns of T read from the basis polynomials); f~ = f + om

@@ -177,6 +177,154 @@ __device__ __forceinline__ void dir19(int a, int& ex, int& ey, int& ez)
     ez = E[a][2];
 }
 
+// What a consumer needs of its tile's row: the staged rows and the
+// neighbouring planes (with their wall flags) of the fluid row (y, z).
+template <class T>
+struct TileRowT {
+    const T* st;      // stage: row r of the 19 (+21) copies at st + r * pitch
+    int pitch;
+    int y, z, ym, yp, zm, zp;
+    bool sym, syp, szm, szp;
+};
+
+// Gather of one node (x = x0 + t) from the stage.  Rows without walls above
+// or below read every source at its x-shift; the node at the periodic seam
+// (x = 0 or nx - 1) takes the sources across it with plain loads.  Rows next
+// to a wall read a bounced link's source unshifted (the stage holds the
+// node row's opposite population there) and negate g's (anti-bounce-back).
+template <int ST, bool MHD>
+__device__ __forceinline__ void tile_gather_one(const StepParams& p, const TileRowT<typename Store<ST>::T>& R, int t,
+                                                int x, const typename Store<ST>::T* __restrict__ fs,
+                                                const typename Store<ST>::T* __restrict__ gs, float (&d)[19],
+                                                float (&q)[21])
+{
+    const size_t N = p.N;
+    const int ny = p.ny;
+    const bool wrap_lo = x == 0, wrap_hi = x == p.nx - 1;
+    const bool wall_row = R.sym || R.syp || R.szm || R.szp;
+    if (!wall_row && !wrap_lo && !wrap_hi) {
+        // the common case: no bounced link, no seam; every source at its x-shift
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            int ex, ey, ez;
+            dir19(a, ex, ey, ez);
+            d[a] = unscale<ST>(p, smem_pop<ST>(R.st + a * R.pitch + TILE_HALO + t - ex));
+        }
+        if (MHD) {
+#pragma unroll
+            for (int i = 0; i < 21; ++i) {
+                int ex, ey, ez;
+                dir19(i % 7, ex, ey, ez);
+                q[i] = unscale<ST>(p, smem_pop<ST>(R.st + (19 + i) * R.pitch + TILE_HALO + t - ex));
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        int ex, ey, ez;
+        dir19(a, ex, ey, ez);
+        const bool sol = wall_row && ((ey > 0 && R.sym) || (ey < 0 && R.syp) || (ez > 0 && R.szm) || (ez < 0 && R.szp));
+        d[a] = unscale<ST>(p, smem_pop<ST>(R.st + a * R.pitch + TILE_HALO + t - (sol ? 0 : ex)));
+        if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+            const int ys = ey > 0 ? R.ym : (ey < 0 ? R.yp : R.y), zs = ez > 0 ? R.zm : (ez < 0 ? R.zp : R.z);
+            const int xw = ex > 0 ? p.nx - 1 : 0;
+            d[a] = unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw));
+        }
+    }
+    if (MHD) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float wall = 0.25f * p.bwall_dev[j];
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                int ex, ey, ez;
+                dir19(a, ex, ey, ez);
+                const bool sol =
+                    wall_row && ((ey > 0 && R.sym) || (ey < 0 && R.syp) || (ez > 0 && R.szm) || (ez < 0 && R.szp));
+                float v = unscale<ST>(p, smem_pop<ST>(R.st + (19 + j * 7 + a) * R.pitch + TILE_HALO + t - (sol ? 0 : ex)));
+                if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                    const int xw = ex > 0 ? p.nx - 1 : 0;
+                    v = unscale<ST>(p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)R.z * ny + R.y) * p.nx + xw));
+                }
+                q[j * 7 + a] = sol ? wall - v : v;
+            }
+        }
+    }
+}
+
+// Gather of the node pair (x, x + 1), x = x0 + 2t, as FP32x2 lanes; the same
+// rules, with aligned pair reads where the x-shift is 0 and lane patches at
+// the periodic seam.
+template <int ST, bool MHD>
+__device__ __forceinline__ void tile_gather_pair(const StepParams& p, const TileRowT<typename Store<ST>::T>& R, int t,
+                                                 int x, const typename Store<ST>::T* __restrict__ fs,
+                                                 const typename Store<ST>::T* __restrict__ gs, F2 (&d)[19],
+                                                 F2 (&q)[21])
+{
+    const size_t N = p.N;
+    const int ny = p.ny;
+    const bool wrap_lo = x == 0, wrap_hi = x + 1 == p.nx - 1;
+    const bool wall_row = R.sym || R.syp || R.szm || R.szp;
+    if (!wall_row && !wrap_lo && !wrap_hi) {
+        // the common case: no bounced link, no seam; aligned pairs where e_x = 0
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            int ex, ey, ez;
+            dir19(a, ex, ey, ez);
+            d[a] = unscale<ST>(p, smem_pair<ST>(R.st + a * R.pitch, TILE_HALO + 2 * t - ex, ex == 0));
+        }
+        if (MHD) {
+#pragma unroll
+            for (int i = 0; i < 21; ++i) {
+                int ex, ey, ez;
+                dir19(i % 7, ex, ey, ez);
+                q[i] = unscale<ST>(p, smem_pair<ST>(R.st + (19 + i) * R.pitch, TILE_HALO + 2 * t - ex, ex == 0));
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        int ex, ey, ez;
+        dir19(a, ex, ey, ez);
+        const bool sol = wall_row && ((ey > 0 && R.sym) || (ey < 0 && R.syp) || (ez > 0 && R.szm) || (ez < 0 && R.szp));
+        const bool shifted = !sol && ex != 0;
+        F2 v = smem_pair<ST>(R.st + a * R.pitch, TILE_HALO + 2 * t - (shifted ? ex : 0), !shifted);
+        if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+            const int ys = ey > 0 ? R.ym : (ey < 0 ? R.yp : R.y), zs = ez > 0 ? R.zm : (ez < 0 ? R.zp : R.z);
+            const int xw = ex > 0 ? p.nx - 1 : 0;
+            const float w = Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw);
+            if (ex > 0) v.v.x = w; else v.v.y = w;
+        }
+        d[a] = unscale<ST>(p, v);
+    }
+    if (MHD) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const F2 wall(0.25f * p.bwall_dev[j]);
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                int ex, ey, ez;
+                dir19(a, ex, ey, ez);
+                const bool sol =
+                    wall_row && ((ey > 0 && R.sym) || (ey < 0 && R.syp) || (ez > 0 && R.szm) || (ez < 0 && R.szp));
+                const bool shifted = !sol && ex != 0;
+                F2 v = smem_pair<ST>(R.st + (19 + j * 7 + a) * R.pitch, TILE_HALO + 2 * t - (shifted ? ex : 0),
+                                     !shifted);
+                if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
+                    const int xw = ex > 0 ? p.nx - 1 : 0;
+                    const float w =
+                        Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)R.z * ny + R.y) * p.nx + xw);
+                    if (ex > 0) v.v.x = w; else v.v.y = w;
+                }
+                v = unscale<ST>(p, v);
+                q[j * 7 + a] = sol ? wall - v : v;
+            }
+        }
+    }
+}
+
 // The same tables for run-time indices (the producer lanes): e_y, e_z and
 // the opposite direction.
 static __constant__ int c_tile_ey[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
@@ -272,166 +420,9 @@ __global__ void __launch_bounds__(tile_threads<PAIR>(), tile_min_blocks<PAIR, MH
         const bool sym = plane_solid(ym, ny, p.wlo[1], p.whi[1]), syp = plane_solid(yp, ny, p.wlo[1], p.whi[1]);
         const bool szm = plane_solid(zm, nz, p.wlo[2], p.whi[2]), szp = plane_solid(zp, nz, p.wlo[2], p.whi[2]);
         V d[19], dl[19], q[21], ql[21];
-        if constexpr (PAIR) {
-            const bool wrap_lo = x == 0, wrap_hi = x + 1 == p.nx - 1;
-            const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
-            if (!wall_row) {
-                // no bounced link: every source pair at its x-shift in the stage
-#pragma unroll
-                for (int a = 0; a < 19; ++a) {
-                    int ex, ey, ez;
-                    dir19(a, ex, ey, ez);
-                    d[a] = unscale<ST>(p, smem_pair<ST>(st + a * RP, TILE_HALO + 2 * t - ex, ex == 0));
-                }
-                if (MHD) {
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-#pragma unroll
-                        for (int a = 0; a < 7; ++a) {
-                            int ex, ey, ez;
-                            dir19(a, ex, ey, ez);
-                            q[j * 7 + a] =
-                                unscale<ST>(p, smem_pair<ST>(st + (19 + j * 7 + a) * RP, TILE_HALO + 2 * t - ex, ex == 0));
-                        }
-                }
-                if (wrap_lo || wrap_hi) {
-                    // the pair at the periodic seam: one lane's x-shifted sources lie across it
-                    const int xw = wrap_lo ? p.nx - 1 : 0, sgn = wrap_lo ? 1 : -1;
-#pragma unroll
-                    for (int a = 1; a < 19; ++a) {
-                        int ex, ey, ez;
-                        dir19(a, ex, ey, ez);
-                        if (ex != sgn) continue;
-                        const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
-                        const float w =
-                            unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw));
-                        if (wrap_lo) d[a].v.x = w; else d[a].v.y = w;
-                    }
-                    if (MHD) {
-                        const int a = wrap_lo ? 1 : 2;
-                        for (int j = 0; j < 3; ++j) {
-                            const float w = unscale<ST>(
-                                p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw));
-                            if (wrap_lo) q[j * 7 + a].v.x = w; else q[j * 7 + a].v.y = w;
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-            for (int a = 0; a < 19; ++a) {
-                int ex, ey, ez;
-                dir19(a, ex, ey, ez);
-                const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
-                const bool shifted = !sol && ex != 0;
-                F2 v = smem_pair<ST>(st + a * RP, TILE_HALO + 2 * t - (shifted ? ex : 0), !shifted);
-                if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
-                    const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
-                    const int xw = ex > 0 ? p.nx - 1 : 0;
-                    const float w = Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw);
-                    if (ex > 0) v.v.x = w; else v.v.y = w;
-                }
-                d[a] = unscale<ST>(p, v);
-            }
-            if (MHD) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const F2 wall(0.25f * p.bwall_dev[j]);
-#pragma unroll
-                    for (int a = 0; a < 7; ++a) {
-                        int ex, ey, ez;
-                        dir19(a, ex, ey, ez);
-                        const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
-                        const bool shifted = !sol && ex != 0;
-                        F2 v = smem_pair<ST>(st + (19 + j * 7 + a) * RP, TILE_HALO + 2 * t - (shifted ? ex : 0),
-                                             !shifted);
-                        if (shifted && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
-                            const int xw = ex > 0 ? p.nx - 1 : 0;
-                            const float w =
-                                Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw);
-                            if (ex > 0) v.v.x = w; else v.v.y = w;
-                        }
-                        v = unscale<ST>(p, v);
-                        q[j * 7 + a] = sol ? wall - v : v;
-                    }
-                }
-            }
-            }
-        } else {
-            const bool wrap_lo = x == 0, wrap_hi = x == p.nx - 1;
-            const bool wall_row = sym || syp || szm || szp;   // the same for the whole tile
-            if (!wall_row) {
-                // no bounced link: every source at its x-shift in the stage
-#pragma unroll
-                for (int a = 0; a < 19; ++a) {
-                    int ex, ey, ez;
-                    dir19(a, ex, ey, ez);
-                    d[a] = unscale<ST>(p, smem_pop<ST>(st + a * RP + TILE_HALO + t - ex));
-                }
-                if (MHD) {
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-#pragma unroll
-                        for (int a = 0; a < 7; ++a) {
-                            int ex, ey, ez;
-                            dir19(a, ex, ey, ez);
-                            q[j * 7 + a] = unscale<ST>(p, smem_pop<ST>(st + (19 + j * 7 + a) * RP + TILE_HALO + t - ex));
-                        }
-                }
-                if (wrap_lo || wrap_hi) {
-                    // the thread at the periodic seam: its x-shifted sources lie across it
-                    const int xw = wrap_lo ? p.nx - 1 : 0, sgn = wrap_lo ? 1 : -1;
-#pragma unroll
-                    for (int a = 1; a < 19; ++a) {
-                        int ex, ey, ez;
-                        dir19(a, ex, ey, ez);
-                        if (ex != sgn) continue;
-                        const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
-                        d[a] = unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + ((size_t)zs * ny + ys) * p.nx + xw));
-                    }
-                    if (MHD) {
-                        const int a = wrap_lo ? 1 : 2;
-                        for (int j = 0; j < 3; ++j)
-                            q[j * 7 + a] = unscale<ST>(
-                                p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + ((size_t)z * ny + y) * p.nx + xw));
-                    }
-                }
-            } else {
-#pragma unroll
-            for (int a = 0; a < 19; ++a) {
-                int ex, ey, ez;
-                dir19(a, ex, ey, ez);
-                const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
-                const int idx = TILE_HALO + t - (sol ? 0 : ex);
-                d[a] = unscale<ST>(p, smem_pop<ST>(st + a * RP + idx));
-                if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
-                    const int ys = ey > 0 ? ym : (ey < 0 ? yp : y), zs = ez > 0 ? zm : (ez < 0 ? zp : z);
-                    const int xw = ex > 0 ? p.nx - 1 : 0;
-                    const size_t src = ((size_t)zs * ny + ys) * p.nx + xw;
-                    d[a] = unscale<ST>(p, Store<ST>::ld(fs + (size_t)a * N + src));
-                }
-            }
-            if (MHD) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const float wall = 0.25f * p.bwall_dev[j];
-#pragma unroll
-                    for (int a = 0; a < 7; ++a) {
-                        int ex, ey, ez;
-                        dir19(a, ex, ey, ez);
-                        const bool sol = (ey > 0 && sym) || (ey < 0 && syp) || (ez > 0 && szm) || (ez < 0 && szp);
-                        const int idx = TILE_HALO + t - (sol ? 0 : ex);
-                        float v = unscale<ST>(p, smem_pop<ST>(st + (19 + j * 7 + a) * RP + idx));
-                        if (!sol && ((ex > 0 && wrap_lo) || (ex < 0 && wrap_hi))) {
-                            const int xw = ex > 0 ? p.nx - 1 : 0;
-                            const size_t src = ((size_t)z * ny + y) * p.nx + xw;
-                            v = unscale<ST>(p, Store<ST>::ld(gs + (size_t)(j * 7 + a) * N + src));
-                        }
-                        q[j * 7 + a] = sol ? wall - v : v;
-                    }
-                }
-            }
-            }
-        }
+        const TileRowT<T> row{st, RP, y, z, ym, yp, zm, zp, sym, syp, szm, szp};
+        if constexpr (PAIR) tile_gather_pair<ST, MHD>(p, row, t, x, fs, gs, d, q);
+        else tile_gather_one<ST, MHD>(p, row, t, x, fs, gs, d, q);
         // the stage is no longer needed: release it; warp 0 refills it with
         // the tile TILE_STAGES ahead once every warp has released it
         __syncwarp();

@@ -226,6 +226,41 @@ def test_paired_tile_kernel_matches_paired_kernel_bitwise(orc, nx, storage, mhd)
     assert abs(r2.r - r4.r) <= 1e-5 * r2.r
 
 
+_CAPTURE_FIRST = """
+import sys
+import numpy as np
+import torch
+from paper_0809_4730_gb300.glbe import Solver
+kw = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 0), gamma=0.5, nu=0.1, F=(2e-5, -1e-5, 5e-6), storage="f32")
+out = []
+for v in (1, int(sys.argv[1])):
+    G = Solver(128, 9, 7, variant=v, **kw)
+    st, n, r = G.solve(1e-6, 200_000)    # the first launches of this process are captured in a graph
+    df, _, _ = G.get_state()
+    G.sync()
+    out.append((st, n, df.cpu().numpy()))
+assert out[0][0] == out[1][0] == 0, out
+assert abs(out[0][1] - out[1][1]) <= 10
+if sys.argv[1] == "3":
+    assert out[0][1] == out[1][1] and np.array_equal(out[0][2], out[1][2])
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_tile_kernel_first_used_inside_a_captured_solve(variant):
+    """In a fresh process whose first steps are the CUDA-graph chunks of
+    glbe_solve, the tile kernel's one-time set-up runs during stream capture;
+    the solve must match the one-node kernel's."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CAPTURE_FIRST, str(variant)], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-2000:]
+
+
 @pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2)])
 @pytest.mark.parametrize("mhd", [False, True])
 @pytest.mark.parametrize("variant", [3, 4])
