@@ -648,6 +648,7 @@ template <class V>
 struct Lin {
     V drho, mx, my, mz;          // rows 0, 3, 5, 7
     V M1, M2;                    // e, e^2 (rows 1, 2)
+    V E1, E2;                    // M1 + 11 drho and M2 - 3 drho (the parts of n_1, n_2 linear in f)
     V Qx, Qy, Qz;                // q (rows 4, 6, 8)
     V P9, P10, P11, P12, P13, P14, P15, P16, P17, P18;
 };
@@ -671,14 +672,18 @@ __device__ __forceinline__ Lin<V> linear_moments(const V (&d)[19])
     L.mz = Zax + Zxz + Zyz;
     L.M1 = V(-30.f) * d[0] - V(11.f) * Sax + V(8.f) * Sdg;
     L.M2 = V(12.f) * d[0] - V(4.f) * Sax + Sdg;
+    L.E1 = V(19.f) * (Sdg - d[0]);
+    L.E2 = V(9.f) * d[0] - V(7.f) * Sax - V(2.f) * Sdg;
     L.Qx = V(-4.f) * Xax + Xxy + Xxz;
     L.Qy = V(-4.f) * Yax + Yxy + Yyz;
     L.Qz = V(-4.f) * Zax + Zxz + Zyz;
     const V two(2.f);
-    L.P9 = two * Ax - Ay - Az + Gxy + Gxz - two * Gyz;
-    L.P10 = V(-4.f) * Ax + two * Ay + two * Az + Gxy + Gxz - two * Gyz;
-    L.P11 = Ay - Az + Gxy - Gxz;
-    L.P12 = V(-2.f) * Ay + two * Az + Gxy - Gxz;
+    const V a9 = two * Ax - Ay - Az, g9 = Gxy + Gxz - two * Gyz;     // axis and diagonal parts of rows 9, 10
+    const V a11 = Ay - Az, g11 = Gxy - Gxz;                          // ... of rows 11, 12
+    L.P9 = a9 + g9;
+    L.P10 = V(-2.f) * a9 + g9;
+    L.P11 = a11 + g11;
+    L.P12 = V(-2.f) * a11 + g11;
     L.P13 = d[7] - d[8] - d[9] + d[10];
     L.P14 = d[15] - d[16] - d[17] + d[18];
     L.P15 = d[11] - d[12] - d[13] + d[14];
@@ -703,29 +708,31 @@ template <class V, bool PRECISE>
 __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<V, PRECISE>& mm, V (&om)[19],
                                              V rho_inv, V jx, V jy, V jz, V Fx, V Fy, V Fz)
 {
-    const V ig(p.inv_gamma), ig2(p.inv_gamma2);
+    const V ig(p.inv_gamma);
     const V gri = ig * rho_inv;                   // 1/(gamma rho)
     const V ux = jx * rho_inv, uy = jy * rho_inv, uz = jz * rho_inv;
-    const V jxx = jx * jx, jyy = jy * jy, jzz = jz * jz, jj = jxx + jyy + jzz;
+    // the quadratic equilibrium terms j_a j_b / (gamma rho)
+    const V gjx = jx * gri, gjy = jy * gri, gjz = jz * gri;
+    const V xx = jx * gjx, yy = jy * gjy, zz = jz * gjz, jjg = xx + yy + zz;
     const Lin<V>& H = mm.H;
     const Lin<V>& L = mm.L;
 #define GLBE_NK(hi, lo) (PRECISE ? (hi) + (lo) : (hi))
     // n_k = f^_k - f^eq,*_k; the rest state contributes -11 rho0 to row 1 and
     // 3 rho0 to row 2 only, so the deviations' moments enter directly
-    const V n1 = GLBE_NK((H.M1 + V(11.f) * H.drho) - V(19.f) * jj * gri, (L.M1 + V(11.f) * L.drho));
-    const V n2 = GLBE_NK((H.M2 - V(3.f) * H.drho) + V(5.5f) * jj * gri, (L.M2 - V(3.f) * L.drho));
+    const V n1 = GLBE_NK(H.E1 - V(19.f) * jjg, L.E1);
+    const V n2 = GLBE_NK(H.E2 + V(5.5f) * jjg, L.E2);
     const V n4 = GLBE_NK(H.Qx, L.Qx) + V(2.f / 3.f) * jx;
     const V n6 = GLBE_NK(H.Qy, L.Qy) + V(2.f / 3.f) * jy;
     const V n8 = GLBE_NK(H.Qz, L.Qz) + V(2.f / 3.f) * jz;
-    const V e9 = (V(3.f) * jxx - jj) * gri;
-    const V e11 = (jyy - jzz) * gri;
+    const V e9 = V(3.f) * xx - jjg;
+    const V e11 = yy - zz;
     const V n9 = GLBE_NK(H.P9 - e9, L.P9);
     const V n10 = GLBE_NK(H.P10 + V(0.5f) * e9, L.P10);
     const V n11 = GLBE_NK(H.P11 - e11, L.P11);
     const V n12 = GLBE_NK(H.P12 + V(0.5f) * e11, L.P12);
-    const V n13 = GLBE_NK(H.P13 - jx * jy * gri, L.P13);
-    const V n14 = GLBE_NK(H.P14 - jy * jz * gri, L.P14);
-    const V n15 = GLBE_NK(H.P15 - jx * jz * gri, L.P15);
+    const V n13 = GLBE_NK(H.P13 - jx * gjy, L.P13);
+    const V n14 = GLBE_NK(H.P14 - jy * gjz, L.P14);
+    const V n15 = GLBE_NK(H.P15 - jx * gjz, L.P15);
     const V n16 = GLBE_NK(H.P16, L.P16);
     const V n17 = GLBE_NK(H.P17, L.P17);
     const V n18 = GLBE_NK(H.P18, L.P18);
