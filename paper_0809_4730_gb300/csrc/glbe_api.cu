@@ -175,11 +175,15 @@ StepParams glbe::make_step_params(const glbe_params* p)
     s.variant = p->variant;
     s.storage = p->storage;
     // interior nodes: on each axis lo = 1 + wall_lo, hi = n - 2 - wall_hi
-    // (neighbours neither on a wall plane nor across the periodic seam)
+    // (neighbours neither on a wall plane nor across the periodic seam); on
+    // an x axis without walls the whole axis, since the gather corrects the
+    // sources that cross the x seam (a warp covers x-consecutive nodes, so
+    // the seam nodes would otherwise split their warps between two paths)
     s.interior_ok = 1;
     const int n[3] = {p->nx, p->ny, p->nz};
     for (int d = 0; d < 3; ++d) {
-        const int lo = 1 + p->wall_lo[d], hi = n[d] - 2 - p->wall_hi[d];
+        int lo = 1 + p->wall_lo[d], hi = n[d] - 2 - p->wall_hi[d];
+        if (d == 0 && !p->wall_lo[0] && !p->wall_hi[0]) { lo = 0; hi = n[0] - 1; }
         if (hi < lo) s.interior_ok = 0;
         s.ilo[d] = (uint32_t)lo;
         s.ispan[d] = hi >= lo ? (uint32_t)(hi - lo) : 0u;

@@ -55,8 +55,10 @@ struct StepParams {
     float scale, inv_scale;
     int variant;          // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 TMA-staged tiles
     int storage;          // Storage of the buffers (for the automatic choice)
-    // interior nodes (no solid node among the 18 neighbours, no periodic wrap):
-    // x - ilo[0] <= ispan[0] (unsigned) and likewise y, z; interior_ok = 0 if none
+    // interior nodes (no solid node among the 18 neighbours, no periodic wrap
+    // on y and z; on an x axis without walls every x, the sources across the
+    // x seam corrected by -+nx): x - ilo[0] <= ispan[0] (unsigned) and
+    // likewise y, z; interior_ok = 0 if none
     int interior_ok;
     uint32_t ilo[3], ispan[3];
     long long doff[19];   // a N - (e_ax + e_ay nx + e_az nx ny): offset of the source of direction a

@@ -390,47 +390,79 @@ __device__ __forceinline__ void load_g(const StepParams& p, const typename Store
 }
 
 // Interior nodes: the node and its 18 neighbours are fluid and no neighbour
-// wraps around a periodic axis, so the source of direction a is the fixed
-// offset p.doff[a] = a N - (e_ax + e_ay nx + e_az nx ny) from the node, the
-// same for every such node (no geometry, no bounce-back choice).
-__device__ __forceinline__ bool is_interior(const StepParams& p, uint32_t n)
+// wraps around a periodic y or z axis, so the source of direction a is the
+// fixed offset p.doff[a] = a N - (e_ax + e_ay nx + e_az nx ny) from the node,
+// the same for every such node (no geometry, no bounce-back choice).  On an x
+// axis without walls the x-seam nodes are interior too: the source x - 1 of
+// x = 0 (directions with e_x = +1) lies nx further on (wp = nx), the source
+// x + 1 of x = nx - 1 (e_x = -1) nx back (wm = -nx); elsewhere wp = wm = 0.
+// (With walls on x no interior node lies on x = 0 or nx - 1.)
+__device__ __forceinline__ bool is_interior(const StepParams& p, uint32_t n, int& wp, int& wm)
 {
     if (!p.interior_ok) return false;
     const uint32_t zy = fdiv(n, p.div_nx);
     const uint32_t z = fdiv(n, p.div_nxy);
     const uint32_t x = n - zy * (uint32_t)p.nx;
     const uint32_t y = zy - z * (uint32_t)p.ny;
+    wp = x == 0u ? p.nx : 0;
+    wm = x == (uint32_t)p.nx - 1u ? -p.nx : 0;
     return (x - p.ilo[0]) <= p.ispan[0] && (y - p.ilo[1]) <= p.ispan[1] && (z - p.ilo[2]) <= p.ispan[2];
+}
+
+// x component of D3Q19 direction a (the order of include/glbe.h; its first
+// seven are the D3Q7 directions)
+__host__ __device__ constexpr int dir_ex(int a)
+{
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+           : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+
+// Source of direction a of an interior node from the node's own position
+// base0 and its x-seam corrected positions: fixed per a after unrolling.
+template <class P>
+__device__ __forceinline__ P seam_src(int a, P base0, P basep, P basem)
+{
+    return dir_ex(a) > 0 ? basep : dir_ex(a) < 0 ? basem : base0;
 }
 
 template <int ST, bool CG = false>
 __device__ __forceinline__ void load_f_interior(const StepParams& p, const typename Store<ST>::T* __restrict__ fs,
-                                                uint32_t n, float (&d)[19], float (&l)[19])
+                                                uint32_t n, int wp, int wm, float (&d)[19], float (&l)[19])
 {
-    const typename Store<ST>::T* __restrict__ fn = fs + n;
+    using T = typename Store<ST>::T;
+    const T* __restrict__ f0 = fs + n;
+    const T* __restrict__ fp = f0 + wp;
+    const T* __restrict__ fm = f0 + wm;
 #pragma unroll
-    for (int a = 0; a < 19; ++a) d[a] = unscale<ST>(p, ldp<ST, CG>(fn + p.doff[a]));
+    for (int a = 0; a < 19; ++a) d[a] = unscale<ST>(p, ldp<ST, CG>(seam_src(a, f0, fp, fm) + p.doff[a]));
     if constexpr (Store<ST>::COMP) {
-        const __half* __restrict__ fl = reinterpret_cast<const __half*>(fs + 19 * (size_t)p.N) + n;
+        const __half* __restrict__ l0 = reinterpret_cast<const __half*>(fs + 19 * (size_t)p.N) + n;
+        const __half* __restrict__ lp = l0 + wp;
+        const __half* __restrict__ lm = l0 + wm;
 #pragma unroll
-        for (int a = 0; a < 19; ++a) l[a] = ldlo<CG>(fl + p.doff[a]);
+        for (int a = 0; a < 19; ++a) l[a] = ldlo<CG>(seam_src(a, l0, lp, lm) + p.doff[a]);
     }
 }
 
 template <int ST, bool CG = false>
 __device__ __forceinline__ void load_g_interior(const StepParams& p, const typename Store<ST>::T* __restrict__ gs,
-                                                uint32_t n, float (&q)[21], float (&ql)[21])
+                                                uint32_t n, int wp, int wm, float (&q)[21], float (&ql)[21])
 {
+    using T = typename Store<ST>::T;
     const size_t N = p.N;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const typename Store<ST>::T* __restrict__ b = gs + (size_t)(j * 7) * N + n;
+        const T* __restrict__ b0 = gs + (size_t)(j * 7) * N + n;
+        const T* __restrict__ bp = b0 + wp;
+        const T* __restrict__ bm = b0 + wm;
 #pragma unroll
-        for (int a = 0; a < 7; ++a) q[j * 7 + a] = unscale<ST>(p, ldp<ST, CG>(b + p.doff[a]));
+        for (int a = 0; a < 7; ++a) q[j * 7 + a] = unscale<ST>(p, ldp<ST, CG>(seam_src(a, b0, bp, bm) + p.doff[a]));
         if constexpr (Store<ST>::COMP) {
-            const __half* __restrict__ bl = reinterpret_cast<const __half*>(gs + 21 * N) + (size_t)(j * 7) * N + n;
+            const __half* __restrict__ l0 = reinterpret_cast<const __half*>(gs + 21 * N) + (size_t)(j * 7) * N + n;
+            const __half* __restrict__ lp = l0 + wp;
+            const __half* __restrict__ lm = l0 + wm;
 #pragma unroll
-            for (int a = 0; a < 7; ++a) ql[j * 7 + a] = ldlo<CG>(bl + p.doff[a]);
+            for (int a = 0; a < 7; ++a) ql[j * 7 + a] = ldlo<CG>(seam_src(a, l0, lp, lm) + p.doff[a]);
         }
     }
 }
@@ -990,10 +1022,12 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
     const uint32_t n = inb ? i : 0u;
     const size_t N = p.N;
     float d[19], dl[19], q[21], ql[21];
-    if (inb && is_interior(p, n)) {
-        // no solid node and no periodic wrap around: every source at a fixed offset
-        load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, d, dl);
-        if (MHD) load_g_interior<ST, CG>(p, static_cast<const T*>(b.gsrc), n, q, ql);
+    int wp = 0, wm = 0;
+    if (inb && is_interior(p, n, wp, wm)) {
+        // no solid node and no y or z wrap around: every source at a fixed
+        // offset (x-seam sources corrected by wp, wm)
+        load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
+        if (MHD) load_g_interior<ST, CG>(p, static_cast<const T*>(b.gsrc), n, wp, wm, q, ql);
     } else {
         const Geo g = make_geo(p, n);
         if (!inb || g.solid) {
