@@ -81,14 +81,72 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
     const size_t N = p.N;
     const bool inb = i < p.N;
     const uint32_t n = inb ? i : 0u;
-    const Geo g = make_geo(p, n);
-    const bool fluid = inb && !g.solid;
     const float* __restrict__ lf = a.lam_in;
     const float* __restrict__ lg = a.lam_in + 19 * N;
     const float* __restrict__ lk = a.lam_in + 40 * N;
     float* __restrict__ of = a.lam_out;
     float* __restrict__ og = a.lam_out + 19 * N;
     float* __restrict__ ok = a.lam_out + 40 * N;
+    // linearisation point (the forward gather of level t: d, q) and
+    // v = P^t lam_{t+1} (vf, vg): the forward pull of slot a from (src, a),
+    // or from the node's own opposite slot o when bounced, read backwards
+    float d[19], dl[19], q[21], ql[21], vf[19], vg[21];
+    // compensated storage: the node update is linearised at high + low part
+    const auto fold_lo = [](auto& v, const auto& lo) {
+        if constexpr (S::COMP) {
+#pragma unroll
+            for (int k = 0; k < (int)(sizeof(v) / sizeof(v[0])); ++k) v[k] += lo[k];
+        }
+    };
+    bool fluid = inb;
+    int wp = 0, wm = 0;
+    if (inb && is_interior(p, n, wp, wm)) {
+        // every link is a plain one: slot o of the node x + e_o at the fixed
+        // offset toff[o] (x-seam targets corrected like the sources of opp(o))
+        load_f_interior<ST>(p, static_cast<const T*>(a.fsrc), n, wp, wm, d, dl);
+        fold_lo(d, dl);
+        if (MHD) {
+            load_g_interior<ST>(p, static_cast<const T*>(a.gsrc), n, wp, wm, q, ql);
+            fold_lo(q, ql);
+        }
+        const float* __restrict__ l0 = lf + n;
+#pragma unroll
+        for (int o = 0; o < 19; ++o) vf[o] = *(seam_src(dir_opp(o), l0, l0 + wp, l0 + wm) + p.toff[o]);
+        if (MHD) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float* __restrict__ b0 = lg + (size_t)(j * 7) * N + n;
+#pragma unroll
+                for (int o = 0; o < 7; ++o) vg[j * 7 + o] = *(seam_src(dir_opp(o), b0, b0 + wp, b0 + wm) + p.toff[o]);
+            }
+        }
+    } else {
+        const Geo g = make_geo(p, n);
+        fluid = inb && !g.solid;
+        if (fluid) {
+            load_f<ST>(p, static_cast<const T*>(a.fsrc), g, d, dl);
+            fold_lo(d, dl);
+            if (MHD) {
+                load_g<ST>(p, static_cast<const T*>(a.gsrc), g, q, ql);
+                fold_lo(q, ql);
+            }
+            vf[0] = lf[n];
+#define GLBE_ADJF(a_, o_, src, sol) vf[o_] = (sol) ? lf[(size_t)(a_) * N + n] : lf[(size_t)(o_) * N + (src)];
+            GLBE_DIRS(GLBE_ADJF)
+#undef GLBE_ADJF
+            if (MHD) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float* __restrict__ b = lg + (size_t)(j * 7) * N;
+                    vg[j * 7] = b[n];
+#define GLBE_ADJG(a_, o_, src, sol) \
+    vg[j * 7 + o_] = (sol) ? -b[(size_t)(a_) * N + n] : b[(size_t)(o_) * N + (src)];
+                    GLBE_DIRS7(GLBE_ADJG)
+#undef GLBE_ADJG
+                }
+            }
+        }
+    }
     if (!fluid) {
         if (inb) {
             for (int k = 0; k < 19; ++k) of[(size_t)k * N + n] = 0.f;
@@ -102,20 +160,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
                 for (int k = 0; k < 3; ++k) a.dsnap[(size_t)k * N + n] = 0.f;
         }
     } else {
-        // linearisation point: the forward gather of level t
-        float d[19], dl[19], q[21], ql[21];
-        load_f<ST>(p, static_cast<const T*>(a.fsrc), g, d, dl);
-        if constexpr (S::COMP) {
-#pragma unroll
-            for (int k = 0; k < 19; ++k) d[k] += dl[k];
-        }
         float FLp[3] = {0.f, 0.f, 0.f};
         if (MHD) {
-            load_g<ST>(p, static_cast<const T*>(a.gsrc), g, q, ql);
-            if constexpr (S::COMP) {
-#pragma unroll
-                for (int k = 0; k < 21; ++k) q[k] += ql[k];
-            }
             FLp[0] = a.FL[n];
             FLp[1] = a.FL[N + n];
             FLp[2] = a.FL[2 * N + n];
@@ -129,23 +175,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
             Fext[1] += __ldg(a.Ffield + N + n);
             Fext[2] += __ldg(a.Ffield + 2 * N + n);
         }
-        // v = P^t lam_{t+1}: the forward pull of slot a from (src, a), or from
-        // the node's own opposite slot o when bounced, read backwards
-        float vf[19], vg[21], vFL[3] = {0.f, 0.f, 0.f};
-        vf[0] = lf[n];
-#define GLBE_ADJF(a_, o_, src, sol) vf[o_] = (sol) ? lf[(size_t)(a_) * N + n] : lf[(size_t)(o_) * N + (src)];
-        GLBE_DIRS(GLBE_ADJF)
-#undef GLBE_ADJF
+        float vFL[3] = {0.f, 0.f, 0.f};
         if (MHD) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float* __restrict__ b = lg + (size_t)(j * 7) * N;
-                vg[j * 7] = b[n];
-#define GLBE_ADJG(a_, o_, src, sol) \
-    vg[j * 7 + o_] = (sol) ? -b[(size_t)(a_) * N + n] : b[(size_t)(o_) * N + (src)];
-                GLBE_DIRS7(GLBE_ADJG)
-#undef GLBE_ADJG
-            }
             vFL[0] = lk[n];
             vFL[1] = lk[N + n];
             vFL[2] = lk[2 * N + n];

@@ -193,7 +193,10 @@ StepParams glbe::make_step_params(const glbe_params* p)
                                  {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1},
                                  {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
     const long long Nn = (long long)p->nx * p->ny * p->nz, sx = 1, sy = p->nx, sz = (long long)p->nx * p->ny;
-    for (int a = 0; a < 19; ++a) s.doff[a] = a * Nn - (E[a][0] * sx + E[a][1] * sy + E[a][2] * sz);
+    for (int a = 0; a < 19; ++a) {
+        s.doff[a] = a * Nn - (E[a][0] * sx + E[a][1] * sy + E[a][2] * sz);
+        s.toff[a] = a * Nn + (E[a][0] * sx + E[a][1] * sy + E[a][2] * sz);
+    }
     return s;
 }
 

@@ -62,6 +62,8 @@ struct StepParams {
     int interior_ok;
     uint32_t ilo[3], ispan[3];
     long long doff[19];   // a N - (e_ax + e_ay nx + e_az nx ny): offset of the source of direction a
+    long long toff[19];   // o N + (e_ox + e_oy nx + e_oz nx ny): offset of the slot o the post-collision
+                          // population o of a node streams into (the transposed pull of the adjoint)
 };
 
 // Buffers of one launch.  Populations are deviations in the storage type,

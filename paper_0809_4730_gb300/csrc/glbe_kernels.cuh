@@ -417,6 +417,18 @@ __host__ __device__ constexpr int dir_ex(int a)
            : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
 }
 
+// direction opposite to D3Q19 direction a (the order of include/glbe.h)
+__host__ __device__ constexpr int dir_opp(int a)
+{
+    return a == 0 ? 0 : a <= 6 ? (a % 2 ? a + 1 : a - 1) : 7 + 4 * ((a - 7) / 4) + 3 - (a - 7) % 4;
+}
+
+static_assert(dir_opp(1) == 2 && dir_opp(4) == 3 && dir_opp(7) == 10 && dir_opp(8) == 9 && dir_opp(12) == 13 &&
+                  dir_opp(14) == 11 && dir_opp(16) == 17 && dir_opp(18) == 15,
+              "D3Q19 opposite directions");
+static_assert(dir_ex(dir_opp(9)) == -dir_ex(9) && dir_ex(dir_opp(13)) == -dir_ex(13) && dir_ex(15) == 0,
+              "D3Q19 x components");
+
 // Source of direction a of an interior node from the node's own position
 // base0 and its x-seam corrected positions: fixed per a after unrolling.
 template <class P>
@@ -1121,7 +1133,7 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
 }
 
 template <int ST, bool MHD, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
+__device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers& b, const FieldOut& fo)
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
@@ -1129,6 +1141,28 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
     scalar_node_step<ST, MHD, MODE>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    step_body<ST, MHD, MODE>(p, b, fo);
+}
+
+// The plain flow step held to MINB resident blocks of 256 threads per SM:
+// with 16-bit storage it fits 48 registers (five blocks, 40 warps, instead of
+// four).  A separate kernel because stating a minimum at all (even one block)
+// changes the register allocation of the forms left free.
+template <int ST, int MINB>
+__global__ void __launch_bounds__(STEP_THREADS, MINB)
+    step_kernel_dense(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    step_body<ST, false, MODE_STEP>(p, b, fo);
+}
+template <int ST>
+constexpr int step_dense_blocks()
+{
+    return (ST == ST_BF16 || ST == ST_F16) ? 5 : ST == ST_F32 ? 4 : 0;   // 0: the free kernel
 }
 
 // The update of the fluid node pair (n0, n0 + 1) from its gathered
@@ -1349,7 +1383,11 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b, const FieldOu
         if (nblocks) *nblocks = grid;
     } else {
         const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
-        step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+        constexpr int MINB = step_dense_blocks<ST>();
+        if constexpr (!MHD && MODE == MODE_STEP && MINB > 0)
+            step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+        else
+            step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         if (nblocks) *nblocks = grid;
     }
     return cudaGetLastError();
