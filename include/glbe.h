@@ -138,8 +138,13 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
  * The source may be freed after the copy completes on the stream. */
 glbe_status glbe_set_force(glbe_ctx* ctx, const float* d_F);
 
-/* Same from host memory (pinned memory makes the copy asynchronous; the host
- * buffer must stay valid until the stream reaches the copy). */
+/* Same from host memory.  The field applies to the steps enqueued after this
+ * call.  The host copy goes to a staging region of the workspace on the
+ * library's own copy stream, so it overlaps the steps already enqueued on the
+ * context's stream; that stream then waits for it and moves the field in with
+ * a device copy.  Pinned memory makes the host copy asynchronous.  The host
+ * buffer must stay valid until the copy completes, which is at the latest
+ * when the context's stream reaches the steps enqueued after this call. */
 glbe_status glbe_set_force_host(glbe_ctx* ctx, const float* h_F);
 
 /* Advances n >= 0 time steps (one fused kernel per step; the residual is

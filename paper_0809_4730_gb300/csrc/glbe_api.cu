@@ -53,7 +53,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t f[2], g[2], FL, Ffield, usnap, partials, record, hist, misc, total;
+    size_t f[2], g[2], FL, Ffield, usnap, partials, record, hist, misc, Fstage, total;
 };
 
 size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : (st == GLBE_F32C ? 6 : 2); }
@@ -82,6 +82,9 @@ Layout make_layout(const glbe_params* p)
     L.record = take(RECORD_STRIDE * sizeof(double));
     L.hist = take((size_t)HIST_CAP * RECORD_STRIDE * sizeof(double));
     L.misc = take(64);
+    // staging buffer of glbe_set_force_host (last, outside the region the
+    // initial memset clears)
+    L.Fstage = p->force_field ? take((size_t)p->force_field * N * sizeof(float)) : (size_t)-1;
     L.total = off;
     return L;
 }
@@ -321,6 +324,11 @@ struct glbe_ctx {
     cudaStream_t stream;
     cudaStream_t cap_stream;
     cudaGraphExec_t chunk;
+    // host force uploads: staged on their own stream (created on first use)
+    float* Fstage;
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_staged;       // the host copy into Fstage is complete
+    cudaEvent_t ev_stage_free;   // the hand-over from Fstage to Ffield is complete
 };
 
 namespace {
@@ -494,6 +502,7 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     c->g[1] = p->induction ? c->ws + L.g[1] : nullptr;
     c->FL = p->induction ? reinterpret_cast<float*>(c->ws + L.FL) : nullptr;
     c->Ffield = p->force_field ? reinterpret_cast<float*>(c->ws + L.Ffield) : nullptr;
+    c->Fstage = p->force_field ? reinterpret_cast<float*>(c->ws + L.Fstage) : nullptr;
     c->usnap = reinterpret_cast<float*>(c->ws + L.usnap);
     c->partials = reinterpret_cast<double*>(c->ws + L.partials);
     c->record = reinterpret_cast<double*>(c->ws + L.record);
@@ -515,6 +524,8 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     c->stream = static_cast<cudaStream_t>(p->stream);
     c->cap_stream = nullptr;
     c->chunk = nullptr;
+    c->copy_stream = nullptr;
+    c->ev_staged = c->ev_stage_free = nullptr;
 
     // rest state: all deviations zero (all-zero bits in every storage type)
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.usnap, c->stream);
@@ -537,6 +548,12 @@ void glbe_destroy(glbe_ctx* c)
     if (!c) return;
     if (c->chunk) cudaGraphExecDestroy(c->chunk);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->ev_staged) cudaEventDestroy(c->ev_staged);
+    if (c->ev_stage_free) cudaEventDestroy(c->ev_stage_free);
     delete c;
 }
 
@@ -556,9 +573,23 @@ glbe_status glbe_set_force_host(glbe_ctx* c, const float* h_F)
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     if (!c->prm.force_field) return fail(GLBE_ERR_STATE, "context was created with force_field = 0");
     if (!h_F) return fail(GLBE_ERR_ARG, "force field is NULL");
-    GLBE_CUDA(cudaMemcpyAsync(c->Ffield, h_F, (size_t)c->prm.force_field * c->N * sizeof(float),
-                              cudaMemcpyHostToDevice, c->stream),
-              "glbe_set_force_host");
+    const size_t bytes = (size_t)c->prm.force_field * c->N * sizeof(float);
+    if (!c->copy_stream) {
+        GLBE_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "glbe_set_force_host");
+        GLBE_CUDA(cudaEventCreateWithFlags(&c->ev_staged, cudaEventDisableTiming), "glbe_set_force_host");
+        GLBE_CUDA(cudaEventCreateWithFlags(&c->ev_stage_free, cudaEventDisableTiming), "glbe_set_force_host");
+    }
+    // The host copy runs on the copy stream into the staging buffer, so it
+    // overlaps the steps already enqueued on the context's stream (they read
+    // Ffield); the context's stream then waits for it and hands the field
+    // over with a device copy (Ffield keeps its address: captured graphs stay
+    // valid).  A second upload waits until the first hand-over is done.
+    GLBE_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_stage_free, 0), "glbe_set_force_host");
+    GLBE_CUDA(cudaMemcpyAsync(c->Fstage, h_F, bytes, cudaMemcpyHostToDevice, c->copy_stream), "glbe_set_force_host");
+    GLBE_CUDA(cudaEventRecord(c->ev_staged, c->copy_stream), "glbe_set_force_host");
+    GLBE_CUDA(cudaStreamWaitEvent(c->stream, c->ev_staged, 0), "glbe_set_force_host");
+    GLBE_CUDA(cudaMemcpyAsync(c->Ffield, c->Fstage, bytes, cudaMemcpyDeviceToDevice, c->stream), "glbe_set_force_host");
+    GLBE_CUDA(cudaEventRecord(c->ev_stage_free, c->stream), "glbe_set_force_host");
     return GLBE_OK;
 }
 

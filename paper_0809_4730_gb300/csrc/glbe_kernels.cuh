@@ -1152,7 +1152,8 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, 
 // The plain flow step held to MINB resident blocks of 256 threads per SM:
 // with 16-bit storage it fits 48 registers (five blocks, 40 warps, instead of
 // four).  A separate kernel because stating a minimum at all (even one block)
-// changes the register allocation of the forms left free.
+// changes the register allocation of the forms left free.  F32 stays free:
+// held to 64 registers (four blocks) it measured slower than at 80 (three).
 template <int ST, int MINB>
 __global__ void __launch_bounds__(STEP_THREADS, MINB)
     step_kernel_dense(const StepParams p, const StepBuffers b, const FieldOut fo)
@@ -1162,7 +1163,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
 template <int ST>
 constexpr int step_dense_blocks()
 {
-    return (ST == ST_BF16 || ST == ST_F16) ? 5 : ST == ST_F32 ? 4 : 0;   // 0: the free kernel
+    return (ST == ST_BF16 || ST == ST_F16) ? 5 : 0;   // 0: the free kernel
 }
 
 // The update of the fluid node pair (n0, n0 + 1) from its gathered
