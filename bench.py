@@ -47,7 +47,7 @@ DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 # scaled here by the fluid nodes of the timed duct: the traffic of a step is
 # proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
 # part of the written data is still in L2 when the kernel ends.
-STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (170722048 + 113628928) / 4064256, "f16": (170749440 + 114333184) / 4064256,
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (170765568 + 113160192) / 4064256, "f16": (170749440 + 114333184) / 4064256,
                                  "f32": (325167360 + 263479296) / 4064256}
 
 

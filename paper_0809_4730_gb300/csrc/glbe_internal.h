@@ -79,6 +79,14 @@ struct StepBuffers {
     double* partials;     // [8][gridDim.x] per-block residual sums
     int have_snap;        // 1: usnap holds u(t-10)
     const int* stop;      // null, or a device flag: when set the launch does nothing
+    // Per-direction addresses of the population buffers, filled by the
+    // launcher from fsrc, fdst and StepParams::doff (kernels launched
+    // otherwise do not read them): fsrc_dir[a] = fsrc + doff[a] (the
+    // interior source of direction a of node n is fsrc_dir[a] + n) and
+    // fdst_dir[a] = fdst + a N (slot a of node n is fdst_dir[a] + n), in
+    // elements of the storage type (F32C: its high parts).
+    const void* fsrc_dir[19];
+    void* fdst_dir[19];
 };
 
 enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };

@@ -1013,18 +1013,34 @@ __device__ __forceinline__ NodeIn<F2> pair_inputs(const StepParams& p, const Ste
     return in;
 }
 
-template <int ST, bool MHD, int MODE>
+template <int ST, bool MHD, int MODE, bool DIR = false>
 __device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                   uint32_t n, const float (&d)[19], const float (&dl)[19],
                                                   const float (&q)[21], const float (&ql)[21],
                                                   const NodeIn<float>& in, float (&acc)[7]);
+
+// Interior gather of f from the per-direction bases b.fsrc_dir (filled by
+// the launcher): one base per direction, and the node's own offset (x-seam
+// corrected for e_x = +-1) shared by all directions.
+template <int ST>
+__device__ __forceinline__ void load_f_interior_dir(const StepParams& p, const StepBuffers& b, uint32_t n, int wp,
+                                                    int wm, float (&d)[19])
+{
+    using T = typename Store<ST>::T;
+    const size_t n0 = n, np = (size_t)((long long)n + wp), nm = (size_t)((long long)n + wm);
+#pragma unroll
+    for (int a = 0; a < 19; ++a)
+        d[a] = unscale<ST>(p, Store<ST>::ld(static_cast<const T*>(b.fsrc_dir[a]) + seam_src(a, n0, np, nm)));
+}
 
 // ---------------------------------------------------------------------------
 // Scalar kernel: one node per thread, any geometry
 // ---------------------------------------------------------------------------
 // The update of node n (i < N) by one thread; accumulates the residual terms
 // of MODE_STEP_RESID into acc.  Returns without work for solid nodes.
-template <int ST, bool MHD, int MODE, bool CG = false>
+// DIR: the per-direction bases of b are filled (kernels launched by
+// launch_mode); they serve the interior gather and the stores of f.
+template <int ST, bool MHD, int MODE, bool CG = false, bool DIR = false>
 __device__ __forceinline__ void scalar_node_step(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                  uint32_t i, float (&acc)[7])
 {
@@ -1038,7 +1054,8 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
     if (inb && is_interior(p, n, wp, wm)) {
         // no solid node and no y or z wrap around: every source at a fixed
         // offset (x-seam sources corrected by wp, wm)
-        load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
+        if constexpr (DIR && !S::COMP && !CG) load_f_interior_dir<ST>(p, b, n, wp, wm, d);
+        else load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
         if (MHD) load_g_interior<ST, CG>(p, static_cast<const T*>(b.gsrc), n, wp, wm, q, ql);
     } else {
         const Geo g = make_geo(p, n);
@@ -1053,7 +1070,7 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
         load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
         if (MHD) load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
     }
-    node_from_sources<ST, MHD, MODE>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE>(p, b, n), acc);
+    node_from_sources<ST, MHD, MODE, DIR>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE>(p, b, n), acc);
 }
 
 // The update of fluid node n from its gathered pre-collision populations
@@ -1061,7 +1078,7 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
 // force and the force field, collides, writes the node's own slots of the
 // destination buffers (or the fields in MODE_FIELDS) and adds the residual
 // terms of MODE_STEP_RESID to acc.
-template <int ST, bool MHD, int MODE>
+template <int ST, bool MHD, int MODE, bool DIR>
 __device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                   uint32_t n, const float (&d)[19], const float (&dl)[19],
                                                   const float (&q)[21], const float (&ql)[21],
@@ -1092,6 +1109,9 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
             fd[(size_t)a * N + n] = nh;
             fdl[(size_t)a * N + n] = S::cv_lo(nl);
         }
+    } else if constexpr (DIR) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) static_cast<T*>(b.fdst_dir[a])[n] = S::cv(toscale<ST>(p, d[a] + om[a]));
     } else {
 #pragma unroll
         for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, d[a] + om[a]));
@@ -1139,7 +1159,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
-    scalar_node_step<ST, MHD, MODE>(p, b, fo, i, acc);
+    // per-direction bases for the BF16 flow step only: measured on one box
+    // against the plain addressing, BF16 0.598 vs 0.612 ms, but F16 0.679 vs
+    // 0.631 and F32 1.058 vs 0.898 ms; with induction they raise the register
+    // count past a block per SM
+    scalar_node_step<ST, MHD, MODE, false, !MHD && ST == ST_BF16>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 
@@ -1370,10 +1394,27 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
 #include "glbe_tile.cuh"
 namespace glbe {
 
+// b with its per-direction bases filled (addresses formed as integers: a
+// base may lie before the buffer, only base + n is ever read)
+template <int ST>
+StepBuffers with_dir_bases(const StepParams& p, StepBuffers b)
+{
+    const size_t e = sizeof(typename Store<ST>::T);
+    for (int a = 0; a < 19; ++a) {
+        b.fsrc_dir[a] = b.fsrc ? reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(b.fsrc) +
+                                                               (uintptr_t)((long long)e * p.doff[a]))
+                               : nullptr;
+        b.fdst_dir[a] = b.fdst ? reinterpret_cast<void*>(reinterpret_cast<uintptr_t>(b.fdst) + e * (size_t)a * p.N)
+                               : nullptr;
+    }
+    return b;
+}
+
 template <int ST, bool MHD, int MODE>
-cudaError_t launch_mode(const StepParams& p, const StepBuffers& b, const FieldOut& fo, cudaStream_t st,
+cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const FieldOut& fo, cudaStream_t st,
                         unsigned* nblocks)
 {
+    const StepBuffers b = with_dir_bases<ST>(p, b_in);
     if constexpr (ST != ST_F32C && MODE != MODE_FIELDS) {
         if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
         if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);
