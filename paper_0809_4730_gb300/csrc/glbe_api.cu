@@ -575,9 +575,21 @@ glbe_status glbe_set_force_host(glbe_ctx* c, const float* h_F)
     if (!h_F) return fail(GLBE_ERR_ARG, "force field is NULL");
     const size_t bytes = (size_t)c->prm.force_field * c->N * sizeof(float);
     if (!c->copy_stream) {
-        GLBE_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "glbe_set_force_host");
-        GLBE_CUDA(cudaEventCreateWithFlags(&c->ev_staged, cudaEventDisableTiming), "glbe_set_force_host");
-        GLBE_CUDA(cudaEventCreateWithFlags(&c->ev_stage_free, cudaEventDisableTiming), "glbe_set_force_host");
+        // all three or none: a failed creation leaves the context as it was
+        cudaStream_t cs = nullptr;
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&e2, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (e2) cudaEventDestroy(e2);
+            if (e1) cudaEventDestroy(e1);
+            if (cs) cudaStreamDestroy(cs);
+            return cuda_fail(e, "glbe_set_force_host");
+        }
+        c->copy_stream = cs;
+        c->ev_staged = e1;
+        c->ev_stage_free = e2;
     }
     // The host copy runs on the copy stream into the staging buffer, so it
     // overlaps the steps already enqueued on the context's stream (they read
