@@ -41,14 +41,28 @@ W19 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
 
 DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 
-# DRAM bytes (read + write) per fluid node of one plain step of the default
-# (one-node) kernel (step_kernel_dense for 16-bit storage, step_kernel for F32), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# DRAM bytes (read + write) per fluid node of one plain step of the kernel the
+# automatic choice launches (PLAIN_STEP_KERNEL), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # on the 256x128x128 duct (4,064,256 fluid nodes; profiles/step_kernel_bf16_duct.md),
 # scaled here by the fluid nodes of the timed duct: the traffic of a step is
 # proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
 # part of the written data is still in L2 when the kernel ends.
-STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (170765568 + 113160192) / 4064256, "f16": (170749440 + 114333184) / 4064256,
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (174369536 + 110802176) / 4064256, "f16": (174375936 + 110828288) / 4064256,
                                  "f32": (325167360 + 263479296) / 4064256}
+# the kernels the automatic choice launches on the duct (x periodic, even nx, no induction)
+PLAIN_STEP_KERNEL = {"bf16": "step_pair_kernel", "f16": "step_pair_kernel", "f32": "step_kernel"}
+RESID_STEP_KERNEL = {"bf16": "step_pair_kernel", "f16": "step_pair_kernel", "f32": "step_kernel"}
+
+
+def step_kernels(storage: str, variant: int):
+    """(plain, residual) step kernel names for a flow-only duct step."""
+    if variant == 0:
+        return PLAIN_STEP_KERNEL[storage], RESID_STEP_KERNEL[storage]
+    if variant == 1:
+        return ("step_kernel" if storage == "f32" else "step_kernel_dense"), "step_kernel"
+    if variant == 2:
+        return "step_pair_kernel", "step_pair_kernel"
+    return "tile_kernel", "tile_kernel"
 
 
 def parse():
@@ -309,10 +323,10 @@ def run_glbe(args, rank, ws):
             "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4),
             "traffic": (round(STEP_TRAFFIC_B_PER_FLUID_NODE[args.storage] * fluid)
-                        if args.variant in (0, 1) and args.storage in STEP_TRAFFIC_B_PER_FLUID_NODE else None),
+                        if args.variant == 0 and args.storage in STEP_TRAFFIC_B_PER_FLUID_NODE else None),
             "traffic_note": "bytes per launch, ncu capture on the 256x128x128 duct scaled by fluid nodes",
-            "kernel": ("step_kernel_dense" if args.storage != "f32" else "step_kernel")
-                      + " (plain fused collide+stream; step_kernel on residual levels)",
+            "kernel": "%s (plain fused collide+stream; %s on residual levels)" % step_kernels(args.storage,
+                                                                                           args.variant),
             "bytes_per_node": bpn,
             "kernel_ms": round(kern_ms, 5),
             "peak_source": peak_src,

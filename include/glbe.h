@@ -98,7 +98,10 @@ typedef struct {
     double storage_scale;     /* F16 only: multiplier on the stored deviations (0 = default 4096);
                                  ignored for the other storage forms */
     void* stream;             /* cudaStream_t owned by the caller                */
-    int variant;              /* kernel form: 0 = automatic; 1 = one node per thread; 2 = two x-adjacent
+    int variant;              /* kernel form: 0 = automatic (on grids without walls along x and an even
+                                 nx, without induction, with BF16 or F16 storage: the paired form,
+                                 as measured faster; else one node per thread);
+                                 1 = one node per thread; 2 = two x-adjacent
                                  nodes per thread with packed FP32x2 arithmetic (needs an even nx and
                                  no walls along x, else the one-node form is used); 3 = tiles of 128
                                  x-nodes whose gathers are staged in shared memory by tensor-memory

@@ -112,9 +112,13 @@ template <> struct Store<ST_BF16> {
     static constexpr bool COMP = false, SCALED = false;
     static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
+    // a BF16 value is the high half of the FP32 with the same bits: the pair
+    // is widened from one 32-bit load by a shift and a mask (exact; measured
+    // 0.584 against 0.620 ms per paired step with __bfloat1622float2)
     static __device__ __forceinline__ F2 ld2(const T* p)
     {
-        return F2(__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p))));
+        const uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
+        return F2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
     }
     static __device__ __forceinline__ void st2(T* p, F2 v)
     {
@@ -1194,7 +1198,8 @@ constexpr int step_dense_blocks()
 // The update of the fluid node pair (n0, n0 + 1) from its gathered
 // pre-collision populations (packed FP32x2): the counterpart of
 // node_from_sources for two nodes; adds the pair's residual terms to acc.
-template <int ST, bool MHD, int MODE>
+// DIR: the f stores address the per-direction bases b.fdst_dir.
+template <int ST, bool MHD, int MODE, bool DIR = false>
 __device__ __forceinline__ void pair_from_sources(const StepParams& p, const StepBuffers& b, uint32_t n0,
                                                   const F2 (&d)[19], const F2 (&dl)[19], const F2 (&q)[21],
                                                   const F2 (&ql)[21], const NodeIn<F2>& in, float (&acc)[7])
@@ -1216,6 +1221,9 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
             S::st2(fd + (size_t)a * N + n0, nh);
             S::st2_lo(fdl + (size_t)a * N + n0, nl);
         }
+    } else if constexpr (DIR) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) S::st2(static_cast<T*>(b.fdst_dir[a]) + n0, toscale<ST>(p, d[a] + om[a]));
     } else {
 #pragma unroll
         for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, d[a] + om[a]));
@@ -1259,6 +1267,47 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
     }
 }
 
+// Interior gather of f for the pair (x0, x0 + 1), x0 even, on a row whose
+// nodes are all interior (x periodic, no wall among the neighbours, no y or z
+// seam), from the per-direction bases b.fsrc_dir.  Direction a with x-shift
+// e_x reads the aligned pair at fsrc_dir[a] + n0 + e_x, the source row's
+// (x0, x0 + 1).  e_x = 0: the pair's own sources.  e_x = +1: node x0 + 1
+// takes x0, node x0 takes x0 - 1 from the left lane's pair (a load of its own
+// at a warp start, and across the x seam at x0 = 0).  e_x = -1: node x0 takes
+// x0 + 1, node x0 + 1 takes x0 + 2 from the right lane (a load of its own at a
+// warp end, and across the seam at x0 + 2 = nx).  Every lane of the warp
+// takes this path or none (the shuffles), and every load is in bounds: the
+// row's neighbour rows exist and are fluid.
+template <int ST>
+__device__ __forceinline__ void load_f_pair_interior(const StepParams& p, const StepBuffers& b, uint32_t n0, int x0,
+                                                     F2 (&d)[19])
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    const int lane = threadIdx.x & 31;
+    const bool left_own = lane == 0 || x0 == 0;
+    const bool right_own = lane == 31 || x0 + 2 == p.nx;
+    const long long nl = (long long)n0 + (x0 == 0 ? p.nx : 0);             // source x0 - 1 of node x0
+    const long long nr = (long long)n0 + 1 + (x0 + 2 == p.nx ? -p.nx : 0);  // source x0 + 2 of node x0 + 1
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const T* __restrict__ base = static_cast<const T*>(b.fsrc_dir[a]);
+        const int ex = dir_ex(a);
+        const F2 v = unscale<ST>(p, S::ld2(base + ((long long)n0 + ex)));
+        if (ex > 0) {
+            const float t = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+            const float left = left_own ? unscale<ST>(p, S::ld(base + nl)) : t;
+            d[a] = F2(left, v.v.x);
+        } else if (ex < 0) {
+            const float t = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+            const float right = right_own ? unscale<ST>(p, S::ld(base + nr)) : t;
+            d[a] = F2(v.v.y, right);
+        } else {
+            d[a] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Paired kernel: two x-adjacent nodes per thread (x periodic, nx even)
 // ---------------------------------------------------------------------------
@@ -1274,29 +1323,46 @@ __global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParam
     // lanes past the end mirror the last pair so that every lane takes part in
     // the shuffles; they write nothing
     const uint32_t n0 = 2u * (inb ? i : npairs - 1u);
-    const GeoP gp = make_geo_pair(p, n0);
-    const Geo& g = gp.g;
-    const bool fluid = inb && !g.solid;
-    const size_t N = p.N;
-
     F2 d[19], dl[19], q[21], ql[21];
-    load_f_pair<ST>(p, static_cast<const T*>(b.fsrc), gp, d, dl);
-    if (MHD) load_g_pair<ST>(p, static_cast<const T*>(b.gsrc), gp, q, ql);
+    bool fluid = inb;
+    // interior rows (flow, 16-bit or F32 storage): fixed offsets, decided for
+    // the whole warp so that every lane takes part in the shuffles
+    constexpr bool FAST = !MHD && !S::COMP;
+    int wp = 0, wm = 0;
+    const bool interior = FAST && __all_sync(0xffffffffu, is_interior(p, n0, wp, wm));
+    if (FAST && interior) {
+        const int x0 = (int)(n0 - fdiv(n0, p.div_nx) * (uint32_t)p.nx);
+        load_f_pair_interior<ST>(p, b, n0, x0, d);
+    } else {
+        const GeoP gp = make_geo_pair(p, n0);
+        fluid = inb && !gp.g.solid;
+        load_f_pair<ST>(p, static_cast<const T*>(b.fsrc), gp, d, dl);
+        if (MHD) load_g_pair<ST>(p, static_cast<const T*>(b.gsrc), gp, q, ql);
+    }
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (fluid) pair_from_sources<ST, MHD, MODE>(p, b, n0, d, dl, q, ql, pair_inputs<MHD, MODE>(p, b, n0), acc);
+    if (fluid)
+        pair_from_sources<ST, MHD, MODE, FAST>(p, b, n0, d, dl, q, ql, pair_inputs<MHD, MODE>(p, b, n0), acc);
     if (MODE == MODE_STEP_RESID) block_partials<PAIR_THREADS>(acc, b.partials);
 }
 
-// The paired kernel serves x-periodic grids with an even nx when asked for
-// (variant 2).  The automatic choice is one node per thread: measured on
-// GB300 the paired form issues 30 % fewer instructions per node but runs
-// 1.1-1.4x slower -- its register footprint (96-144 registers) leaves too
-// few resident warps to cover the memory latency.
-inline bool pair_eligible(const StepParams& p)
+// The paired kernel serves x-periodic grids with an even nx: when asked for
+// (variant 2), or by the automatic choice (variant 0) where it measured
+// faster on the 512 x 256 x 256 duct.  There its interior rows issue 39 %
+// fewer instructions per node than the one-node kernel, but its 96 registers
+// leave 28 % of the warp slots active, so which form wins depends on the
+// storage: F16 0.563 against 0.631 ms per plain step and 0.780 against
+// 0.848 ms per residual step; BF16 0.620 against 0.599 ms (plain) but 0.769
+// against 0.838 ms (residual), and with the pair widened from one 32-bit
+// load (Store<ST_BF16>::ld2) 0.584 and 0.757 ms; F32 1.172 against 0.898 ms.
+// The coupled forms and F32C have no interior pair path and stay on one node
+// per thread.
+inline bool pair_eligible(const StepParams& p, bool mhd, int mode)
 {
-    if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0]) return false;
-    return p.variant == 2;
+    if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0] || mode == MODE_FIELDS) return false;
+    if (p.variant == 2) return true;
+    if (p.variant != 0 || mhd) return false;
+    return p.storage == ST_F16 || p.storage == ST_BF16;
 }
 
 // ---------------------------------------------------------------------------
@@ -1420,7 +1486,7 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
         if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
         if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);
     }
-    if (MODE != MODE_FIELDS && pair_eligible(p)) {
+    if (pair_eligible(p, MHD, MODE)) {
         const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);
         step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
         if (nblocks) *nblocks = grid;

@@ -138,7 +138,11 @@ def test_nonfinite_state_is_reported_as_divergence(orc):
 # x periodic.  nx = 2 and 6 make rows shorter than a warp, so every
 # row-start, row-end and warp-edge case of its lane shuffles occurs; nx = 38
 # leaves a partial last warp.
-@pytest.mark.parametrize("nx", [2, 6, 38])
+# nx = 38 and 66: warps straddle rows; nx = 64: a warp of 32 pairs covers one
+# row.  The flow forms with 16-bit or F32 storage gather the warps that lie
+# wholly on interior rows at fixed offsets (every nx here but 2 and 6 has such
+# warps), the rest through the row geometry.
+@pytest.mark.parametrize("nx", [2, 6, 38, 64, 66])
 @pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2), ("f32c", 3e-5)])
 @pytest.mark.parametrize("mhd", [False, True])
 def test_step_parity_paired_kernel(orc, nx, storage, tol, mhd):
