@@ -159,6 +159,7 @@ StepParams glbe::make_step_params(const glbe_params* p)
             const double sk = (k == 9 || k == 11 || k == 13 || k == 14 || k == 15) ? snu : p->s[k];
             s.rl_a[k] = (float)(-sk / norm2[k]);
             s.rl_b[k] = (float)((1.0 - 0.5 * sk) * ps[k] * ck[k] / norm2[k]);
+            s.rl_c[k] = (float)((1.0 - sk) / norm2[k]);
         }
         s.rl_cons = (float)(ig / 10.0);
     }

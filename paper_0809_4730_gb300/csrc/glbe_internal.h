@@ -43,6 +43,8 @@ struct StepParams {
     float rl_a[19];       // -s_k / |row_k|^2
     float rl_b[19];       // (1 - s_k/2) P_S,k c_k / |row_k|^2
     float rl_cons;        // 1 / (10 gamma): rows 3, 5, 7
+    float rl_c[19];       // (1 - s_k) / |row_k|^2 = rl_a[k] + 1/|row_k|^2: row k of the
+                          // post-collision moments over |row_k|^2 (16-bit storage forms)
     float F[3];           // uniform force
     int force_ncomp;      // 0, 1 (F_x field), 3
     // D3Q7 vector lattice

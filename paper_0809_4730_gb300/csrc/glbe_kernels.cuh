@@ -795,28 +795,67 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     // Conserved rows: delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
     const V Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
     const V R9 = V(2.f) * Fux - Fuy - Fuz, R11 = Fuy - Fuz;
+    // Precise forms: q_k = delta_k, and om = T^t q is the change added to f.
+    // 16-bit forms (RECON): q_k = (m_k + delta_k)/|row_k|^2, the post-collision
+    // moments, and om = T^t q is f~ itself (T T^t = diag |row_k|^2, so
+    // f = T^t diag(1/|row_k|^2) m); f is then dead once its moments are formed.
+    // Per row p.rl_c[k] = rl_a[k] + 1/|row_k|^2 takes the moment's own share;
+    // rows 1, 2 carry m_1 = E1 - 11 drho and m_2 = E2 + 3 drho, row 0 gives
+    // q_0 = drho / 19.  The extra FP32 rounding (~1e-7 of the moments) is far
+    // below that of the stored 16-bit values.
+    constexpr bool RECON = !PRECISE;
 #define GLBE_DK(k, nk, Rk) vfma(V(p.rl_a[k]), (nk), V(p.rl_b[k]) * (Rk))
-    const V q1 = GLBE_DK(1, n1, Fu);
-    const V q2 = GLBE_DK(2, n2, Fu);
-    const V q3 = Fx * V(p.rl_cons), q5 = Fy * V(p.rl_cons), q7 = Fz * V(p.rl_cons);
-    const V q4 = GLBE_DK(4, n4, Fx);
-    const V q6 = GLBE_DK(6, n6, Fy);
-    const V q8 = GLBE_DK(8, n8, Fz);
-    const V q9 = GLBE_DK(9, n9, R9);
-    const V q10 = GLBE_DK(10, n10, R9);
-    const V q11 = GLBE_DK(11, n11, R11);
-    const V q12 = GLBE_DK(12, n12, R11);
-    const V q13 = GLBE_DK(13, n13, Fx * uy + Fy * ux);
-    const V q14 = GLBE_DK(14, n14, Fy * uz + Fz * uy);
-    const V q15 = GLBE_DK(15, n15, Fx * uz + Fz * ux);
-    const V q16 = V(p.rl_a[16]) * n16;
-    const V q17 = V(p.rl_a[17]) * n17;
-    const V q18 = V(p.rl_a[18]) * n18;
+#define GLBE_RK(k, hk, ek, Rk) vfma(V(p.rl_c[k]), (hk), vfma(V(-p.rl_a[k]), (ek), V(p.rl_b[k]) * (Rk)))
+    V q1, q2, q3, q4, q5, q6, q7, q8, q9, q10, q11, q12, q13, q14, q15, q16, q17, q18, q0;
+    if constexpr (RECON) {
+        const V dr = H.drho;
+        q0 = V(1.f / 19.f) * dr;
+        q1 = vfma(V(p.rl_c[1]), H.E1, vfma(V(-19.f * p.rl_a[1]), jjg, vfma(V(p.rl_b[1]), Fu, V(-11.f / 2394.f) * dr)));
+        q2 = vfma(V(p.rl_c[2]), H.E2, vfma(V(5.5f * p.rl_a[2]), jjg, vfma(V(p.rl_b[2]), Fu, V(3.f / 252.f) * dr)));
+        q3 = vfma(V(0.1f), H.mx, Fx * V(p.rl_cons));
+        q5 = vfma(V(0.1f), H.my, Fy * V(p.rl_cons));
+        q7 = vfma(V(0.1f), H.mz, Fz * V(p.rl_cons));
+        q4 = GLBE_RK(4, H.Qx, V(-2.f / 3.f) * jx, Fx);
+        q6 = GLBE_RK(6, H.Qy, V(-2.f / 3.f) * jy, Fy);
+        q8 = GLBE_RK(8, H.Qz, V(-2.f / 3.f) * jz, Fz);
+        q9 = GLBE_RK(9, H.P9, e9, R9);
+        q10 = GLBE_RK(10, H.P10, V(-0.5f) * e9, R9);
+        q11 = GLBE_RK(11, H.P11, e11, R11);
+        q12 = GLBE_RK(12, H.P12, V(-0.5f) * e11, R11);
+        q13 = GLBE_RK(13, H.P13, jx * gjy, Fx * uy + Fy * ux);
+        q14 = GLBE_RK(14, H.P14, jy * gjz, Fy * uz + Fz * uy);
+        q15 = GLBE_RK(15, H.P15, jx * gjz, Fx * uz + Fz * ux);
+        q16 = V(p.rl_c[16]) * H.P16;
+        q17 = V(p.rl_c[17]) * H.P17;
+        q18 = V(p.rl_c[18]) * H.P18;
+    } else {
+        q0 = V(0.f);
+        q1 = GLBE_DK(1, n1, Fu);
+        q2 = GLBE_DK(2, n2, Fu);
+        q3 = Fx * V(p.rl_cons);
+        q5 = Fy * V(p.rl_cons);
+        q7 = Fz * V(p.rl_cons);
+        q4 = GLBE_DK(4, n4, Fx);
+        q6 = GLBE_DK(6, n6, Fy);
+        q8 = GLBE_DK(8, n8, Fz);
+        q9 = GLBE_DK(9, n9, R9);
+        q10 = GLBE_DK(10, n10, R9);
+        q11 = GLBE_DK(11, n11, R11);
+        q12 = GLBE_DK(12, n12, R11);
+        q13 = GLBE_DK(13, n13, Fx * uy + Fy * ux);
+        q14 = GLBE_DK(14, n14, Fy * uz + Fz * uy);
+        q15 = GLBE_DK(15, n15, Fx * uz + Fz * ux);
+        q16 = V(p.rl_a[16]) * n16;
+        q17 = V(p.rl_a[17]) * n17;
+        q18 = V(p.rl_a[18]) * n18;
+    }
 #undef GLBE_DK
+#undef GLBE_RK
 
-    // om = T^t delta  (columns of T read from the basis polynomials); f~ = f + om
-    om[0] = V(-30.f) * q1 + V(12.f) * q2;
-    const V A = V(-11.f) * q1 - V(4.f) * q2;          // axis directions, c^2 = 1
+    // om = T^t q  (columns of T read from the basis polynomials); row 0 adds
+    // q_0 to every direction (RECON only)
+    om[0] = RECON ? vfma(V(-30.f), q1, vfma(V(12.f), q2, q0)) : V(-30.f) * q1 + V(12.f) * q2;
+    const V A = RECON ? vfma(V(-11.f), q1, vfma(V(-4.f), q2, q0)) : V(-11.f) * q1 - V(4.f) * q2;   // axis, c^2 = 1
     const V X9 = V(2.f) * q9 - V(4.f) * q10;           // 3c_x^2 - c^2 = 2 on +-x
     const V Y9 = V(2.f) * q10 - q9;                    // ... = -1 on +-y, +-z
     const V W11 = q11 - V(2.f) * q12;
@@ -829,7 +868,7 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     t = q7 - V(4.f) * q8;
     om[5] = A + Y9 - W11 + t;
     om[6] = A + Y9 - W11 - t;
-    const V Dg = V(8.f) * q1 + q2;                  // diagonal directions, c^2 = 2
+    const V Dg = RECON ? vfma(V(8.f), q1, q2 + q0) : V(8.f) * q1 + q2;   // diagonal directions, c^2 = 2
     const V P = q9 + q10, Q = q11 + q12;
     {   // (+-1, +-1, 0)
         const V b = Dg + P + Q, ax = q3 + q4 + q16, by = q5 + q6 - q17;
@@ -852,6 +891,16 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
         om[17] = b + ay - bz - q14;
         om[18] = b - ay - bz + q14;
     }
+}
+
+// Post-collision deviation of one population from the gathered one (f) and
+// the collision output om of flow_collide: the precise forms add the change,
+// the 16-bit forms get f~ itself (the moment-space reconstruction).
+template <int ST, class V>
+__device__ __forceinline__ V post_collision(V f, V om)
+{
+    if constexpr (ST == ST_F32 || ST == ST_F32C) return f + om;
+    else return om;
 }
 
 // Result of one node's (or pair's) update besides the new populations.
@@ -1115,10 +1164,10 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
         }
     } else if constexpr (DIR) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) static_cast<T*>(b.fdst_dir[a])[n] = S::cv(toscale<ST>(p, d[a] + om[a]));
+        for (int a = 0; a < 19; ++a) static_cast<T*>(b.fdst_dir[a])[n] = S::cv(toscale<ST>(p, post_collision<ST>(d[a], om[a])));
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, d[a] + om[a]));
+        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, post_collision<ST>(d[a], om[a])));
     }
     if (MHD) {
         T* __restrict__ gd = static_cast<T*>(b.gdst);
@@ -1223,10 +1272,10 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
         }
     } else if constexpr (DIR) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) S::st2(static_cast<T*>(b.fdst_dir[a]) + n0, toscale<ST>(p, d[a] + om[a]));
+        for (int a = 0; a < 19; ++a) S::st2(static_cast<T*>(b.fdst_dir[a]) + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])));
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, d[a] + om[a]));
+        for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])));
     }
     if (MHD) {
         T* __restrict__ gd = static_cast<T*>(b.gdst);
