@@ -795,9 +795,9 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     // Conserved rows: delta_3,5,7 = (F/gamma)/10 whatever the rate; delta_0 = 0.
     const V Fux = Fx * ux, Fuy = Fy * uy, Fuz = Fz * uz, Fu = Fux + Fuy + Fuz;
     const V R9 = V(2.f) * Fux - Fuy - Fuz, R11 = Fuy - Fuz;
-    // Precise forms: q_k = delta_k, and om = T^t q is the change added to f.
-    // 16-bit forms (RECON): q_k = (m_k + delta_k)/|row_k|^2, the post-collision
-    // moments, and om = T^t q is f~ itself (T T^t = diag |row_k|^2, so
+    // Precise forms: q_k = delta_k/|row_k|^2, and om = T^t q is the change
+    // added to f.  16-bit forms (RECON): q_k = (m_k + delta_k)/|row_k|^2, the
+    // post-collision moments, and om = T^t q is f~ itself (T T^t = diag |row_k|^2, so
     // f = T^t diag(1/|row_k|^2) m); f is then dead once its moments are formed.
     // Per row p.rl_c[k] = rl_a[k] + 1/|row_k|^2 takes the moment's own share;
     // rows 1, 2 carry m_1 = E1 - 11 drho and m_2 = E2 + 3 drho, row 0 gives
