@@ -47,11 +47,11 @@ DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 # scaled here by the fluid nodes of the timed duct: the traffic of a step is
 # proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
 # part of the written data is still in L2 when the kernel ends.
-STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (174367488 + 110480896) / 4064256, "f16": (174370816 + 110041344) / 4064256,
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (174384896 + 112900608) / 4064256, "f16": (174380288 + 111759360) / 4064256,
                                  "f32": (325167360 + 263479296) / 4064256}
 # the kernels the automatic choice launches on the duct (x periodic, even nx, no induction)
-PLAIN_STEP_KERNEL = {"bf16": "step_pair_kernel", "f16": "step_pair_kernel", "f32": "step_kernel"}
-RESID_STEP_KERNEL = {"bf16": "step_pair_kernel", "f16": "step_pair_kernel", "f32": "step_kernel"}
+PLAIN_STEP_KERNEL = {"bf16": "step_pair_kernel_dense", "f16": "step_pair_kernel_dense", "f32": "step_kernel"}
+RESID_STEP_KERNEL = {"bf16": "step_pair_kernel_dense", "f16": "step_pair_kernel_dense", "f32": "step_kernel"}
 
 
 def step_kernels(storage: str, variant: int):
@@ -61,7 +61,8 @@ def step_kernels(storage: str, variant: int):
     if variant == 1:
         return ("step_kernel" if storage == "f32" else "step_kernel_dense"), "step_kernel"
     if variant == 2:
-        return "step_pair_kernel", "step_pair_kernel"
+        k = "step_pair_kernel" if storage == "f32" else "step_pair_kernel_dense"
+        return k, k
     return "tile_kernel", "tile_kernel"
 
 

@@ -114,10 +114,14 @@ template <> struct Store<ST_BF16> {
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
     // a BF16 value is the high half of the FP32 with the same bits: the pair
     // is widened from one 32-bit load by a shift and a mask (exact; measured
-    // 0.584 against 0.620 ms per paired step with __bfloat1622float2)
+    // 0.584 against 0.620 ms per paired step with __bfloat1622float2).  The
+    // load asks L2 for the whole 256-byte block: a warp reads 128 bytes of a
+    // direction row and the next warp the following 128 (0.4847 against
+    // 0.4893 ms per paired step)
     static __device__ __forceinline__ F2 ld2(const T* p)
     {
-        const uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
+        uint32_t u;
+        asm("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(u) : "l"(p));
         return F2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
     }
     static __device__ __forceinline__ void st2(T* p, F2 v)
@@ -1361,7 +1365,7 @@ __device__ __forceinline__ void load_f_pair_interior(const StepParams& p, const 
 // Paired kernel: two x-adjacent nodes per thread (x periodic, nx even)
 // ---------------------------------------------------------------------------
 template <int ST, bool MHD, int MODE>
-__global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParams p, const StepBuffers b)
+__device__ __forceinline__ void pair_step_body(const StepParams& p, const StepBuffers& b)
 {
     using S = Store<ST>;
     using T = typename S::T;
@@ -1393,6 +1397,30 @@ __global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParam
     if (fluid)
         pair_from_sources<ST, MHD, MODE, FAST>(p, b, n0, d, dl, q, ql, pair_inputs<MHD, MODE>(p, b, n0), acc);
     if (MODE == MODE_STEP_RESID) block_partials<PAIR_THREADS>(acc, b.partials);
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(PAIR_THREADS) step_pair_kernel(const StepParams p, const StepBuffers b)
+{
+    pair_step_body<ST, MHD, MODE>(p, b);
+}
+
+// The 16-bit flow forms held to MINB resident blocks of 128 threads per SM.
+// The paired kernel is latency-bound: at its free 80 registers 24 warps per
+// SM; held to 72 (7 blocks, 28 warps, a few spilled bytes) the BF16 plain
+// step took 0.488 instead of 0.527 ms and the residual step 0.656 instead of
+// 0.741 ms, measured alternately on one box (F16: 0.517 against 0.519 ms).
+// Held to 6 blocks it was slower than free: stating a minimum changes the
+// register allocation, hence a kernel of its own.
+template <int ST, int MODE, int MINB>
+__global__ void __launch_bounds__(PAIR_THREADS, MINB) step_pair_kernel_dense(const StepParams p, const StepBuffers b)
+{
+    pair_step_body<ST, false, MODE>(p, b);
+}
+template <int ST>
+constexpr int pair_dense_blocks()
+{
+    return (ST == ST_BF16 || ST == ST_F16) ? 7 : 0;   // 0: the free kernel
 }
 
 // The paired kernel serves x-periodic grids with an even nx: when asked for
@@ -1537,7 +1565,11 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
     }
     if (pair_eligible(p, MHD, MODE)) {
         const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);
-        step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
+        constexpr int PMINB = pair_dense_blocks<ST>();
+        if constexpr (!MHD && MODE != MODE_FIELDS && PMINB > 0)
+            step_pair_kernel_dense<ST, MODE, PMINB><<<grid, PAIR_THREADS, 0, st>>>(p, b);
+        else
+            step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
         if (nblocks) *nblocks = grid;
     } else {
         const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
