@@ -1441,16 +1441,13 @@ constexpr int pair_dense_blocks()
 }
 
 // The paired kernel serves x-periodic grids with an even nx: when asked for
-// (variant 2), or by the automatic choice (variant 0) where it measured
-// faster on the 512 x 256 x 256 duct.  There its interior rows issue 39 %
-// fewer instructions per node than the one-node kernel, but its 96 registers
-// leave 28 % of the warp slots active, so which form wins depends on the
-// storage: F16 0.563 against 0.631 ms per plain step and 0.780 against
-// 0.848 ms per residual step; BF16 0.620 against 0.599 ms (plain) but 0.769
-// against 0.838 ms (residual), and with the pair widened from one 32-bit
-// load (Store<ST_BF16>::ld2) 0.584 and 0.757 ms; F32 1.172 against 0.898 ms.
-// The coupled forms and F32C have no interior pair path and stay on one node
-// per thread.
+// (variant 2), or by the automatic choice (variant 0) for the 16-bit flow
+// steps, where it measured faster on the 512 x 256 x 256 duct: its interior
+// rows issue about 310 instructions per node against 538 for the one-node
+// kernel.  Plain step, BF16 0.485 against 0.598 ms, F16 0.509 against 0.631
+// ms; residual step, BF16 0.655 against 0.838 ms.  F32 stays on one node per
+// thread: paired, its 142 registers leave 8 warps per SM (1.17 against 0.89
+// ms).  The coupled forms and F32C have no interior pair path.
 inline bool pair_eligible(const StepParams& p, bool mhd, int mode)
 {
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0] || mode == MODE_FIELDS) return false;
