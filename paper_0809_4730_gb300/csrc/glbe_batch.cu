@@ -413,7 +413,7 @@ glbe_status glbe_batch_workspace_bytes(const glbe_params* doms, int n, size_t* b
 {
     if (!bytes) return fail(GLBE_ERR_ARG, "bytes is NULL");
     std::vector<DomLayout> lay;
-    size_t misc, total, pd;
+    size_t misc = 0, total = 0, pd = 0;
     glbe_status s = batch_layout(doms, n, &lay, &misc, &total, &pd);
     if (s != GLBE_OK) return s;
     *bytes = total;
@@ -426,7 +426,7 @@ glbe_status glbe_batch_init(const glbe_params* doms, int n, void* d_workspace, s
     if (!out) return fail(GLBE_ERR_ARG, "out is NULL");
     *out = nullptr;
     std::vector<DomLayout> lay;
-    size_t misc, total, pd;
+    size_t misc = 0, total = 0, pd = 0;
     glbe_status s = batch_layout(doms, n, &lay, &misc, &total, &pd);
     if (s != GLBE_OK) return s;
     if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))

@@ -362,7 +362,6 @@ __global__ void __launch_bounds__(tile_threads<PAIR>(), tile_min_blocks<PAIR, MH
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = threadIdx.x;
     const int ny = p.ny, nz = p.nz;
-    const size_t N = p.N;
     const T* __restrict__ fs = static_cast<const T*>(b.fsrc);
     const T* __restrict__ gs = static_cast<const T*>(b.gsrc);
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
