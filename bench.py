@@ -599,6 +599,13 @@ def adjoint_duct(n: int, storage: str = "f32c"):
     return G, F, fluid
 
 
+# DRAM bytes (read + write) per fluid node of one adjoint launch, from `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum -k regex:adjoint_kernel -s 40 -c 1` on the 96^3 coupled
+# duct (848,256 fluid nodes; profiles/adjoint_kernel_hartmann_duct.md).  The captured launch was a
+# convergence-check iteration, which also reads and writes the 12 B gradient snapshot per node.
+ADJ_TRAFFIC_B_PER_FLUID_NODE = (381026304 + 147569408) / 848256
+
+
 def adjoint_bytes_per_node(mhd: bool, storage: str = "f32c") -> int:
     """Algorithmic bytes of one adjoint step per fluid node: forward gather
     (19 f + 21 g) x 4 B (F32) or 6 B (F32C), lagged Lorentz force and force
@@ -688,9 +695,10 @@ def run_adjoint(args, rank, ws):
         "unrolled_adjoint": {"steps": args.adjoint_unrolled_steps, "K": args.adjoint_K, "seconds": round(unr_s, 3),
                              "max_abs_dQdF": float(dQu.abs().max())},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 3), "traffic": None,
+                     "frac": round(achieved / hbm, 3), "traffic": round(ADJ_TRAFFIC_B_PER_FLUID_NODE * fluid),
                      "note": "per iteration of glbe_adjoint_steady (adjoint kernel + finalize every 10 + host "
-                             f"polling), {bpn} B per fluid node, peak of measured"},
+                             f"polling), {bpn} B per fluid node, peak of measured; traffic: bytes per launch, ncu "
+                             "capture of a convergence-check launch on the 96^3 duct scaled by fluid nodes"},
         "full_size_check": fd, "clocks": clk.summary(),
     }
 
