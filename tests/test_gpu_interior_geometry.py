@@ -86,3 +86,36 @@ def test_unrolled_adjoint_on_narrow_periodic_ducts(orc, nx):
     mask = ~orc.solid_mask(cfg)
     g, r = dQ[:, mask], ref.T[:, mask]
     assert np.abs(g - r).max() / np.abs(r).max() <= 5e-5
+
+
+# The paired kernel's interior path needs a whole warp (32 pairs) on interior
+# rows; with nx = 2 or 4 a warp spans 32 or 16 rows.  Each grid here has at
+# least two such warps (counted from the warp-to-row map), and with nx = 2
+# both seam corrections apply to the same pair.
+PAIR_GEOMETRIES = [
+    (2, 57, 6, (0, 1, 1), (0, 1, 1)),
+    (2, 45, 6, (0, 0, 0), (0, 0, 0)),
+    (4, 30, 5, (0, 1, 0), (0, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("geom", PAIR_GEOMETRIES, ids=[f"{g[0]}x{g[1]}x{g[2]}" for g in PAIR_GEOMETRIES])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_paired_step_parity_on_narrow_x(orc, geom, storage):
+    from paper_0809_4730_gb300.inputs import random_force
+    nx, ny, nz, lo, hi = geom
+    cfg = orc.Config(nx, ny, nz, wall_lo=lo, wall_hi=hi, gamma=0.3, nu=0.02, F=(2e-5, -1e-5, 5e-6))
+    S, G = make_pair(orc, cfg, Fext=random_force(nx, ny, nz, 3e-5, seed=9), storage=storage, variant=2)
+    _perturb(S, 23)
+    push_oracle_state(S, G)
+    fluid = ~S.solid_mask()
+    if storage != "f32":
+        df0, _, _ = gpu_state(G)
+        S.f[fluid] = df0[:, fluid].T + W19[None, :] * cfg.rho0
+    n = 13
+    S.run(n)
+    G.step(n)
+    df, _, _ = gpu_state(G)
+    odf, _, _ = oracle_state_dev(S)
+    tol = {"f32": 3e-5, "bf16": 3e-2, "f16": 4e-3}[storage]
+    assert rel_linf(df, odf, fluid) < tol
