@@ -89,6 +89,11 @@ struct StepBuffers {
     // elements of the storage type (F32C: its high parts).
     const void* fsrc_dir[19];
     void* fdst_dir[19];
+    // L2 prefetch distance in blocks, filled by the launcher (0: none): a
+    // flow-step block prefetches the f rows and the force row that the block
+    // pf_ahead positions later will gather -- one resident wave of the
+    // launched kernel ahead
+    long long pf_ahead;
 };
 
 enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };

@@ -1226,10 +1226,48 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     }
 }
 
+// L2 prefetch for a flow step: the block b.pf_ahead positions later (one
+// resident wave of the kernel, so it starts about when this one ends) will
+// gather NODES consecutive nodes; threads 0..18 each ask L2 for the source
+// segment of one direction, [first node - 1, last node + 1] shifted by the
+// direction's offset, thread 19 for the force row (bulk prefetch, no data
+// enters the SM).  Ranges are clamped to their buffers and trimmed to 16-byte
+// boundaries.  Measured on the 512 x 256 x 256 duct: BF16 paired step 0.4535
+// against 0.4835 ms, F16 paired step 0.4835 against 0.4975 ms.
+template <int ST, int NODES>
+__device__ __forceinline__ void prefetch_ahead(const StepParams& p, const StepBuffers& b)
+{
+    using T = typename Store<ST>::T;
+    const int t = threadIdx.x;
+    if (b.pf_ahead <= 0 || t > 19) return;
+    const long long N = p.N;
+    const long long nb = ((long long)blockIdx.x + b.pf_ahead) * NODES;
+    if (nb >= N) return;
+    uintptr_t lo, hi, blo;
+    if (t < 19) {
+        blo = reinterpret_cast<uintptr_t>(b.fsrc) + (uintptr_t)t * (uintptr_t)N * sizeof(T);
+        const long long shift = p.doff[t] - (long long)t * N;           // -(e_x + e_y nx + e_z nx ny)
+        const long long s0 = nb + shift - 1, s1 = nb + NODES + shift + 1;
+        lo = blo + (uintptr_t)(s0 < 0 ? 0 : s0) * sizeof(T);
+        hi = blo + (uintptr_t)(s1 > N ? N : s1) * sizeof(T);
+    } else {
+        if (p.force_ncomp < 1 || b.Ffield == nullptr) return;
+        blo = reinterpret_cast<uintptr_t>(b.Ffield);
+        const long long s1 = nb + NODES;
+        lo = blo + (uintptr_t)nb * sizeof(float);
+        hi = blo + (uintptr_t)(s1 > N ? N : s1) * sizeof(float);
+    }
+    lo = (lo + 15) & ~(uintptr_t)15;
+    hi &= ~(uintptr_t)15;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
 template <int ST, bool MHD, int MODE>
 __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers& b, const FieldOut& fo)
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
+    if constexpr (!MHD && MODE != MODE_FIELDS && !Store<ST>::COMP) prefetch_ahead<ST, STEP_THREADS>(p, b);
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
@@ -1387,6 +1425,7 @@ __device__ __forceinline__ void pair_step_body(const StepParams& p, const StepBu
     using S = Store<ST>;
     using T = typename S::T;
     if (b.stop != nullptr && *b.stop) return;
+    if constexpr (!MHD && !S::COMP) prefetch_ahead<ST, 2 * PAIR_THREADS>(p, b);
     const uint32_t npairs = p.N >> 1;
     const uint32_t i = blockIdx.x * PAIR_THREADS + threadIdx.x;
     const bool inb = i < npairs;
@@ -1571,11 +1610,25 @@ StepBuffers with_dir_bases(const StepParams& p, StepBuffers b)
     return b;
 }
 
+// Blocks of `kernel` resident on the whole device at once (one wave): the
+// distance of the L2 prefetch.  Computed once per kernel (the first device
+// that launches it); 0, and so no prefetch, if the runtime cannot tell.
+template <class K>
+long long resident_wave(K kernel, int threads)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return 0;
+    return (long long)sms * per_sm;
+}
+
 template <int ST, bool MHD, int MODE>
 cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const FieldOut& fo, cudaStream_t st,
                         unsigned* nblocks)
 {
-    const StepBuffers b = with_dir_bases<ST>(p, b_in);
+    StepBuffers b = with_dir_bases<ST>(p, b_in);
+    b.pf_ahead = 0;
     if constexpr (ST != ST_F32C && MODE != MODE_FIELDS) {
         if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
         if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);
@@ -1583,18 +1636,28 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
     if (pair_eligible(p, MHD, MODE)) {
         const unsigned grid = (unsigned)(((size_t)(p.N / 2) + PAIR_THREADS - 1) / PAIR_THREADS);
         constexpr int PMINB = pair_dense_blocks<ST, MODE>();
-        if constexpr (!MHD && MODE != MODE_FIELDS && PMINB > 0)
+        if constexpr (!MHD && MODE != MODE_FIELDS && PMINB > 0) {
+            static const long long wave = resident_wave(step_pair_kernel_dense<ST, MODE, PMINB>, PAIR_THREADS);
+            b.pf_ahead = wave;
             step_pair_kernel_dense<ST, MODE, PMINB><<<grid, PAIR_THREADS, 0, st>>>(p, b);
-        else
+        } else {
+            static const long long wave = resident_wave(step_pair_kernel<ST, MHD, MODE>, PAIR_THREADS);
+            b.pf_ahead = wave;
             step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
+        }
         if (nblocks) *nblocks = grid;
     } else {
         const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
         constexpr int MINB = step_dense_blocks<ST>();
-        if constexpr (!MHD && MODE == MODE_STEP && MINB > 0)
+        if constexpr (!MHD && MODE == MODE_STEP && MINB > 0) {
+            static const long long wave = resident_wave(step_kernel_dense<ST, MINB>, STEP_THREADS);
+            b.pf_ahead = wave;
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
-        else
+        } else {
+            static const long long wave = resident_wave(step_kernel<ST, MHD, MODE>, STEP_THREADS);
+            b.pf_ahead = wave;
             step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+        }
         if (nblocks) *nblocks = grid;
     }
     return cudaGetLastError();
