@@ -1226,37 +1226,57 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     }
 }
 
-// L2 prefetch for a flow step: the block b.pf_ahead positions later (one
-// resident wave of the kernel, so it starts about when this one ends) will
-// gather NODES consecutive nodes; threads 0..18 each ask L2 for the source
-// segment of one direction, [first node - 1, last node + 1] shifted by the
-// direction's offset, thread 19 for the force row (bulk prefetch, no data
-// enters the SM).  Ranges are clamped to their buffers and trimmed to 16-byte
-// boundaries.  Measured on the 512 x 256 x 256 duct: BF16 paired step 0.4535
-// against 0.4835 ms, F16 paired step 0.4835 against 0.4975 ms.
-template <int ST, int NODES>
+// L2 prefetch for a step: the block b.pf_ahead positions later (one resident
+// wave of the kernel, so it starts about when this one ends) will gather
+// NODES consecutive nodes.  One thread per row asks L2 for that block's
+// segment of the row (bulk prefetch, no data enters the SM): threads 0..18
+// the f rows, with the direction's source shift and one node of halo on
+// each side; with induction the 21 g rows (shifted like their D3Q7
+// direction) and the 3 rows of the lagged Lorentz force; the force rows; on
+// residual steps the 3 rows of the velocity snapshot.  Ranges are clamped to
+// their rows and trimmed to 16-byte boundaries.  Measured on the
+// 512 x 256 x 256 duct: BF16 paired step 0.4516 against 0.4829 ms, F32
+// one-node step 0.869 against 0.888 ms.
+template <int ST, int NODES, bool MHD, bool RESID>
 __device__ __forceinline__ void prefetch_ahead(const StepParams& p, const StepBuffers& b)
 {
     using T = typename Store<ST>::T;
+    constexpr int NG = MHD ? 21 : 0, NL = MHD ? 3 : 0, NS = RESID ? 3 : 0;
     const int t = threadIdx.x;
-    if (b.pf_ahead <= 0 || t > 19) return;
+    if (b.pf_ahead <= 0 || t >= 19 + NG + NL + 3 + NS) return;
     const long long N = p.N;
     const long long nb = ((long long)blockIdx.x + b.pf_ahead) * NODES;
     if (nb >= N) return;
-    uintptr_t lo, hi, blo;
-    if (t < 19) {
-        blo = reinterpret_cast<uintptr_t>(b.fsrc) + (uintptr_t)t * (uintptr_t)N * sizeof(T);
-        const long long shift = p.doff[t] - (long long)t * N;           // -(e_x + e_y nx + e_z nx ny)
-        const long long s0 = nb + shift - 1, s1 = nb + NODES + shift + 1;
-        lo = blo + (uintptr_t)(s0 < 0 ? 0 : s0) * sizeof(T);
-        hi = blo + (uintptr_t)(s1 > N ? N : s1) * sizeof(T);
+    uintptr_t row;               // start of the row
+    size_t esz;                  // bytes per element
+    long long shift = 0, halo = 0;
+    int r = t;
+    if (r < 19) {
+        row = reinterpret_cast<uintptr_t>(b.fsrc) + (uintptr_t)r * (uintptr_t)N * sizeof(T);
+        esz = sizeof(T);
+        shift = p.doff[r] - (long long)r * N;            // -(e_x + e_y nx + e_z nx ny)
+        halo = 1;
+    } else if ((r -= 19) < NG) {
+        const int a = r % 7;
+        row = reinterpret_cast<uintptr_t>(b.gsrc) + (uintptr_t)r * (uintptr_t)N * sizeof(T);
+        esz = sizeof(T);
+        shift = p.doff[a] - (long long)a * N;
+        halo = 1;
+    } else if ((r -= NG) < NL) {
+        row = reinterpret_cast<uintptr_t>(b.FL) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
+    } else if ((r -= NL) < 3) {
+        if (r >= p.force_ncomp || b.Ffield == nullptr) return;
+        row = reinterpret_cast<uintptr_t>(b.Ffield) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
     } else {
-        if (p.force_ncomp < 1 || b.Ffield == nullptr) return;
-        blo = reinterpret_cast<uintptr_t>(b.Ffield);
-        const long long s1 = nb + NODES;
-        lo = blo + (uintptr_t)nb * sizeof(float);
-        hi = blo + (uintptr_t)(s1 > N ? N : s1) * sizeof(float);
+        r -= 3;
+        row = reinterpret_cast<uintptr_t>(b.usnap) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
     }
+    const long long s0 = nb + shift - halo, s1 = nb + NODES + shift + halo;
+    uintptr_t lo = row + (uintptr_t)(s0 < 0 ? 0 : s0) * esz;
+    uintptr_t hi = row + (uintptr_t)(s1 > N ? N : s1) * esz;
     lo = (lo + 15) & ~(uintptr_t)15;
     hi &= ~(uintptr_t)15;
     if (hi > lo)
@@ -1267,7 +1287,10 @@ template <int ST, bool MHD, int MODE>
 __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers& b, const FieldOut& fo)
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
-    if constexpr (!MHD && MODE != MODE_FIELDS && !Store<ST>::COMP) prefetch_ahead<ST, STEP_THREADS>(p, b);
+    // with induction only for F32 storage: coupled F32 step 0.1241 against
+    // 0.1382 ms, coupled BF16 step 0.0845 against 0.0829 ms
+    if constexpr (MODE != MODE_FIELDS && !Store<ST>::COMP && (!MHD || ST == ST_F32))
+        prefetch_ahead<ST, STEP_THREADS, MHD, MODE == MODE_STEP_RESID>(p, b);
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
@@ -1425,7 +1448,7 @@ __device__ __forceinline__ void pair_step_body(const StepParams& p, const StepBu
     using S = Store<ST>;
     using T = typename S::T;
     if (b.stop != nullptr && *b.stop) return;
-    if constexpr (!MHD && !S::COMP) prefetch_ahead<ST, 2 * PAIR_THREADS>(p, b);
+    if constexpr (!MHD && !S::COMP) prefetch_ahead<ST, 2 * PAIR_THREADS, false, MODE == MODE_STEP_RESID>(p, b);
     const uint32_t npairs = p.N >> 1;
     const uint32_t i = blockIdx.x * PAIR_THREADS + threadIdx.x;
     const bool inb = i < npairs;
