@@ -1633,9 +1633,14 @@ StepBuffers with_dir_bases(const StepParams& p, StepBuffers b)
     return b;
 }
 
-// Blocks of `kernel` resident on the whole device at once (one wave): the
-// distance of the L2 prefetch.  Computed once per kernel (the first device
-// that launches it); 0, and so no prefetch, if the runtime cannot tell.
+// Blocks of `kernel` resident on the whole device at once (one wave), from
+// which the L2 prefetch distance is set.  Computed once per kernel (the first
+// device that launches it); 0, and so no prefetch, if the runtime cannot tell.
+// Measured on the 512 x 256 x 256 duct: the one-node plain steps prefetch one
+// wave ahead (F32 0.875 ms; half a wave 0.886, two waves 0.957); the paired
+// steps and the residual steps half a wave ahead (BF16 plain 0.4528 against
+// 0.4555 ms at one wave, BF16 residual 0.613 against 0.643 ms; two waves
+// 0.505 ms, the prefetched rows then leave L2 before they are read).
 template <class K>
 long long resident_wave(K kernel, int threads)
 {
@@ -1661,11 +1666,11 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
         constexpr int PMINB = pair_dense_blocks<ST, MODE>();
         if constexpr (!MHD && MODE != MODE_FIELDS && PMINB > 0) {
             static const long long wave = resident_wave(step_pair_kernel_dense<ST, MODE, PMINB>, PAIR_THREADS);
-            b.pf_ahead = wave;
+            b.pf_ahead = wave / 2;
             step_pair_kernel_dense<ST, MODE, PMINB><<<grid, PAIR_THREADS, 0, st>>>(p, b);
         } else {
             static const long long wave = resident_wave(step_pair_kernel<ST, MHD, MODE>, PAIR_THREADS);
-            b.pf_ahead = wave;
+            b.pf_ahead = wave / 2;
             step_pair_kernel<ST, MHD, MODE><<<grid, PAIR_THREADS, 0, st>>>(p, b);
         }
         if (nblocks) *nblocks = grid;
@@ -1678,7 +1683,7 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         } else {
             static const long long wave = resident_wave(step_kernel<ST, MHD, MODE>, STEP_THREADS);
-            b.pf_ahead = wave;
+            b.pf_ahead = MODE == MODE_STEP_RESID ? wave / 2 : wave;
             step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         }
         if (nblocks) *nblocks = grid;
