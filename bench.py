@@ -47,8 +47,8 @@ DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 # scaled here by the fluid nodes of the timed duct: the traffic of a step is
 # proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
 # part of the written data is still in L2 when the kernel ends.
-STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (176621568 + 114953728) / 4064256, "f16": (179339776 + 119544832) / 4064256,
-                                 "f32": (332323328 + 267836672) / 4064256}
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (175747584 + 114489600) / 4064256, "f16": (175882752 + 119174144) / 4064256,
+                                 "f32": (332382976 + 267721472) / 4064256}
 # the kernels the automatic choice launches on the duct (x periodic, even nx, no induction)
 PLAIN_STEP_KERNEL = {"bf16": "step_pair_kernel_dense", "f16": "step_pair_kernel_dense", "f32": "step_kernel"}
 RESID_STEP_KERNEL = {"bf16": "step_pair_kernel_dense", "f16": "step_pair_kernel_dense", "f32": "step_kernel"}
