@@ -1288,7 +1288,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
     // with induction only for F32 storage: coupled F32 step 0.1241 against
-    // 0.1382 ms, coupled BF16 step 0.0845 against 0.0829 ms
+    // 0.1382 ms (half a wave ahead: 0.1200 ms), coupled BF16 step 0.0845
+    // against 0.0829 ms (half a wave ahead: 0.0841 ms)
     if constexpr (MODE != MODE_FIELDS && !Store<ST>::COMP && (!MHD || ST == ST_F32))
         prefetch_ahead<ST, STEP_THREADS, MHD, MODE == MODE_STEP_RESID>(p, b);
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
@@ -1638,7 +1639,7 @@ StepBuffers with_dir_bases(const StepParams& p, StepBuffers b)
 // device that launches it); 0, and so no prefetch, if the runtime cannot tell.
 // Measured on the 512 x 256 x 256 duct: the one-node plain steps prefetch one
 // wave ahead (F32 0.875 ms; half a wave 0.886, two waves 0.957); the paired
-// steps and the residual steps half a wave ahead (BF16 plain 0.4528 against
+// steps, the coupled steps and the residual steps half a wave ahead (BF16 plain 0.4528 against
 // 0.4555 ms at one wave, BF16 residual 0.613 against 0.643 ms; two waves
 // 0.505 ms, the prefetched rows then leave L2 before they are read).
 template <class K>
@@ -1683,7 +1684,7 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         } else {
             static const long long wave = resident_wave(step_kernel<ST, MHD, MODE>, STEP_THREADS);
-            b.pf_ahead = MODE == MODE_STEP_RESID ? wave / 2 : wave;
+            b.pf_ahead = (MHD || MODE == MODE_STEP_RESID) ? wave / 2 : wave;
             step_kernel<ST, MHD, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         }
         if (nblocks) *nblocks = grid;
