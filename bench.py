@@ -220,19 +220,21 @@ def duct_solver(storage: str, device="cuda", variant: int = 0):
 
 
 def hartmann_duct_solver(n=128, Ha=10.0, gamma=0.1, device="cuda", storage="f32", variant=0, force_field=0,
-                         nu=0.01):
-    """Hartmann duct of n^3 nodes: x periodic, walls on y and z, B0 along y,
-    nu = eta (0.01 by default), chi = 0.01 (Pr_m = 0.01), F_x = 1e-6 uniform
-    (or, with force_field = 3, a per-node field set by the caller), FP32."""
+                         nu=0.01, shape=None):
+    """Hartmann duct of n^3 nodes (or shape = (nx, ny, nz)): x periodic,
+    walls on y and z, B0 along y, nu = eta (0.01 by default), chi = 0.01
+    (Pr_m = 0.01), F_x = 1e-6 uniform (or, with force_field = 3, a per-node
+    field set by the caller), FP32."""
     from paper_0809_4730_gb300.glbe import Solver
+    nx, ny, nz = shape if shape is not None else (n, n, n)
     eta = nu
-    L = (n - 2) / 2
+    L = (ny - 2) / 2
     B0 = Ha * math.sqrt(nu * eta) / L
     F = (0.0, 0.0, 0.0) if force_field else (1e-6, 0, 0)
-    G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=F, induction=1,
+    G = Solver(nx, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=nu, F=F, induction=1,
                gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0), device=device, storage=storage,
                variant=variant, force_field=force_field)
-    return G, n * (n - 2) * (n - 2)
+    return G, nx * (ny - 2) * (nz - 2)
 
 
 def bytes_per_node(storage: str, mhd: bool, force_comp: int) -> int:
@@ -359,10 +361,13 @@ def run_glbe(args, rank, ws):
     del G
     torch.cuda.empty_cache()
 
+    refs = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], refs = cpu_baseline()
     if not args.no_variants:
         line["variants"] = variants(args, hbm_peak, stream)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        if refs is not None:
+            line["steady_error"], line["time_to_solution"] = duct64_study(refs)
     return line
 
 
@@ -399,8 +404,52 @@ def variants(args, hbm_peak, stream):
         G.close()
         del G
         torch.cuda.empty_cache()
+    # the fused coupled step on the large coupled grid: the Hartmann physics
+    # (Ha = 10, gamma = 0.1, Pr_m = 0.01) on 512 x 256 x 256
+    for st in ("f32", "bf16"):
+        G, fluid = hartmann_duct_solver(storage=st, shape=(512, 256, 256))
+        G.step(30)
+        G.sync()
+        total_ms, plain_ms, nplain = timed_steps(G, 3, stream)
+        kern_ms = plain_ms / nplain
+        bpn = bytes_per_node(st, True, 0)
+        out[f"mhd_duct_512x256x256_{st}"] = {
+            "mlups": round(30 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
+            "bytes_per_node": bpn, "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+    out["batch_64_ducts_bounded"] = batch_bounded(hbm_peak)
     out["time_to_1e-8_hartmann_64x64x8"] = time_to_solution()
     return out
+
+
+def batch_bounded(hbm_peak: float, levels: int = 200):
+    """The 64-duct batch (F32C) marched a fixed number of levels in one
+    persistent launch (no domain converges that early): aggregate MLUPS and
+    the fraction of the HBM roofline at the algorithmic bytes of each domain
+    (F32C: 19 x 6 x 2 B per flow node; coupled nodes add 21 x 6 x 2 B of the
+    vector lattice and 24 B of lagged Lorentz force; the residual snapshot,
+    24 B read + written once per 10 levels, adds 4.8 B per level)."""
+    import torch
+    from paper_0809_4730_gb300.glbe import Batch
+    doms, meta = batch_domains("f32c")
+    B = Batch(doms)
+    bt, bps, sps = B.autotune(10)
+    st, res, sec = B.solve(1e-300, levels, use_graph=True)
+    upd, byt = 0, 0.0
+    for m in meta:
+        fluid = m["n"] * (m["n"] - 2) ** 2
+        bpn = 19 * 6 * 2 + 4.8 + ((21 * 6 * 2 + 24) if m["Ha"] > 0 else 0)
+        upd += fluid * levels
+        byt += fluid * levels * bpn
+    B.close()
+    del B
+    torch.cuda.empty_cache()
+    return {"levels": levels, "mlups": round(upd / sec / 1e6, 1), "seconds": round(sec, 4),
+            "achieved_gbs": round(byt / sec / 1e9, 1), "hbm_frac": round(byt / sec / 1e9 / hbm_peak, 4),
+            "launch": {"block_threads": bt, "blocks_per_sm": bps}, "status": st,
+            "note": "one persistent cooperative launch over all 64 domains, F32C storage, device time"}
 
 
 def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
@@ -466,7 +515,41 @@ def oracle_sample():
     return S, fluid, f"oracle FP64 on an {nx}x{d['ny']}x{d['nz']} slab of the duct"
 
 
+DUCT64_GAMMAS = (1.0, 0.5, 0.1, 0.05)
+
+
+def duct64_oracle_columns():
+    """The 64^3 copy of the duct (same F_x(y, z) and nu, H = 64): its steady
+    state is x-invariant, so the oracle marches the 1 x 64 x 64 column, the
+    same discrete problem, at each gamma of the sweep: timed to r <= 1e-8
+    (steps and wall time of the FP64 CPU method), then on to r <= 1e-11 for
+    the converged reference field."""
+    import numpy as np
+    import oracle
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    n = 64
+    Fx = duct_force_x(1, n, n, DUCT["F0"])[0].reshape(-1)
+    Fext = np.zeros((n * n, 3))
+    Fext[:, 0] = Fx
+    out = {}
+    for gamma in DUCT64_GAMMAS:
+        S = oracle.Solver(oracle.Config(1, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=DUCT["nu"]),
+                          Fext=Fext)
+        t0 = time.perf_counter()
+        S.run(3_000_000, tol=1e-8)
+        dt = time.perf_counter() - t0
+        t8 = S.t
+        S.run(3_000_000, tol=1e-11)
+        _, u, _, _ = S.fields()
+        out[gamma] = {"steps_1e-8": t8, "wall_s_1e-8_column": round(dt, 3),
+                      "mlups": round(n * n * t8 / dt / 1e6, 3), "col": u[:, 0].reshape(n, n)}
+    return out
+
+
 def cpu_baseline(target_s: float = 10.0):
+    """The CPU leg: the FP64 oracle timed on a bounded sample of the duct
+    (value), and on the 64^3 duct copy's column per gamma, whose converged
+    fields are the references of the GPU steady errors (returned apart)."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
@@ -478,8 +561,68 @@ def cpu_baseline(target_s: float = 10.0):
     t0 = time.perf_counter()
     S.run(n)
     dt = time.perf_counter() - t0
-    return {"value": round(n * fluid / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{desc}, {n} time steps, {dt:.1f} s"}
+    refs = duct64_oracle_columns()
+    cols = {f"gamma_{g}": {k: v for k, v in r.items() if k != "col"} for g, r in refs.items()}
+    return ({"value": round(n * fluid / dt / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(),
+             "kind": "oracle", "sample": f"{desc}, {n} time steps, {dt:.1f} s",
+             "duct64_column_to_1e-8": cols}, refs)
+
+
+def duct64_study(refs):
+    """GPU side of the 64^3 duct copy, against the oracle references:
+    (1) steady error of each storage form at gamma = 0.1 after 4000 steps
+    (relative L-infinity of u_x over the fluid nodes); (2) time to r <= 1e-8
+    with compensated storage at each gamma of the sweep: steps, device wall
+    time, error against the converged oracle field, and the gain over
+    gamma = 1 at the same physical nu."""
+    import numpy as np
+    import torch
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    n = 64
+    Ff = torch.tensor(duct_force_x(n, n, n, DUCT["F0"])[0].reshape(1, -1), dtype=torch.float32, device="cuda")
+
+    def make(st, gamma):
+        G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=DUCT["nu"], force_field=1,
+                   storage=st)
+        G.set_force(Ff)
+        return G
+
+    def err(G, col):
+        _, u, _ = G.fields()
+        torch.cuda.synchronize()
+        ux = u[0].double().cpu().numpy().reshape(n, n, n)[1:-1, 1:-1, :]
+        c = col[1:-1, 1:-1]
+        return float(np.abs(ux - c[:, :, None]).max() / np.abs(c).max())
+
+    steady = {"workload": "64^3 duct copy, gamma = 0.1, 4000 steps from rest, rel. L-inf error of u_x against "
+                          "the converged FP64 oracle"}
+    for st in ("f32c", "f32", "f16", "bf16", "f16sr", "bf16sr"):
+        G = make(st, 0.1)
+        G.step(4000)
+        info = G.residual()
+        steady[st] = {"error": err(G, refs[0.1]["col"]), "r": info.r}
+        G.close()
+    stream = torch.cuda.current_stream()
+    tts = {"workload": "64^3 duct copy (nu = 0.5, F0 = 1e-6), F32C storage, glbe_solve to r <= 1e-8 from rest"}
+    for gamma in DUCT64_GAMMAS:
+        G = make("f32c", gamma)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        status, steps, r = G.solve(1e-8, 500_000)
+        e1.record(stream)
+        e1.synchronize()
+        tts[f"gamma_{gamma}"] = {"status": status, "steps": steps, "r": r, "wall_s": round(e0.elapsed_time(e1) / 1e3, 4),
+                                 "error_vs_oracle": err(G, refs[gamma]["col"]),
+                                 "oracle_steps_1e-8": refs[gamma]["steps_1e-8"]}
+        G.close()
+    base = tts["gamma_1.0"]
+    for gamma in DUCT64_GAMMAS[1:]:
+        a = tts[f"gamma_{gamma}"]
+        a["gain_wall_vs_gamma_1"] = round(base["wall_s"] / a["wall_s"], 2) if a["wall_s"] > 0 else None
+        a["gain_steps_vs_gamma_1"] = round(base["steps"] / max(1, a["steps"]), 2)
+    return steady, tts
 
 
 def run_reference(args, rank, ws):

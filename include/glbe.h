@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define GLBE_ABI_VERSION 3
+#define GLBE_ABI_VERSION 4
 
 typedef struct glbe_ctx glbe_ctx;
 
@@ -70,11 +70,23 @@ typedef enum {
     GLBE_F32 = 0,   /* deviations stored as FP32                                    */
     GLBE_BF16 = 1,  /* deviations stored as BF16 (round to nearest even), FP32 math */
     GLBE_F16 = 2,   /* deviations stored as FP16, times storage_scale, FP32 math    */
-    GLBE_F32C = 3   /* compensated: FP32 deviation plus an FP16 remainder (2^36
+    GLBE_F32C = 3,  /* compensated: FP32 deviation plus an FP16 remainder (2^36
                        scaled), updated by an exact two-sum; FP32 math; 6 bytes
                        per population.  Corrections below one FP32 ulp of the
                        stored deviation accumulate instead of being dropped, which
                        removes the FP32 stagnation floor of steady solves.    */
+    GLBE_BF16_SR = 4, /* BF16 deviations rounded stochastically (unbiased: rounded
+                       away from zero with probability equal to the dropped
+                       fraction of a unit in the last place), FP32 math; 2 bytes
+                       per population.  Round-to-nearest drops every correction
+                       below half a unit in the last place, so a steady march
+                       freezes at a false fixed point (error ~ ulp / decay rate
+                       of the slowest mode); stochastic rounding removes that
+                       bias and leaves zero-mean noise of about one ulp.  The
+                       random bits are counter-based (node, population, step),
+                       so a march is reproducible.                            */
+    GLBE_F16_SR = 5   /* FP16 deviations times storage_scale, rounded
+                       stochastically as GLBE_BF16_SR                         */
 } glbe_storage;
 
 typedef struct {
@@ -95,7 +107,7 @@ typedef struct {
     double mu;                /* magnetic permeability                           */
     double B0[3];             /* applied field: initial state and wall value      */
     int storage;              /* glbe_storage                                    */
-    double storage_scale;     /* F16 only: multiplier on the stored deviations (0 = default 4096);
+    double storage_scale;     /* F16 and F16_SR: multiplier on the stored deviations (0 = default 4096);
                                  ignored for the other storage forms */
     void* stream;             /* cudaStream_t owned by the caller                */
     int variant;              /* kernel form: 0 = automatic (on grids without walls along x and an even
@@ -106,7 +118,7 @@ typedef struct {
                                  no walls along x, else the one-node form is used); 3 = tiles of 128
                                  x-nodes whose gathers are staged in shared memory by tensor-memory
                                  copies (needs no walls along x, nx a multiple of 128, F32, BF16 or
-                                 F16 storage; else the one-node form is used); 4 = the same tiles with
+                                 F16 storage, not the _SR forms; else the one-node form is used); 4 = the same tiles with
                                  two x-adjacent nodes per thread in packed FP32x2 arithmetic */
 } glbe_params;
 
@@ -236,8 +248,14 @@ void glbe_destroy(glbe_ctx* ctx);
  * file-scope static array in the library's device memory, held by every GPU
  * that loads the library until the process exits.  The first call on a device
  * looks up that array's device address; make this first call before any
- * stream capture.  Every call shares the array, so calls that overlap on the
- * GPU (other threads or streams) race and must be serialised by the caller.
+ * stream capture.  The address is kept per device and per driver context: after
+ * cudaDeviceReset (or when the device's primary context is released and
+ * created again) the next call looks it up anew, so make that call, too,
+ * outside any stream capture.  Every call shares the array, so calls that
+ * overlap on the GPU (other threads or streams) race and must be serialised by
+ * the caller.  With variant 3 or 4, GLBE_ERR_TIMEOUT reports that a bounded
+ * pipeline wait of the TMA-staged kernel ran out (the outputs are then
+ * incomplete).  The residual record is read back on p->stream.
  * Grids of more than 4,194,304 nodes (16384 blocks of 256) and buffers that
  * are not 16-byte aligned are rejected with GLBE_ERR_ARG.  No call to cudaMalloc, cudaFree or any allocating routine is
  * made. */

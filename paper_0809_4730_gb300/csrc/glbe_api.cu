@@ -56,9 +56,13 @@ struct Layout {
     size_t f[2], g[2], FL, Ffield, usnap, partials, record, hist, misc, Fstage, total;
 };
 
-size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : (st == GLBE_F32C ? 6 : 2); }
+size_t storage_bytes(int st) { return st == GLBE_F32 ? 4 : (st == GLBE_F32C ? 6 : 2); }   // the others: 16 bits
 
 unsigned step_grid(size_t N) { return (unsigned)((N + STEP_THREADS - 1) / STEP_THREADS); }
+
+// Rows of the velocity snapshot: the FP32 and compensated forms keep u as a
+// double-float pair (high and low parts), the 16-bit forms the high part.
+size_t snap_rows(int st) { return (st == GLBE_F32 || st == GLBE_F32C) ? 6 : 3; }
 
 Layout make_layout(const glbe_params* p)
 {
@@ -77,7 +81,7 @@ Layout make_layout(const glbe_params* p)
         L.g[0] = L.g[1] = L.FL = (size_t)-1;
     }
     L.Ffield = p->force_field ? take((size_t)p->force_field * N * sizeof(float)) : (size_t)-1;
-    L.usnap = take(3 * N * sizeof(float));
+    L.usnap = take(snap_rows(p->storage) * N * sizeof(float));
     L.partials = take((size_t)step_grid(N) * PARTIAL_STRIDE * sizeof(double));
     L.record = take(RECORD_STRIDE * sizeof(double));
     L.hist = take((size_t)HIST_CAP * RECORD_STRIDE * sizeof(double));
@@ -117,8 +121,8 @@ glbe_status glbe::validate_params(const glbe_params* p)
         if (!(p->chi > 0.0)) return fail(GLBE_ERR_ARG, "chi must be > 0");
         if (!(p->mu > 0.0)) return fail(GLBE_ERR_ARG, "mu must be > 0");
     }
-    if (p->storage != GLBE_F32 && p->storage != GLBE_BF16 && p->storage != GLBE_F16 && p->storage != GLBE_F32C)
-        return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16 or GLBE_F32C");
+    if (p->storage < GLBE_F32 || p->storage > GLBE_F16_SR)
+        return fail(GLBE_ERR_ARG, "storage must be GLBE_F32, GLBE_BF16, GLBE_F16, GLBE_F32C, GLBE_BF16_SR or GLBE_F16_SR");
     if (p->variant < 0 || p->variant > 4) return fail(GLBE_ERR_ARG, "variant must be 0 ... 4");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
@@ -172,7 +176,7 @@ StepParams glbe::make_step_params(const glbe_params* p)
         s.J_coef = (float)(-1.0 / (p->mu * p->chi * tau_m * THETA_M));
     }
     double scale = p->storage_scale;
-    if (p->storage != GLBE_F16) scale = 1.0;   // only FP16 stores scaled deviations
+    if (p->storage != GLBE_F16 && p->storage != GLBE_F16_SR) scale = 1.0;   // only FP16 stores scaled deviations
     else if (scale == 0.0) scale = 4096.0;
     s.scale = (float)scale;
     s.inv_scale = (float)(1.0 / scale);
@@ -319,6 +323,7 @@ struct glbe_ctx {
     long long* t_dev;
     int* stop_dev;
     double* tol_dev;
+    unsigned* sr_ctr;   // [2] seeds of stochastic rounding, read by the step of parity t & 1
     double mass0;   // rho0 x number of fluid nodes
     long t;         // current time level
     long t_snap;    // level of the velocity snapshot, -1 if none
@@ -341,6 +346,8 @@ cudaError_t launch_step_any(glbe_ctx* c, int mode, const StepBuffers& b, const F
     case GLBE_F32: return launch_step_t<ST_F32>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
     case GLBE_BF16: return launch_step_t<ST_BF16>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
     case GLBE_F16: return launch_step_t<ST_F16>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
+    case GLBE_BF16_SR: return launch_step_t<ST_BF16_SR>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
+    case GLBE_F16_SR: return launch_step_t<ST_F16_SR>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
     default: return launch_step_t<ST_F32C>(c->prm.induction, mode, c->sp, b, fo, st, nblocks);
     }
 }
@@ -359,6 +366,10 @@ StepBuffers buffers_for(glbe_ctx* c, long t)
     b.partials = c->partials;
     b.have_snap = 0;
     b.stop = nullptr;
+    b.snap_lo = snap_rows(c->prm.storage) == 6 ? 1 : 0;
+    b.sr_ctr = c->sr_ctr;
+    b.sr_par = s;
+    b.sr_seed = 0;
     return b;
 }
 
@@ -513,6 +524,7 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     c->t_dev = reinterpret_cast<long long*>(misc + 8);
     c->tol_dev = reinterpret_cast<double*>(misc + 16);
     c->stop_dev = reinterpret_cast<int*>(misc + 24);
+    c->sr_ctr = reinterpret_cast<unsigned*>(misc + 32);
     {
         // fluid nodes: product over the axes of the planes not on a wall
         const long long fx = p->nx - p->wall_lo[0] - p->wall_hi[0];
@@ -530,7 +542,9 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
 
     // rest state: all deviations zero (all-zero bits in every storage type)
     cudaError_t e = cudaMemsetAsync(c->ws, 0, L.usnap, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.usnap, 0, 3 * c->N * sizeof(float), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->ws + L.usnap, 0, snap_rows(p->storage) * c->N * sizeof(float), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sr_ctr, 0, 2 * sizeof(unsigned), c->stream);
     if (e == cudaSuccess) {
         misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, 10, c->stop_dev, 0, c->tol_dev, 0.0, c->record,
                                                 c->hist_count, 1);
@@ -792,6 +806,8 @@ glbe_status glbe_get_state(glbe_ctx* c, float* d_df, float* d_dg, float* d_FL)
     case GLBE_F32: e = launch_get_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_BF16: e = launch_get_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_F16: e = launch_get_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_BF16_SR: e = launch_get_state_t<ST_BF16_SR>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_F16_SR: e = launch_get_state_t<ST_F16_SR>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     default: e = launch_get_state_t<ST_F32C>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     }
     GLBE_CUDA(e, "get_state kernel");
@@ -809,6 +825,8 @@ glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, co
     case GLBE_F32: e = launch_set_state_t<ST_F32>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_BF16: e = launch_set_state_t<ST_BF16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     case GLBE_F16: e = launch_set_state_t<ST_F16>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_BF16_SR: e = launch_set_state_t<ST_BF16_SR>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
+    case GLBE_F16_SR: e = launch_set_state_t<ST_F16_SR>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     default: e = launch_set_state_t<ST_F32C>(mhd, c->sp, c->f[s], c->g[s], c->FL, d_df, d_dg, d_FL, c->stream); break;
     }
     GLBE_CUDA(e, "set_state kernel");
@@ -845,7 +863,7 @@ size_t ckpt_total(const glbe_ctx* c)
     const size_t fb = 19 * c->N * storage_bytes(c->prm.storage);
     const size_t gb = c->prm.induction ? 21 * c->N * storage_bytes(c->prm.storage) : 0;
     return sizeof(CkptHeader) + fb + gb + (c->prm.induction ? 3 * c->N * sizeof(float) : 0) +
-           (size_t)c->prm.force_field * c->N * sizeof(float) + 3 * c->N * sizeof(float) +
+           (size_t)c->prm.force_field * c->N * sizeof(float) + snap_rows(c->prm.storage) * c->N * sizeof(float) +
            RECORD_STRIDE * sizeof(double);
 }
 
@@ -879,6 +897,9 @@ extern "C" glbe_status glbe_checkpoint_save(glbe_ctx* c, void* h_buf, size_t byt
     long long tdev = 0;
     GLBE_CUDA(cudaMemcpy(&tdev, c->t_dev, sizeof tdev, cudaMemcpyDeviceToHost), "checkpoint t");
     h.t_dev = tdev;
+    unsigned seed = 0;   // stochastic-rounding seed of the step from level t
+    GLBE_CUDA(cudaMemcpy(&seed, c->sr_ctr + (c->t & 1), sizeof seed, cudaMemcpyDeviceToHost), "checkpoint seed");
+    h.reserved[0] = seed;
     h.N = c->N;
     h.f_bytes = 19 * c->N * storage_bytes(c->prm.storage);
     h.g_bytes = c->prm.induction ? 21 * c->N * storage_bytes(c->prm.storage) : 0;
@@ -900,8 +921,9 @@ extern "C" glbe_status glbe_checkpoint_save(glbe_ctx* c, void* h_buf, size_t byt
         GLBE_CUDA(cudaMemcpy(o, c->Ffield, fb, cudaMemcpyDeviceToHost), "checkpoint force");
         o += fb;
     }
-    GLBE_CUDA(cudaMemcpy(o, c->usnap, 3 * c->N * sizeof(float), cudaMemcpyDeviceToHost), "checkpoint snapshot");
-    o += 3 * c->N * sizeof(float);
+    const size_t snap_bytes = snap_rows(c->prm.storage) * c->N * sizeof(float);
+    GLBE_CUDA(cudaMemcpy(o, c->usnap, snap_bytes, cudaMemcpyDeviceToHost), "checkpoint snapshot");
+    o += snap_bytes;
     GLBE_CUDA(cudaMemcpy(o, c->record, RECORD_STRIDE * sizeof(double), cudaMemcpyDeviceToHost), "checkpoint record");
     return GLBE_OK;
 }
@@ -935,14 +957,18 @@ extern "C" glbe_status glbe_checkpoint_load(glbe_ctx* c, const void* h_buf, size
         GLBE_CUDA(cudaMemcpy(c->Ffield, in, fb, cudaMemcpyHostToDevice), "restore force");
         in += fb;
     }
-    GLBE_CUDA(cudaMemcpy(c->usnap, in, 3 * c->N * sizeof(float), cudaMemcpyHostToDevice), "restore snapshot");
-    in += 3 * c->N * sizeof(float);
+    const size_t snap_bytes = snap_rows(c->prm.storage) * c->N * sizeof(float);
+    GLBE_CUDA(cudaMemcpy(c->usnap, in, snap_bytes, cudaMemcpyHostToDevice), "restore snapshot");
+    in += snap_bytes;
     GLBE_CUDA(cudaMemcpy(c->record, in, RECORD_STRIDE * sizeof(double), cudaMemcpyHostToDevice), "restore record");
     // residual level counter as saved; a fresh history; no pending stop
     misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, (long long)h.t_dev, c->stop_dev, 0, c->tol_dev, 0.0, nullptr,
                                             nullptr, 0);
     GLBE_CUDA(cudaGetLastError(), "restore counters");
     GLBE_CUDA(cudaMemsetAsync(c->hist_count, 0, sizeof(unsigned long long), c->stream), "restore history");
+    const unsigned seed = (unsigned)h.reserved[0];
+    GLBE_CUDA(cudaMemcpyAsync(c->sr_ctr + (h.t & 1), &seed, sizeof seed, cudaMemcpyHostToDevice, c->stream),
+              "restore seed");
     GLBE_CUDA(cudaStreamSynchronize(c->stream), "restore sync");
     c->t = (long)h.t;
     c->t_snap = (long)h.t_snap;

@@ -150,14 +150,19 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
                 b.gdst = D.g[par ^ 1];
                 b.FL = D.FL;
                 b.usnap = D.usnap;
+                b.snap_lo = 1;
                 b.have_snap = have_snap ? 1 : 0;
                 const FieldOut fo{nullptr, nullptr, nullptr};
                 const uint32_t i = (tile - tile_start[d]) * BT + threadIdx.x;
                 // populations written by other blocks earlier in this launch:
-                // coherent (L2) loads
+                // coherent (L2) loads.  A coupled node is updated in two passes
+                // (induction, then flow with this step's Lorentz force), each
+                // within the kernel's register budget; the one-pass update
+                // spilled over a kilobyte per thread.
                 if (D.mhd) {
-                    if (resid) scalar_node_step<ST, true, MODE_STEP_RESID, true>(sp, b, fo, i, acc);
-                    else scalar_node_step<ST, true, MODE_STEP, true>(sp, b, fo, i, acc);
+                    coupled_induction_pass<ST, true>(sp, b, i);
+                    if (resid) scalar_node_step<ST, false, MODE_STEP_RESID, true, false, true>(sp, b, fo, i, acc);
+                    else scalar_node_step<ST, false, MODE_STEP, true, false, true>(sp, b, fo, i, acc);
                 } else {
                     if (resid) scalar_node_step<ST, false, MODE_STEP_RESID, true>(sp, b, fo, i, acc);
                     else scalar_node_step<ST, false, MODE_STEP, true>(sp, b, fo, i, acc);
@@ -311,7 +316,7 @@ glbe_status batch_layout(const glbe_params* doms, int n, std::vector<DomLayout>*
         } else {
             L.g[0] = L.g[1] = L.FL = (size_t)-1;
         }
-        L.usnap = take(3 * N * sizeof(float));
+        L.usnap = take(6 * N * sizeof(float));   // double-float velocity snapshot (F32, F32C)
         L.end = off;
         tiles128 += (N + 127) / 128;
     }

@@ -77,9 +77,11 @@ struct StepBuffers {
     void* gdst;
     float* FL;            // [3][N] Lorentz force of the previous step (in place)
     const float* Ffield;  // [force_ncomp][N] or null
-    float* usnap;         // [3][N] velocity snapshot of the last residual level
+    float* usnap;         // [3][N] velocity snapshot of the last residual level; with snap_lo
+                          // [6][N], rows 3..5 the low parts of u (double-float snapshot)
     double* partials;     // [8][gridDim.x] per-block residual sums
     int have_snap;        // 1: usnap holds u(t-10)
+    int snap_lo;          // 1: usnap is [6][N] (FP32 and compensated storage)
     const int* stop;      // null, or a device flag: when set the launch does nothing
     // Per-direction addresses of the population buffers, filled by the
     // launcher from fsrc, fdst and StepParams::doff (kernels launched
@@ -94,9 +96,20 @@ struct StepBuffers {
     // pf_ahead positions later will gather -- one resident wave of the
     // launched kernel ahead
     long long pf_ahead;
+    // Stochastic rounding (storage forms BF16_SR, F16_SR): the step's seed is
+    // sr_ctr[sr_par] (a device counter pair; the step writes the next step's
+    // seed, sr_ctr[sr_par ^ 1] = seed + 1, which no block of this step
+    // reads), or sr_seed when sr_ctr is null.
+    unsigned* sr_ctr;
+    int sr_par;
+    unsigned sr_seed;
 };
 
-enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3 };
+// Storage forms of the population deviations.  The _SR forms store BF16 /
+// FP16 like ST_BF16 / ST_F16 but round each stored value stochastically.
+enum Storage { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2, ST_F32C = 3, ST_BF16_SR = 4, ST_F16_SR = 5 };
+// The layout (and load path) a storage form shares
+constexpr int base_storage(int st) { return st == ST_BF16_SR ? ST_BF16 : (st == ST_F16_SR ? ST_F16 : st); }
 enum Mode { MODE_STEP = 0, MODE_STEP_RESID = 1, MODE_FIELDS = 2 };
 
 constexpr int STEP_THREADS = 256;   // scalar kernel: one node per thread

@@ -75,6 +75,20 @@ __device__ __forceinline__ V two_sum_round(V a, V b, V c)
     return vadd_rn(s, vadd_rn(e, c));
 }
 
+// The same rounded sum, and in lo its remainder: hi + lo = fl(a + b) exactly
+// + fl(e + c) (the double-float value the rounding of hi dropped).
+template <class V>
+__device__ __forceinline__ V two_sum_round_lo(V a, V b, V c, V& lo)
+{
+    const V s = vadd_rn(a, b);
+    const V bp = vsub_rn(s, a);
+    const V e = vadd_rn(vsub_rn(a, vsub_rn(s, bp)), vsub_rn(b, bp));
+    const V t = vadd_rn(e, c);
+    const V hi = vadd_rn(s, t);
+    lo = vsub_rn(t, vsub_rn(hi, s));
+    return hi;
+}
+
 // h + o + l as a new (high, low) pair: exact two-sum of h and o, the
 // remainder plus the old low part renormalised into the new low part.
 template <class V>
@@ -119,7 +133,7 @@ __device__ __forceinline__ uint32_t ldg_l2_256(const uint32_t* p)
 
 template <> struct Store<ST_F32> {
     using T = float;
-    static constexpr bool COMP = false, SCALED = false;
+    static constexpr bool COMP = false, SCALED = false, SR = false;
     static __device__ __forceinline__ float ld(const T* p) { return ldg_l2_256(p); }
     static __device__ __forceinline__ T cv(float v) { return v; }
     static __device__ __forceinline__ F2 ld2(const T* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
@@ -127,7 +141,7 @@ template <> struct Store<ST_F32> {
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
-    static constexpr bool COMP = false, SCALED = false;
+    static constexpr bool COMP = false, SCALED = false, SR = false;
     static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
     // a BF16 value is the high half of the FP32 with the same bits: the pair
@@ -145,7 +159,7 @@ template <> struct Store<ST_BF16> {
 };
 template <> struct Store<ST_F16> {
     using T = __half;
-    static constexpr bool COMP = false, SCALED = true;
+    static constexpr bool COMP = false, SCALED = true, SR = false;
     static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v); }
     static __device__ __forceinline__ F2 ld2(const T* p)
@@ -159,7 +173,7 @@ template <> struct Store<ST_F16> {
 };
 template <> struct Store<ST_F32C> {
     using T = float;
-    static constexpr bool COMP = true, SCALED = false;
+    static constexpr bool COMP = true, SCALED = false, SR = false;
     static __device__ __forceinline__ float ld(const T* p) { return ldg_l2_256(p); }
     static __device__ __forceinline__ T cv(float v) { return v; }
     static __device__ __forceinline__ F2 ld2(const T* p) { return F2(__ldg(reinterpret_cast<const float2*>(p))); }
@@ -177,6 +191,105 @@ template <> struct Store<ST_F32C> {
     }
 };
 
+// Stochastically rounded 16-bit forms.  A value is stored as the 16-bit
+// number next to it towards zero or away from zero, the latter with
+// probability equal to the fraction of a unit in the last place by which it
+// exceeds the former, so the stored value is unbiased.  Round-to-nearest
+// drops every correction smaller than half a unit in the last place, which
+// freezes the slow modes of a steady march at a false fixed point (the
+// stagnation error ~ ulp / decay rate); rounded stochastically they keep
+// moving to the right state on average.  Blackwell converts with explicit
+// random bits (cvt.rs): the conversion of the pair (a, b) packs a into the
+// upper and b into the lower 16 bits.
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float a, float b, uint32_t rbits)
+{
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float a, float b, uint32_t rbits)
+{
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    return d;
+}
+
+template <> struct Store<ST_BF16_SR> : Store<ST_BF16> {
+    static constexpr bool SR = true;
+    static __device__ __forceinline__ T cv_sr(float v, uint32_t r)
+    {
+        return __ushort_as_bfloat16((unsigned short)(cvt_rs_bf16x2(v, 0.f, r) >> 16));
+    }
+    static __device__ __forceinline__ void st2_sr(T* p, F2 v, uint32_t r)
+    {
+        *reinterpret_cast<uint32_t*>(p) = cvt_rs_bf16x2(v.v.y, v.v.x, r);   // element 0 in the low half
+    }
+};
+template <> struct Store<ST_F16_SR> : Store<ST_F16> {
+    static constexpr bool SR = true;
+    static __device__ __forceinline__ T cv_sr(float v, uint32_t r)
+    {
+        return __ushort_as_half((unsigned short)(cvt_rs_f16x2(v, 0.f, r) >> 16));
+    }
+    static __device__ __forceinline__ void st2_sr(T* p, F2 v, uint32_t r)
+    {
+        *reinterpret_cast<uint32_t*>(p) = cvt_rs_f16x2(v.v.y, v.v.x, r);
+    }
+};
+
+// Random bits of the stochastic rounding: counter-based, so that a march is
+// reproducible.  A node's (or pair's) generator starts from the MurmurHash3
+// 32-bit finalizer (Appleby) of its index mixed with the hashed step seed,
+// then steps a linear congruential generator (Numerical Recipes constants)
+// once per stored population, its output whitened by a xor-shift.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+struct SrBits {
+    uint32_t s;
+    __device__ __forceinline__ SrBits(uint32_t node, uint32_t seed) : s(fmix32(node * 0x9e3779b9u + fmix32(seed))) {}
+    __device__ __forceinline__ uint32_t next()
+    {
+        s = s * 1664525u + 1013904223u;
+        return s ^ (s >> 16);
+    }
+};
+// The step's seed (see StepBuffers::sr_ctr); 0 for the other forms.
+template <int ST>
+__device__ __forceinline__ uint32_t step_seed(const StepBuffers& b)
+{
+    if constexpr (Store<ST>::SR) return b.sr_ctr ? __ldg(b.sr_ctr + b.sr_par) : b.sr_seed;
+    else return 0u;
+}
+// One thread of the step writes the next step's seed; no block of this step
+// reads that slot.
+template <int ST>
+__device__ __forceinline__ void advance_seed(const StepBuffers& b)
+{
+    if constexpr (Store<ST>::SR) {
+        if (b.sr_ctr && blockIdx.x == 0 && threadIdx.x == 0) b.sr_ctr[b.sr_par ^ 1] = step_seed<ST>(b) + 1u;
+    }
+}
+// Stores of one value / one x-adjacent pair in the storage type.
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::T store_cv(float v, SrBits& rb)
+{
+    if constexpr (Store<ST>::SR) return Store<ST>::cv_sr(v, rb.next());
+    else return Store<ST>::cv(v);
+}
+template <int ST>
+__device__ __forceinline__ void store_pair(typename Store<ST>::T* p, F2 v, SrBits& rb)
+{
+    if constexpr (Store<ST>::SR) Store<ST>::st2_sr(p, v, rb.next());
+    else Store<ST>::st2(p, v);
+}
+
 // Loads of populations written earlier in the same launch (the persistent
 // batch kernel) must not use the non-coherent read-only path: CG = true reads
 // through L2 (ld.global.cg).
@@ -184,8 +297,8 @@ template <int ST, bool CG>
 __device__ __forceinline__ float ldp(const typename Store<ST>::T* p)
 {
     if constexpr (CG) {
-        if constexpr (ST == ST_BF16) return __bfloat162float(__ldcg(p));
-        else if constexpr (ST == ST_F16) return __half2float(__ldcg(p));
+        if constexpr (base_storage(ST) == ST_BF16) return __bfloat162float(__ldcg(p));
+        else if constexpr (base_storage(ST) == ST_F16) return __half2float(__ldcg(p));
         else return __ldcg(p);
     } else {
         return Store<ST>::ld(p);
@@ -772,10 +885,11 @@ struct NodeMoments {
 
 // D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
 // (I - Lambda*/2) S*] (Eqs. ppostcollision, prelax_term).  F is the total
-// force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32.
+// force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32, (jlx, jly, jlz) the
+// remainders of that rounding (precise forms; 0 otherwise).
 template <class V, bool PRECISE>
 __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<V, PRECISE>& mm, V (&om)[19],
-                                             V rho_inv, V jx, V jy, V jz, V Fx, V Fy, V Fz)
+                                             V rho_inv, V jx, V jy, V jz, V jlx, V jly, V jlz, V Fx, V Fy, V Fz)
 {
     const V ig(p.inv_gamma);
     const V gri = ig * rho_inv;                   // 1/(gamma rho)
@@ -790,9 +904,23 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     // 3 rho0 to row 2 only, so the deviations' moments enter directly
     const V n1 = GLBE_NK(H.E1 - V(19.f) * jjg, L.E1);
     const V n2 = GLBE_NK(H.E2 + V(5.5f) * jjg, L.E2);
-    const V n4 = GLBE_NK(H.Qx, L.Qx) + V(2.f / 3.f) * jx;
-    const V n6 = GLBE_NK(H.Qy, L.Qy) + V(2.f / 3.f) * jy;
-    const V n8 = GLBE_NK(H.Qz, L.Qz) + V(2.f / 3.f) * jz;
+    // heat-flux rows: n = q + (2/3) j is a near-cancellation of two values of
+    // the size of j.  The precise forms take 3 n = (3 q_h + 2 j) + (3 q_l +
+    // 2 j_l): the first sum is exact (3 q_h on the 2^-28 grid, 2 j an FP32
+    // number, nearly opposite), so n no longer carries the rounding of j --
+    // which otherwise moved the converged FP32 state by about one unit in
+    // the last place every few steps (residual floor ~1.4e-8).
+    V n4, n6, n8;
+    if constexpr (PRECISE) {
+        const V third(1.f / 3.f);
+        n4 = (vadd_rn(V(3.f) * H.Qx, V(2.f) * jx) + (V(3.f) * L.Qx + V(2.f) * jlx)) * third;
+        n6 = (vadd_rn(V(3.f) * H.Qy, V(2.f) * jy) + (V(3.f) * L.Qy + V(2.f) * jly)) * third;
+        n8 = (vadd_rn(V(3.f) * H.Qz, V(2.f) * jz) + (V(3.f) * L.Qz + V(2.f) * jlz)) * third;
+    } else {
+        n4 = H.Qx + V(2.f / 3.f) * jx;
+        n6 = H.Qy + V(2.f / 3.f) * jy;
+        n8 = H.Qz + V(2.f / 3.f) * jz;
+    }
     const V e9 = V(3.f) * xx - jjg;
     const V e11 = yy - zz;
     const V n9 = GLBE_NK(H.P9 - e9, L.P9);
@@ -925,9 +1053,15 @@ __device__ __forceinline__ V post_collision(V f, V om)
 }
 
 // Result of one node's (or pair's) update besides the new populations.
+// ulx, uly, ulz (the FP32 and compensated forms): the low parts of u, so
+// that u = u_hi + u_lo resolves changes below one unit in the last place of
+// u_hi.  The residual of a converged march in FP32 arithmetic is otherwise
+// floored by u_hi's own rounding (a state that still moves by 1e-12 flips
+// u_hi by one unit of 6e-8 at many nodes: r ~ 3e-8).
 template <class V>
 struct NodeState {
     V rho, drho, jx, jy, jz, ux, uy, uz;
+    V ulx, uly, ulz;
     NodeMacro<V> mac;
 };
 
@@ -974,10 +1108,11 @@ __device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19
     // j = m + F/(2 gamma): in the precise path the high parts and the
     // half-force are added by an exact two-sum before rounding once
     const V hg(0.5f * p.inv_gamma);
+    V jlx(0.f), jly(0.f), jlz(0.f);
     if constexpr (PRECISE) {
-        ns.jx = two_sum_round(mxh, hg * Fx, mxl);
-        ns.jy = two_sum_round(myh, hg * Fy, myl);
-        ns.jz = two_sum_round(mzh, hg * Fz, mzl);
+        ns.jx = two_sum_round_lo(mxh, hg * Fx, mxl, jlx);
+        ns.jy = two_sum_round_lo(myh, hg * Fy, myl, jly);
+        ns.jz = two_sum_round_lo(mzh, hg * Fz, mzl, jlz);
     } else {
         ns.jx = mxh + hg * Fx;
         ns.jy = myh + hg * Fy;
@@ -986,7 +1121,17 @@ __device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19
     ns.ux = ns.jx * rho_inv;
     ns.uy = ns.jy * rho_inv;
     ns.uz = ns.jz * rho_inv;
-    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, Fx, Fy, Fz);
+    ns.ulx = ns.uly = ns.ulz = V(0.f);
+    if constexpr (PRECISE) {
+        // rho's low part: rho0 - rho is exact next to rho0, and so is its sum
+        // with the high part of drho (both on the 2^-28 grid, small)
+        const V rlo = vadd_rn(vadd_rn(vsub_rn(V(p.rho0), ns.rho), mm.H.drho), mm.L.drho);
+        // u_lo = (j - u_hi rho + j_lo - u_hi rho_lo) / rho
+        ns.ulx = (vfma(-ns.ux, ns.rho, ns.jx) + jlx - ns.ux * rlo) * rho_inv;
+        ns.uly = (vfma(-ns.uy, ns.rho, ns.jy) + jly - ns.uy * rlo) * rho_inv;
+        ns.ulz = (vfma(-ns.uz, ns.rho, ns.jz) + jlz - ns.uz * rlo) * rho_inv;
+    }
+    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, jlx, jly, jlz, Fx, Fy, Fz);
 }
 
 template <typename V>
@@ -1029,9 +1174,13 @@ __device__ __forceinline__ void block_partials(float (&acc)[7], double* partials
 template <class V>
 struct NodeIn {
     V FLx, FLy, FLz, Fx, Fy, Fz, us0, us1, us2;
+    V ul0, ul1, ul2;   // low parts of the snapshot (b.snap_lo)
 };
 
-template <bool MHD, int MODE>
+// FL_IN_F: the flow pass of a two-pass coupled update (coupled_induction_pass
+// wrote this step's Lorentz force into b.FL): the total force is the external
+// force plus b.FL, added as the one-pass update adds it.
+template <bool MHD, int MODE, bool FL_IN_F = false>
 __device__ __forceinline__ NodeIn<float> node_inputs(const StepParams& p, const StepBuffers& b, uint32_t n)
 {
     const size_t N = p.N;
@@ -1050,11 +1199,22 @@ __device__ __forceinline__ NodeIn<float> node_inputs(const StepParams& p, const 
         in.Fy += __ldg(b.Ffield + N + n);
         in.Fz += __ldg(b.Ffield + 2 * N + n);
     }
+    if constexpr (FL_IN_F) {
+        in.Fx += b.FL[n];
+        in.Fy += b.FL[N + n];
+        in.Fz += b.FL[2 * N + n];
+    }
     in.us0 = in.us1 = in.us2 = 0.f;
+    in.ul0 = in.ul1 = in.ul2 = 0.f;
     if (MODE == MODE_STEP_RESID && b.have_snap) {
         in.us0 = b.usnap[n];
         in.us1 = b.usnap[N + n];
         in.us2 = b.usnap[2 * N + n];
+        if (b.snap_lo) {
+            in.ul0 = b.usnap[3 * N + n];
+            in.ul1 = b.usnap[4 * N + n];
+            in.ul2 = b.usnap[5 * N + n];
+        }
     }
     return in;
 }
@@ -1079,10 +1239,16 @@ __device__ __forceinline__ NodeIn<F2> pair_inputs(const StepParams& p, const Ste
         in.Fz += F2(__ldg(reinterpret_cast<const float2*>(b.Ffield + 2 * N + n0)));
     }
     in.us0 = in.us1 = in.us2 = F2(0.f);
+    in.ul0 = in.ul1 = in.ul2 = F2(0.f);
     if (MODE == MODE_STEP_RESID && b.have_snap) {
         in.us0 = F2(*reinterpret_cast<const float2*>(b.usnap + n0));
         in.us1 = F2(*reinterpret_cast<const float2*>(b.usnap + N + n0));
         in.us2 = F2(*reinterpret_cast<const float2*>(b.usnap + 2 * N + n0));
+        if (b.snap_lo) {
+            in.ul0 = F2(*reinterpret_cast<const float2*>(b.usnap + 3 * N + n0));
+            in.ul1 = F2(*reinterpret_cast<const float2*>(b.usnap + 4 * N + n0));
+            in.ul2 = F2(*reinterpret_cast<const float2*>(b.usnap + 5 * N + n0));
+        }
     }
     return in;
 }
@@ -1114,7 +1280,7 @@ __device__ __forceinline__ void load_f_interior_dir(const StepParams& p, const S
 // of MODE_STEP_RESID into acc.  Returns without work for solid nodes.
 // DIR: the per-direction bases of b are filled (kernels launched by
 // launch_mode); they serve the interior gather and the stores of f.
-template <int ST, bool MHD, int MODE, bool CG = false, bool DIR = false>
+template <int ST, bool MHD, int MODE, bool CG = false, bool DIR = false, bool FL_IN_F = false>
 __device__ __forceinline__ void scalar_node_step(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                  uint32_t i, float (&acc)[7])
 {
@@ -1144,7 +1310,79 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
         load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
         if (MHD) load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
     }
-    node_from_sources<ST, MHD, MODE, DIR>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE>(p, b, n), acc);
+    node_from_sources<ST, MHD, MODE, DIR>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE, FL_IN_F>(p, b, n), acc);
+}
+
+// Two-pass coupled update, pass 1 (the persistent batch kernel: one update
+// of a coupled node does not fit its register budget).  Gathers f and g of
+// node i, forms rho and m (Eq. precondhydrofields), runs the induction part
+// exactly as node_update does (B, Lorentz force from the previous step's
+// half-force velocity, D3Q7 collision; Sec. 4) and writes g~ and this step's
+// Lorentz force into b.FL.  Pass 2 is scalar_node_step<ST, false, MODE, CG,
+// false, true>: it gathers f again (from L2) and runs the flow update with
+// F = F_ext + b.FL, which is the one-pass update's arithmetic in the same
+// order, so the result is bit for bit the same.
+template <int ST, bool CG>
+__device__ __forceinline__ void coupled_induction_pass(const StepParams& p, const StepBuffers& b, uint32_t i)
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    constexpr bool PRECISE = (ST == ST_F32 || ST == ST_F32C);
+    if (!(i < p.N)) return;
+    const uint32_t n = i;
+    const size_t N = p.N;
+    float d[19], dl[19], q[21], ql[21];
+    int wp = 0, wm = 0;
+    if (is_interior(p, n, wp, wm)) {
+        load_f_interior<ST, CG>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
+        load_g_interior<ST, CG>(p, static_cast<const T*>(b.gsrc), n, wp, wm, q, ql);
+    } else {
+        const Geo g = make_geo(p, n);
+        if (g.solid) return;
+        load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+        load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
+    }
+    const NodeIn<float> in = node_inputs<true, MODE_STEP>(p, b, n);
+    // rho and m as node_update forms them
+    NodeMoments<float, PRECISE> mm;
+    if constexpr (PRECISE) {
+        float dh[19], dlo[19];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            split_exact(d[a], dh[a], dlo[a]);
+            if constexpr (S::COMP) dlo[a] += dl[a];
+        }
+        mm.H = linear_moments(dh);
+        mm.L = linear_moments(dlo);
+    } else {
+        mm.H = linear_moments(d);
+    }
+    const float rho = p.rho0 + mm.drho();
+    const float rho_inv = vrcp(rho);
+    const float mx = PRECISE ? mm.H.mx + mm.L.mx : mm.H.mx;
+    const float my = PRECISE ? mm.H.my + mm.L.my : mm.H.my;
+    const float mz = PRECISE ? mm.H.mz + mm.L.mz : mm.H.mz;
+    float og[21];
+    NodeMacro<float> mac;
+    induction_collide<float, PRECISE, S::COMP>(p, q, ql, og, rho_inv, mx, my, mz, in.Fx, in.Fy, in.Fz, in.FLx,
+                                              in.FLy, in.FLz, mac);
+    T* __restrict__ gd = static_cast<T*>(b.gdst);
+    if constexpr (S::COMP) {
+        __half* __restrict__ gdl = reinterpret_cast<__half*>(gd + 21 * N);
+#pragma unroll
+        for (int a = 0; a < 21; ++a) {
+            float nh, nl;
+            comp_add(q[a], ql[a], og[a], nh, nl);
+            gd[(size_t)a * N + n] = nh;
+            gdl[(size_t)a * N + n] = S::cv_lo(nl);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv(toscale<ST>(p, q[a] + og[a]));
+    }
+    b.FL[n] = mac.FLx;
+    b.FL[N + n] = mac.FLy;
+    b.FL[2 * N + n] = mac.FLz;
 }
 
 // The update of fluid node n from its gathered pre-collision populations
@@ -1174,6 +1412,7 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     }
     // f~ = f + om, written to the node's own slot of the other buffer
     T* __restrict__ fd = static_cast<T*>(b.fdst);
+    [[maybe_unused]] SrBits rb(n, step_seed<ST>(b));
     if constexpr (S::COMP) {
         __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
 #pragma unroll
@@ -1185,10 +1424,11 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
         }
     } else if constexpr (DIR) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) static_cast<T*>(b.fdst_dir[a])[n] = S::cv(toscale<ST>(p, post_collision<ST>(d[a], om[a])));
+        for (int a = 0; a < 19; ++a)
+            static_cast<T*>(b.fdst_dir[a])[n] = store_cv<ST>(toscale<ST>(p, post_collision<ST>(d[a], om[a])), rb);
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = S::cv(toscale<ST>(p, post_collision<ST>(d[a], om[a])));
+        for (int a = 0; a < 19; ++a) fd[(size_t)a * N + n] = store_cv<ST>(toscale<ST>(p, post_collision<ST>(d[a], om[a])), rb);
     }
     if (MHD) {
         T* __restrict__ gd = static_cast<T*>(b.gdst);
@@ -1203,7 +1443,7 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = S::cv(toscale<ST>(p, q[a] + og[a]));
+            for (int a = 0; a < 21; ++a) gd[(size_t)a * N + n] = store_cv<ST>(toscale<ST>(p, q[a] + og[a]), rb);
         }
         b.FL[n] = ns.mac.FLx;
         b.FL[N + n] = ns.mac.FLy;
@@ -1211,7 +1451,11 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     }
     if (MODE == MODE_STEP_RESID) {
         if (b.have_snap) {
-            const float dx = ns.ux - in.us0, dy = ns.uy - in.us1, dz = ns.uz - in.us2;
+            // u_hi - us_hi is exact for nearby values; the low parts add what
+            // u_hi cannot resolve (0 without b.snap_lo)
+            const float dx = (ns.ux - in.us0) + (ns.ulx - in.ul0);
+            const float dy = (ns.uy - in.us1) + (ns.uly - in.ul1);
+            const float dz = (ns.uz - in.us2) + (ns.ulz - in.ul2);
             acc[0] += dx * dx + dy * dy + dz * dz;
         }
         acc[1] += ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz;
@@ -1223,6 +1467,11 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
         b.usnap[n] = ns.ux;
         b.usnap[N + n] = ns.uy;
         b.usnap[2 * N + n] = ns.uz;
+        if (b.snap_lo) {
+            b.usnap[3 * N + n] = ns.ulx;
+            b.usnap[4 * N + n] = ns.uly;
+            b.usnap[5 * N + n] = ns.ulz;
+        }
     }
 }
 
@@ -1241,7 +1490,8 @@ template <int ST, int NODES, bool MHD, bool RESID>
 __device__ __forceinline__ void prefetch_ahead(const StepParams& p, const StepBuffers& b)
 {
     using T = typename Store<ST>::T;
-    constexpr int NG = MHD ? 21 : 0, NL = MHD ? 3 : 0, NS = RESID ? 3 : 0;
+    constexpr int NG = MHD ? 21 : 0, NL = MHD ? 3 : 0;
+    const int NS = RESID ? (b.snap_lo ? 6 : 3) : 0;
     const int t = threadIdx.x;
     if (b.pf_ahead <= 0 || t >= 19 + NG + NL + 3 + NS) return;
     const long long N = p.N;
@@ -1287,6 +1537,7 @@ template <int ST, bool MHD, int MODE>
 __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers& b, const FieldOut& fo)
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
+    if constexpr (MODE != MODE_FIELDS) advance_seed<ST>(b);
     // with induction only for F32 storage: coupled F32 step 0.1241 against
     // 0.1382 ms (half a wave ahead: 0.1200 ms), coupled BF16 step 0.0845
     // against 0.0829 ms (half a wave ahead: 0.0841 ms)
@@ -1300,7 +1551,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers
     // vs 0.631 ms, F32 1.058 vs 0.898 ms and the BF16 residual step 0.914 vs
     // 0.842 ms; with induction they raise the register count past a block
     // per SM
-    scalar_node_step<ST, MHD, MODE, false, !MHD && ST == ST_BF16 && MODE == MODE_STEP>(p, b, fo, i, acc);
+    scalar_node_step<ST, MHD, MODE, false, !MHD && base_storage(ST) == ST_BF16 && MODE == MODE_STEP>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 
@@ -1324,7 +1575,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
 template <int ST>
 constexpr int step_dense_blocks()
 {
-    return (ST == ST_BF16 || ST == ST_F16) ? 5 : 0;   // 0: the free kernel
+    return (base_storage(ST) == ST_BF16 || base_storage(ST) == ST_F16) ? 5 : 0;   // 0: the free kernel
 }
 
 // The update of the fluid node pair (n0, n0 + 1) from its gathered
@@ -1344,6 +1595,7 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
     node_update<F2, ST, MHD>(p, d, dl, q, ql, in.FLx, in.FLy, in.FLz, in.Fx, in.Fy, in.Fz, true, om, og, ns);
 
     T* __restrict__ fd = static_cast<T*>(b.fdst);
+    [[maybe_unused]] SrBits rb(n0, step_seed<ST>(b));
     if constexpr (S::COMP) {
         __half* __restrict__ fdl = reinterpret_cast<__half*>(fd + 19 * N);
 #pragma unroll
@@ -1355,10 +1607,12 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
         }
     } else if constexpr (DIR) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) S::st2(static_cast<T*>(b.fdst_dir[a]) + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])));
+        for (int a = 0; a < 19; ++a)
+            store_pair<ST>(static_cast<T*>(b.fdst_dir[a]) + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])), rb);
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) S::st2(fd + (size_t)a * N + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])));
+        for (int a = 0; a < 19; ++a)
+            store_pair<ST>(fd + (size_t)a * N + n0, toscale<ST>(p, post_collision<ST>(d[a], om[a])), rb);
     }
     if (MHD) {
         T* __restrict__ gd = static_cast<T*>(b.gdst);
@@ -1373,7 +1627,7 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < 21; ++a) S::st2(gd + (size_t)a * N + n0, toscale<ST>(p, q[a] + og[a]));
+            for (int a = 0; a < 21; ++a) store_pair<ST>(gd + (size_t)a * N + n0, toscale<ST>(p, q[a] + og[a]), rb);
         }
         *reinterpret_cast<float2*>(b.FL + n0) = ns.mac.FLx.v;
         *reinterpret_cast<float2*>(b.FL + N + n0) = ns.mac.FLy.v;
@@ -1384,7 +1638,9 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
         float2* vs = reinterpret_cast<float2*>(b.usnap + N + n0);
         float2* ws = reinterpret_cast<float2*>(b.usnap + 2 * N + n0);
         if (b.have_snap) {
-            const F2 dx = ns.ux - in.us0, dy = ns.uy - in.us1, dz = ns.uz - in.us2;
+            const F2 dx = (ns.ux - in.us0) + (ns.ulx - in.ul0);
+            const F2 dy = (ns.uy - in.us1) + (ns.uly - in.ul1);
+            const F2 dz = (ns.uz - in.us2) + (ns.ulz - in.ul2);
             acc[0] += lane_sum(dx * dx + dy * dy + dz * dz);
         }
         acc[1] += lane_sum(ns.ux * ns.ux + ns.uy * ns.uy + ns.uz * ns.uz);
@@ -1396,6 +1652,11 @@ __device__ __forceinline__ void pair_from_sources(const StepParams& p, const Ste
         *us = ns.ux.v;
         *vs = ns.uy.v;
         *ws = ns.uz.v;
+        if (b.snap_lo) {
+            *reinterpret_cast<float2*>(b.usnap + 3 * N + n0) = ns.ulx.v;
+            *reinterpret_cast<float2*>(b.usnap + 4 * N + n0) = ns.uly.v;
+            *reinterpret_cast<float2*>(b.usnap + 5 * N + n0) = ns.ulz.v;
+        }
     }
 }
 
@@ -1449,6 +1710,7 @@ __device__ __forceinline__ void pair_step_body(const StepParams& p, const StepBu
     using S = Store<ST>;
     using T = typename S::T;
     if (b.stop != nullptr && *b.stop) return;
+    advance_seed<ST>(b);
     if constexpr (!MHD && !S::COMP) prefetch_ahead<ST, 2 * PAIR_THREADS, false, MODE == MODE_STEP_RESID>(p, b);
     const uint32_t npairs = p.N >> 1;
     const uint32_t i = blockIdx.x * PAIR_THREADS + threadIdx.x;
@@ -1502,8 +1764,8 @@ __global__ void __launch_bounds__(PAIR_THREADS, MINB) step_pair_kernel_dense(con
 template <int ST, int MODE>
 constexpr int pair_dense_blocks()
 {
-    if (ST == ST_F16) return MODE == MODE_STEP ? 8 : 7;
-    return ST == ST_BF16 ? 7 : 0;   // 0: the free kernel
+    if (base_storage(ST) == ST_F16) return MODE == MODE_STEP ? 8 : 7;
+    return base_storage(ST) == ST_BF16 ? 7 : 0;   // 0: the free kernel
 }
 
 // The paired kernel serves x-periodic grids with an even nx: when asked for
@@ -1519,7 +1781,7 @@ inline bool pair_eligible(const StepParams& p, bool mhd, int mode)
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0] || mode == MODE_FIELDS) return false;
     if (p.variant == 2) return true;
     if (p.variant != 0 || mhd) return false;
-    return p.storage == ST_F16 || p.storage == ST_BF16;
+    return base_storage(p.storage) == ST_F16 || base_storage(p.storage) == ST_BF16;
 }
 
 // ---------------------------------------------------------------------------
@@ -1658,7 +1920,7 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
 {
     StepBuffers b = with_dir_bases<ST>(p, b_in);
     b.pf_ahead = 0;
-    if constexpr (ST != ST_F32C && MODE != MODE_FIELDS) {
+    if constexpr (ST != ST_F32C && !Store<ST>::SR && MODE != MODE_FIELDS) {
         if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
         if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);
     }

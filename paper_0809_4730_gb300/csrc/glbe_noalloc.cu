@@ -16,8 +16,14 @@
 // array's name as a device address (on the host it names a host-side stand-in;
 // a kernel given it would fault or, where the GPU can reach host memory,
 // silently use the wrong memory), so the address is looked up once per device
-// with cudaGetSymbolAddress while that device is current.  Nothing here calls
-// cudaMalloc, cudaFree or any allocating library routine.
+// with cudaGetSymbolAddress while that device is current.  The lookup is keyed
+// on the device's current driver context as well: after cudaDeviceReset (or a
+// primary context that was released and created again) the module is loaded
+// anew and the array may sit elsewhere, so a new context triggers a new
+// lookup.  Nothing here calls cudaMalloc, cudaFree or any allocating library
+// routine.
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -40,22 +46,49 @@ static __device__ __align__(256) double g_scratch[SCRATCH_DOUBLES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double* g_scratch_addr[MAX_DEVICES] = {};
+CUcontext g_scratch_ctx[MAX_DEVICES] = {};   // driver context the address belongs to
 
-// Device address of g_scratch on the current device (looked up on the first
-// call per device).
+// cuCtxGetCurrent through the runtime's driver entry point (the library links
+// the static CUDA runtime only, not libcuda directly).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    return fn;
+}
+
+// Device address of g_scratch on the current device: looked up on the first
+// call per device, and again whenever the device's current driver context is
+// not the one the cached address was taken in.
 glbe_status scratch_address(double** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES) return fail(GLBE_ERR_ARG, "device ordinal %d out of range", dev);
+    // make the device's primary context current on this thread (a no-op when
+    // it already is)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get || get(&ctx) != CUDA_SUCCESS || !ctx)
+        return fail(GLBE_ERR_CUDA, "cuCtxGetCurrent is unavailable: cannot key the static scratch on its context");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess || !ptr)
             return fail(GLBE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
         g_scratch_addr[dev] = static_cast<double*>(ptr);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return GLBE_OK;
@@ -114,6 +147,8 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
     b.partials = partials;
     b.have_snap = have_prev ? 1 : 0;
     b.stop = nullptr;
+    b.sr_ctr = nullptr;              // stochastic rounding (the _SR forms) seeded by the time level
+    b.sr_seed = (unsigned)t;
     const FieldOut fo{nullptr, nullptr, nullptr};
 
     unsigned grid = 0;   // blocks of the step launch (at most NOALLOC_MAX_BLOCKS for N within the limit)
@@ -124,6 +159,8 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
         case GLBE_F32: e = launch_step_t<ST_F32>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         case GLBE_BF16: e = launch_step_t<ST_BF16>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         case GLBE_F16: e = launch_step_t<ST_F16>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
+        case GLBE_BF16_SR: e = launch_step_t<ST_BF16_SR>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
+        case GLBE_F16_SR: e = launch_step_t<ST_F16_SR>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         default: e = launch_step_t<ST_F32C>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         }
     }
@@ -133,15 +170,28 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
         e = launch_finalize(partials, grid, p->rho0 * (double)fluid, t_dev, record, hist, hist_count, 1, stop, tol,
                             stream);
     if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "allocation-free step: %s", cudaGetErrorString(e));
+    // the record is read on the caller's stream (no device-wide synchronisation)
+    double rec[RECORD_STRIDE];
+    if (have_prev) {
+        e = cudaMemcpyAsync(rec, record, sizeof rec, cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "allocation-free record read: %s", cudaGetErrorString(e));
+    }
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "allocation-free step sync: %s", cudaGetErrorString(e));
+    // the TMA-staged tile kernel (variants 3 and 4) returns early when one of
+    // its bounded pipeline waits runs out; its outputs are then incomplete
+    int waited_out = 0;
+    if (p->variant >= 3) switch (p->storage) {
+    case GLBE_F32: waited_out = tile_wait_error_t<ST_F32>(); break;
+    case GLBE_BF16: waited_out = tile_wait_error_t<ST_BF16>(); break;
+    case GLBE_F16: waited_out = tile_wait_error_t<ST_F16>(); break;
+    default: break;
+    }
+    if (waited_out) return fail(GLBE_ERR_TIMEOUT, "a pipeline wait of the TMA-staged step kernel ran out");
 
     std::memset(out, 0, sizeof *out);
     out->t = -1;
     if (!have_prev) return GLBE_OK;
-    double rec[RECORD_STRIDE];
-    e = cudaMemcpy(rec, record, sizeof rec, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(GLBE_ERR_CUDA, "allocation-free record read: %s", cudaGetErrorString(e));
     out->t = (long)rec[0];
     out->r = rec[1];
     out->num = rec[2];

@@ -17,8 +17,9 @@ import threading
 from . import build as _build
 
 GLBE_OK, GLBE_ERR_ARG, GLBE_ERR_CUDA, GLBE_ERR_DIVERGED, GLBE_ERR_TIMEOUT, GLBE_ERR_STATE = range(6)
-GLBE_F32, GLBE_BF16, GLBE_F16, GLBE_F32C = 0, 1, 2, 3
-STORAGE = {"f32": GLBE_F32, "bf16": GLBE_BF16, "f16": GLBE_F16, "f32c": GLBE_F32C}
+GLBE_F32, GLBE_BF16, GLBE_F16, GLBE_F32C, GLBE_BF16_SR, GLBE_F16_SR = 0, 1, 2, 3, 4, 5
+STORAGE = {"f32": GLBE_F32, "bf16": GLBE_BF16, "f16": GLBE_F16, "f32c": GLBE_F32C, "bf16sr": GLBE_BF16_SR,
+           "f16sr": GLBE_F16_SR}
 
 
 class GlbeError(RuntimeError):
@@ -120,7 +121,7 @@ def load(build_if_missing: bool = True):
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            if lib.glbe_abi_version() != 3:
+            if lib.glbe_abi_version() != 4:
                 raise RuntimeError("libglbe ABI version mismatch")
             ps, isz = C.c_size_t(0), C.c_size_t(0)
             lib.glbe_struct_sizes(C.byref(ps), C.byref(isz))

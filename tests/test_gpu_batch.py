@@ -132,3 +132,76 @@ def test_batch_reports_the_unstable_domain_and_finishes_the_others():
     assert res[3]["nonfinite"] and not res[3]["converged"]
     assert all(r["converged"] and not r["nonfinite"] for r in res[:3])
     B.close()
+
+
+# ---------------------------------------------------------------------------
+# The batch against the FP64 oracle itself.
+# ---------------------------------------------------------------------------
+def _oracle_cfg(orc, nx, ny, nz, kw):
+    c = dict(wall_lo=kw["wall_lo"], wall_hi=kw["wall_hi"], gamma=kw["gamma"], nu=kw["nu"], F=kw["F"])
+    if kw.get("induction"):
+        c.update(induction=True, gamma_m=kw["gamma_m"], eta=kw["eta"], chi=kw["chi"], mu=kw["mu"], B0=kw["B0"])
+    return orc.Config(nx, ny, nz, **c)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f32c"])
+def test_batch_domains_match_oracle_after_23_levels(orc, storage):
+    """Every domain (flow and coupled, gamma 1 to 0.1, odd and even sizes) is
+    marched 23 levels from rest in one launch and compared node by node with
+    the oracle's march of the same domain: the per-step parity bar of the
+    single-context tests (3e-5 of the largest value)."""
+    B = _batch(storage)
+    st, res, _ = B.solve(1e-300, 23, use_graph=True)    # no domain leaves early
+    from paper_0809_4730_gb300.glbe import GLBE_ERR_TIMEOUT
+    assert st == GLBE_ERR_TIMEOUT and not any(r["converged"] for r in res)
+    for d, (nx, ny, nz, kw) in enumerate(_params(storage)):
+        S = orc.Solver(_oracle_cfg(orc, nx, ny, nz, kw))
+        S.run(23)
+        orho, ou, oB, _ = S.fields()
+        fluid = ~S.solid_mask()
+        rho, u, Bf = B.fields(d)
+        torch_sync()
+        u = u.double().cpu().numpy()[:, fluid]
+        want = ou.T[:, fluid]
+        assert np.abs(u - want).max() <= 3e-5 * np.abs(want).max(), d
+        drho = rho.double().cpu().numpy()[fluid] - kw.get("rho0", 1.0)
+        odr = orho[fluid] - 1.0
+        assert np.abs(drho - odr).max() <= 3e-5 * np.abs(odr).max() + 2 ** -24, d
+        if Bf is not None:
+            b = Bf.double().cpu().numpy()[:, fluid] - np.asarray(kw["B0"])[:, None]
+            ob = oB.T[:, fluid] - np.asarray(kw["B0"])[:, None]
+            assert np.abs(b - ob).max() <= 3e-5 * np.abs(ob).max() + 2 ** -24 * np.abs(kw["B0"]).max(), d
+    B.close()
+
+
+def test_batch_steady_state_matches_converged_oracle(orc):
+    """The batch solved to r <= 1e-8 (compensated storage) against the FP64
+    oracle converged to 1e-11.  The ducts are x-periodic with walls in y and
+    z and a uniform force, so their steady state is x-invariant and the
+    oracle solves the 1 x ny x nz column.  Bar: the FP32 steady bar, velocity
+    L-infinity relative error 1e-5."""
+    B = _batch("f32c")
+    st, res, _ = B.solve(1e-8, 400_000, use_graph=True)
+    assert st == 0, res
+    for d, (nx, ny, nz, kw) in enumerate(_params("f32c")):
+        S = orc.Solver(_oracle_cfg(orc, 1, ny, nz, kw))
+        S.run(3_000_000, tol=1e-11)
+        _, ou, oB, _ = S.fields()
+        col = ou[:, 0].reshape(nz, ny)
+        _, u, Bf = B.fields(d)
+        torch_sync()
+        ux = u[0].double().cpu().numpy().reshape(nz, ny, nx)
+        fl = (slice(1, nz - 1), slice(1, ny - 1))
+        err = np.abs(ux[fl[0], fl[1], :] - col[fl][:, :, None]).max() / np.abs(col[fl]).max()
+        assert err <= 1e-5, (d, err, res[d])
+        if Bf is not None:
+            bcol = oB[:, 0].reshape(nz, ny)
+            bx = Bf[0].double().cpu().numpy().reshape(nz, ny, nx)
+            eb = np.abs(bx[fl[0], fl[1], :] - bcol[fl][:, :, None]).max() / np.abs(bcol[fl]).max()
+            assert eb <= 1e-4, (d, eb)
+    B.close()
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()

@@ -30,7 +30,8 @@ def _state(G):
     return [None if a is None else a.cpu().numpy() for a in G.get_state()]
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16", "f16", "f32c"])
+# the stochastically rounded forms resume with the rounding seed of the saved level
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16", "f32c", "bf16sr", "f16sr"])
 @pytest.mark.parametrize("mhd", [False, True])
 def test_resume_is_bit_exact(storage, mhd):
     A = _solver(storage, mhd)

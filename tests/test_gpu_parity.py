@@ -38,6 +38,25 @@ def _perturb(S, seed, scale=2e-3):
         S.FL[:] = perturbation(3, cfg.nx, cfg.ny, cfg.nz, 1e-6, seed + 2).reshape(3, -1).T
 
 
+def _check_record_sums(info, row, S, fluid, tol):
+    """The GPU record's mass and momentum against the oracle record of the
+    same level.  Both are compared through their deviations: sum drho =
+    mass - rho0 N_fluid, which the scheme conserves, and sum j.  The bound is
+    tol times (fluid nodes x the largest population deviation, resp. the
+    largest |j|): far below rho0 N_fluid, so a dropped, doubled or
+    solid-node term is seen."""
+    cfg = S.cfg
+    nf = int(fluid.sum())
+    odf, _, _ = oracle_state_dev(S)
+    D = np.abs(odf[:, fluid]).max()
+    rho, u, _, _ = S.fields()
+    jmax = np.abs(rho[fluid, None] * u[fluid]).max()
+    m0 = cfg.rho0 * nf
+    assert abs((info.mass - m0) - (row["mass"] - m0)) <= tol * nf * D, (info.mass - m0, row["mass"] - m0)
+    assert np.abs(np.array(info.momentum[:]) - row["mom"]).max() <= tol * nf * jmax, \
+        (info.momentum[:], row["mom"])
+
+
 @pytest.mark.parametrize("mhd", [False, True])
 def test_state_roundtrip_is_exact(orc, mhd):
     cfg = _cfg(orc, mhd)
@@ -87,10 +106,12 @@ def test_step_parity_f32(orc, mhd, gamma, storage):
     h = {row["t"]: row for row in S.hist}
     assert info.t == 20
     assert abs(info.r - h[20]["r"]) <= 1e-3 * h[20]["r"]
-    assert abs(info.mass - h[20]["mass"]) <= 1e-6 * h[20]["mass"]
+    _check_record_sums(info, h[20], S, fluid, 3e-5)
 
 
-@pytest.mark.parametrize("storage,tol", [("bf16", 3e-2), ("f16", 4e-3)])
+# A stochastically rounded value is off by less than one unit in the last
+# place (round-to-nearest: half a unit), zero on average: twice the bound.
+@pytest.mark.parametrize("storage,tol", [("bf16", 3e-2), ("f16", 4e-3), ("bf16sr", 6e-2), ("f16sr", 8e-3)])
 def test_step_parity_reduced_storage(orc, storage, tol):
     from paper_0809_4730_gb300.inputs import random_force
     cfg = _cfg(orc, True, gamma=0.5)
@@ -102,7 +123,7 @@ def test_step_parity_reduced_storage(orc, storage, tol):
     df0, dg0, FL0 = gpu_state(G)
     fluid = ~S.solid_mask()
     odf, odg, _ = oracle_state_dev(S)
-    assert rel_linf(df0, odf, fluid) < (8e-3 if storage == "bf16" else 1e-3)
+    assert rel_linf(df0, odf, fluid) < (8e-3 if storage.startswith("bf16") else 1e-3)
     S.f[fluid] = (df0[:, fluid].T + W19[None, :] * cfg.rho0)
     B0 = np.asarray(cfg.B0)
     S.g[fluid] = dg0[:, fluid].T.reshape(-1, 3, 7) + W7[None, None, :] * B0[None, :, None]
@@ -143,7 +164,8 @@ def test_nonfinite_state_is_reported_as_divergence(orc):
 # wholly on interior rows at fixed offsets (every nx here but 2 and 6 has such
 # warps), the rest through the row geometry.
 @pytest.mark.parametrize("nx", [2, 6, 38, 64, 66])
-@pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2), ("f32c", 3e-5)])
+@pytest.mark.parametrize("storage,tol", [("f32", 3e-5), ("bf16", 3e-2), ("f32c", 3e-5), ("bf16sr", 6e-2),
+                                         ("f16sr", 8e-3)])
 @pytest.mark.parametrize("mhd", [False, True])
 def test_step_parity_paired_kernel(orc, nx, storage, tol, mhd):
     from paper_0809_4730_gb300.inputs import random_force
@@ -174,7 +196,7 @@ def test_step_parity_paired_kernel(orc, nx, storage, tol, mhd):
     h = {row["t"]: row for row in S.hist}
     assert info.t == 10
     assert abs(info.r - h[10]["r"]) <= max(1e-3, 30 * tol) * h[10]["r"]
-    assert abs(info.mass - h[10]["mass"]) <= 1e-6 * h[10]["mass"]
+    _check_record_sums(info, h[10], S, fluid, max(tol, 3e-5))
 
 
 # The TMA-staged tile kernel (variant 3): x periodic, nx a multiple of 128.
@@ -361,14 +383,13 @@ def _hartmann_oracle(orc, Ha, gamma, nu=0.01, eta=0.01, chi=0.01):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f32c"])
-@pytest.mark.parametrize("Ha", [5, 20])
-def test_steady_hartmann_parity(orc, Ha, storage):
+@pytest.mark.parametrize("Ha,gamma", [(5, 0.1), (10, 0.1), (20, 0.1), (10, 1.0)])
+def test_steady_hartmann_parity(orc, Ha, gamma, storage):
     from paper_0809_4730_gb300.glbe import Solver
     nu = eta = 0.01
     chi = 0.01
     L = 31.0
     B0 = Ha * np.sqrt(nu * eta) / L
-    gamma = 0.1
     cfg = orc.Config(1, 64, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
                      induction=True, gamma_m=gamma, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0))
     S = orc.Solver(cfg)
@@ -384,13 +405,15 @@ def test_steady_hartmann_parity(orc, Ha, storage):
     eu = np.abs(ux[fl] - ou[fl, 0][:, None]).max() / np.abs(ou[fl, 0]).max()
     eb = np.abs(bx[fl] - oB[fl, 0][:, None]).max() / np.abs(oB[fl, 0]).max()
     # F32C meets the FP32 bar of 1e-5; plain FP32 storage keeps the
-    # stagnation error of its slowest mode, measured near 1e-5 (bound 3e-5)
-    bar = 1e-5 if storage == "f32c" else 3e-5
+    # stagnation error of its slowest mode: measured 1-2e-5 at gamma = 0.1
+    # (bound 3e-5) and 6.3e-5 at Ha = 10, gamma = 1 (bound 1e-4)
+    bar = 1e-5 if storage == "f32c" else (1e-4 if gamma == 1.0 else 3e-5)
     assert eu <= bar, f"u error {eu:.3e} (GPU r = {r:.2e}, {steps} steps)"
     assert eb <= 1e-4, f"b error {eb:.3e}"
 
 
-@pytest.mark.parametrize("storage,bound", [("f32c", 1e-5), ("f32", 3e-5), ("f16", 5e-2), ("bf16", 5e-1)])
+@pytest.mark.parametrize("storage,bound", [("f32c", 1e-5), ("f32", 3e-5), ("f16", 5e-2), ("bf16", 5e-1),
+                                           ("f16sr", 5e-2), ("bf16sr", 5e-1)])
 def test_steady_accuracy_per_storage(orc, storage, bound):
     """Steady Hartmann (Ha = 10, gamma = 0.1) after a fixed 40000 steps: the
     error of each storage form against the converged FP64 oracle.  The
@@ -411,6 +434,72 @@ def test_steady_accuracy_per_storage(orc, storage, bound):
     err = np.abs(ux[fl] - ou[fl, 0][:, None]).max() / np.abs(ou[fl, 0]).max()
     print(f"steady accuracy {storage}: rel L-inf error {err:.3e}, residual r({info.t}) = {info.r:.3e}")
     assert err <= bound
+
+
+# ---------------------------------------------------------------------------
+# The 64^3 copy of the square duct (walls y, z; x periodic; F_x(y, z) of the
+# duct workload, F0 = 1e-6, nu = 0.5).  Its steady state is x-invariant, so
+# the oracle solves the 1 x 64 x 64 column, the same discrete problem, to
+# r <= 1e-11.
+# ---------------------------------------------------------------------------
+def _duct64_oracle(orc, gamma, n=64):
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    F = duct_force_x(1, n, n)[0].reshape(-1)
+    Fext = np.zeros((n * n, 3))
+    Fext[:, 0] = F
+    S = orc.Solver(orc.Config(1, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=0.5), Fext=Fext)
+    S.run(2_000_000, tol=1e-11)
+    _, ou, _, _ = S.fields()
+    return S, ou[:, 0].reshape(n, n)
+
+
+def _duct64_gpu(storage, gamma, n=64):
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    torch = require_cuda()
+    G = Solver(n, n, n, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=0.5, force_field=1, storage=storage)
+    G.set_force(torch.tensor(duct_force_x(n, n, n)[0].reshape(1, -1), dtype=torch.float32, device="cuda"))
+    return G
+
+
+def _duct64_error(G, col, n=64):
+    _, u, _ = gpu_fields(G)
+    ux = u[0].reshape(n, n, n)[1:-1, 1:-1, :]
+    c = col[1:-1, 1:-1]
+    return np.abs(ux - c[:, :, None]).max() / np.abs(c).max()
+
+
+# Bounds about twice the errors measured on a GB300 after 6000-12000 steps
+# (F32C 1.5e-7, F32 1.6e-7, F16 2.9e-4, BF16 1.8e-3, F16_SR 5-7e-4, BF16_SR
+# 4.4-4.9e-3).  The 16-bit forms leave the error of their stored precision:
+# round-to-nearest stagnates (error ~ ulp / decay rate), stochastic rounding
+# leaves zero-mean noise of about one ulp.
+@pytest.mark.parametrize("storage,bound", [("f32c", 1e-6), ("f32", 1e-6), ("f16", 1e-3), ("bf16", 5e-3),
+                                           ("f16sr", 2e-3), ("bf16sr", 1.2e-2)])
+def test_duct64_steady_accuracy_per_storage(orc, storage, bound):
+    _, col = _duct64_oracle(orc, 0.1)
+    G = _duct64_gpu(storage, 0.1)
+    G.step(6000)
+    err = _duct64_error(G, col)
+    info = G.residual()
+    print(f"64^3 duct steady error {storage}: {err:.3e}, r({info.t}) = {info.r:.3e}")
+    assert err <= bound
+    G.close()
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+def test_duct64_compensated_march_reaches_1e8(orc, gamma):
+    """The compensated form solves the 64^3 duct to r <= 1e-8 (the residual
+    keeps u as a double-float pair, so FP32 rounding of u does not floor it)
+    within 25 % of the oracle's step count, at the FP32 bar of 1e-5."""
+    S, col = _duct64_oracle(orc, gamma)
+    t8 = min(h["t"] for h in S.hist if h["r"] <= 1e-8)
+    G = _duct64_gpu("f32c", gamma)
+    st, steps, r = G.solve(1e-8, 200_000)
+    assert st == 0 and r <= 1e-8, (st, steps, r)
+    assert abs(steps - t8) <= 0.25 * t8, (steps, t8)
+    assert _duct64_error(G, col) <= 1e-5
+    G.close()
 
 
 # ---------------------------------------------------------------------------

@@ -253,6 +253,71 @@ def test_mass_conservation(orc):
 
 
 # ---------------------------------------------------------------------------
+# The FP64 sums of the residual record (Sec. 5 residual bookkeeping): the mass
+# column is the sum of every fluid population at that level (a definition;
+# with walls, a force field and induction it also stays at its initial value,
+# the scheme conserving mass), and the momentum column is sum rho u.
+# ---------------------------------------------------------------------------
+def test_history_mass_is_fluid_population_sum(orc):
+    nx, ny, nz = 5, 9, 6
+    rng = np.random.default_rng(21)
+    F = rng.uniform(-1e-5, 1e-5, size=(nz * ny * nx, 3))
+    cfg = orc.Config(nx, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 0), gamma=0.3, nu=0.03,
+                     induction=True, gamma_m=0.3, eta=0.02, chi=0.2, B0=(0.01, 0.02, 0.0))
+    S = orc.Solver(cfg, Fext=F)
+    S.f += rng.uniform(-2e-3, 2e-3, size=S.f.shape) * W
+    fluid = ~S.solid_mask()
+    m0 = S.f[fluid].sum()
+    sums = {}
+    for t in (10, 20, 30):
+        S.run(t - S.t)
+        sums[t] = S.f[fluid].sum()          # every population of every fluid node at level t
+    S.run(1)                                # the record of level 30 is taken when level 30 is collided
+    h = {row["t"]: row for row in S.hist}
+    for t in (20, 30):
+        assert abs(h[t]["mass"] - sums[t]) <= 1e-13 * sums[t]
+        assert abs(h[t]["mass"] - m0) <= 1e-13 * m0
+    # a solid node's populations never enter the sum
+    assert abs(S.f[~fluid].sum()) > 1e-3
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+def test_history_momentum_of_uniform_forcing(orc, gamma):
+    """P8 through the record: in a fully periodic box under a uniform force
+    from rest, sum rho u over the N nodes is N (t + 1/2) F / gamma exactly."""
+    F = np.array([2e-6, -1e-6, 5e-7])
+    nx, ny, nz = 4, 3, 5
+    N = nx * ny * nz
+    S = orc.Solver(orc.Config(nx, ny, nz, gamma=gamma, nu=0.05, F=tuple(F)))
+    S.run(41)
+    h = {row["t"]: row for row in S.hist}
+    for t in (20, 30, 40):
+        want = N * (t + 0.5) * F / gamma
+        assert np.abs(h[t]["mom"] - want).max() <= 1e-12 * np.abs(want).max()
+        assert abs(h[t]["mass"] - N * 1.0) <= 1e-13 * N
+
+
+def test_history_momentum_is_sum_of_j(orc):
+    """With walls and a force field the momentum column is the sum over fluid
+    nodes of j = sum_a f_a e_a + F/(2 gamma) (Eq. precondhydrofields),
+    recomputed here from the populations."""
+    nx, ny, nz = 6, 7, 5
+    rng = np.random.default_rng(5)
+    Fx = rng.uniform(-1e-5, 1e-5, size=(nz * ny * nx, 3))
+    gamma = 0.25
+    Fu = np.array([1e-6, 0.0, -2e-6])
+    S = orc.Solver(orc.Config(nx, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=0.02,
+                              F=tuple(Fu)), Fext=Fx)
+    S.f += rng.uniform(-1e-3, 1e-3, size=S.f.shape) * W
+    fluid = ~S.solid_mask()
+    S.run(20)
+    j = S.f[fluid] @ E + (Fx[fluid] + Fu) / (2 * gamma)
+    S.run(1)
+    h = {row["t"]: row for row in S.hist}
+    assert np.abs(h[20]["mom"] - j.sum(axis=0)).max() <= 1e-12 * np.abs(j).sum()
+
+
+# ---------------------------------------------------------------------------
 # P8: fully periodic box, uniform force, rest start.  From S*_3 = F/gamma and
 # the half-force shift, j(t) = (t + 1/2) F / gamma exactly, state uniform.
 # ---------------------------------------------------------------------------
