@@ -18,9 +18,12 @@ variants: FP32 / FP16 storage on the same duct, the fused D3Q19 + D3Q7 step
 on the 128^3 Hartmann duct, and wall time to a 1e-8 residual at gamma = 0.1
 vs gamma = 1 on the 64 x 64 x 8 Hartmann duct.
 
-Multi-GPU: replicas only (each rank runs the same workload on its own GPU;
-no data-path collective); the value aggregates all ranks, timing is the max
-over ranks.
+Multi-GPU (torchrun, N > 1): the duct is split into N slabs of z planes, one
+per rank (strong scaling: the whole job is one duct); after every time step
+each rank sends the populations crossing its slab faces to its neighbours
+(NCCL point-to-point) and every 10 steps the FP64 residual sums are
+all-reduced.  Timing is the max over ranks.  ``--replicas`` runs N
+independent copies instead (weak scaling).
 """
 from __future__ import annotations
 
@@ -88,10 +91,11 @@ def parse():
     ap.add_argument("--no-adjoint-fd", action="store_true")
     ap.add_argument("--batch-storage", choices=["f32", "f32c"], default="f32c",
                     help="f32c by default: with F32 storage these ducts stall near r = 3e-8 (measured)")
-    ap.add_argument("--batch-max-steps", type=int, default=50_000)
-    ap.add_argument("--batch-tol", type=float, default=3e-8,
-                    help="3e-8 by default: these ducts (nu = 0.1, |u| ~ 1e-3) settle at r = 1.2-3.6e-8 in FP32 "
-                         "arithmetic (measured with F32 and F32C storage), below which 1e-8 is not reached")
+    ap.add_argument("--batch-max-steps", type=int, default=400_000,
+                    help="level cap: the gamma = 1 ducts of up to 160 nodes need ~2e5 levels at nu = 0.1")
+    ap.add_argument("--batch-tol", type=float, default=1e-8)
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1: N independent replicas of the duct instead of one duct split into N slabs")
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -369,6 +373,60 @@ def run_glbe(args, rank, ws):
         if refs is not None:
             line["steady_error"], line["time_to_solution"] = duct64_study(refs)
     return line
+
+
+def run_sharded(args, rank, ws):
+    """One 512 x 256 x 256 duct split along z into ws slabs, slab `rank` on
+    this GPU; every time step is the fused step plus the exchange of the
+    crossing populations with the neighbouring ranks."""
+    import torch
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    from paper_0809_4730_gb300.slabs import RankSlab, SolverSlab, global_planes, plan, slab_params
+    stream = torch.cuda.current_stream()
+    d = DUCT
+    slabs = plan(d["nz"], ws, 1, 1)
+    s = slabs[rank]
+    kw = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=d["gamma"], nu=d["nu"], force_field=1,
+              storage=args.storage, variant=args.variant)
+    G = Solver(d["nx"], d["ny"], s.nz_local, **slab_params(kw, s))
+    Fx = duct_force_x(d["nx"], d["ny"], d["nz"], d["F0"])[0]
+    zs = global_planes(s, d["nz"])
+    G.set_force(torch.tensor(Fx[zs].reshape(1, -1), dtype=torch.float32, device="cuda"))
+    R = RankSlab(slabs, rank, SolverSlab(G))
+    fluid_total = d["nx"] * (d["ny"] - 2) * (d["nz"] - 2)
+    R.step(10 * args.warmup)
+    R.residual()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            R.step(10)
+        e1.record(stream)
+        e1.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    info = R.residual()
+    updates = 10 * args.steps * fluid_total
+    G.close()
+    return {
+        "metric": "MLUPS (fluid-node updates/s) and % of HBM roofline of the fused GLBE step",
+        "value": round(updates / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"square duct {d['nx']}x{d['ny']}x{d['nz']} split into {ws} z slabs, "
+                               f"{args.storage} deviation storage; 1 bench step = 10 time steps, each followed by "
+                               "the halo exchange (NCCL send/recv), FP64 all-reduce of the residual sums",
+                   "fluid_nodes": fluid_total, "storage": args.storage, "parallelism": f"z slabs x{ws}",
+                   "l2": "inputs larger than L2 (no flush)"},
+        # per time step: the fused step, a pack and an unpack per ghost face;
+        # per bench step the residual finalize (one or two kernels)
+        "gpu_launches": args.steps * (10 * (1 + 2 * (s.ghost_lo + s.ghost_hi)) + 2),
+        "residual_at_end": {"t": info.t, "r": info.r},
+        "clocks": clk.summary(),
+    }
 
 
 def variants(args, hbm_peak, stream):
@@ -860,6 +918,8 @@ def main():
         line = run_batch(args, rank, ws)
     elif args.workload == "adjoint":
         line = run_adjoint(args, rank, ws)
+    elif ws > 1 and not args.replicas:
+        line = run_sharded(args, rank, ws)
     else:
         line = run_glbe(args, rank, ws)
     if rank == 0:

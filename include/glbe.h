@@ -120,6 +120,11 @@ typedef struct {
                                  copies (needs no walls along x, nx a multiple of 128, F32, BF16 or
                                  F16 storage, not the _SR forms; else the one-node form is used); 4 = the same tiles with
                                  two x-adjacent nodes per thread in packed FP32x2 arithmetic */
+    int ghost_lo, ghost_hi;   /* slab decomposition along z.  1: the plane z = 0 (resp. z = nz-1) is a ghost
+                                 plane holding what the neighbouring slab streams across the face
+                                 (glbe_halo_unpack): it is never collided, is outside every sum and
+                                 output (like a solid plane), and a gather reads it as fluid.  Not
+                                 together with a wall on the same side.  0 (default): no ghost plane */
 } glbe_params;
 
 /* Latest residual evaluation (time level t, a multiple of 10). */
@@ -376,6 +381,45 @@ glbe_status glbe_adjoint_steady(glbe_ctx* ctx, const float* d_w, double tol, lon
  * on the final state.  Enqueued asynchronously on the stream. */
 glbe_status glbe_adjoint_unrolled(glbe_ctx* ctx, const float* d_w, long nsteps, long K, void* d_work, size_t bytes,
                                   float* d_dQdF);
+
+/* ------------------------------------------------------------------------ */
+/* Slab decomposition along z (the update is local except nearest-neighbour  */
+/* streaming, Eqs. pstreaming and mstreaming): a grid is split into slabs of */
+/* z planes, each a context with ghost planes (glbe_params.ghost_lo/hi).     */
+/* After every step, the populations that cross a face -- the 5 D3Q19       */
+/* directions with e_z = +-1 and, with induction, the D3Q7 direction e_z =   */
+/* +-1 of each of the 3 components -- go from the slab's outermost computed  */
+/* plane into the neighbour's ghost plane: glbe_halo_pack on one side, a     */
+/* copy of the packed buffer (same device, a peer device or another process  */
+/* by a collective library), glbe_halo_unpack on the other.  The lagged      */
+/* Lorentz force is local.  A march of slabs is then bit for bit the march  */
+/* of the whole grid.                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of one packed face: (5 + 3 with induction) rows of nx*ny values in
+ * the storage type; the compensated form appends the FP16 low parts of the
+ * same rows.  Layout: f rows, g rows, then (F32C) f low rows, g low rows;
+ * rows in direction order. */
+glbe_status glbe_halo_bytes(const glbe_ctx* ctx, size_t* bytes);
+
+/* Packs (device buffer d_buf of glbe_halo_bytes) the post-collision
+ * populations of the current level that leave through face 1 (high z: the
+ * e_z = +1 directions of plane nz-2) or face 0 (low z: the e_z = -1
+ * directions of plane 1).  The face must have a ghost plane.  Enqueued on the
+ * context's stream. */
+glbe_status glbe_halo_pack(glbe_ctx* ctx, int face, void* d_buf);
+
+/* Writes a neighbour's packed face into this slab's ghost plane: face 0 (z =
+ * 0) takes the neighbour's face-1 pack (e_z = +1 directions), face 1 (z =
+ * nz-1) its face-0 pack.  Enqueued on the context's stream; the buffer must
+ * hold the data when the stream reaches the copy. */
+glbe_status glbe_halo_unpack(glbe_ctx* ctx, int face, const void* d_buf);
+
+/* Combines the residual records of the n slabs of one grid taken at the same
+ * level (sums of num, den, mass, momentum and non-finite counts, added in
+ * FP64 in slab order) into the record of the grid, r = sqrt(num / den).
+ * GLBE_ERR_ARG if the levels differ. */
+glbe_status glbe_residual_combine(const glbe_residual_info* parts, int n, glbe_residual_info* out);
 
 /* ABI version of the loaded library (GLBE_ABI_VERSION). */
 int glbe_abi_version(void);

@@ -126,6 +126,11 @@ glbe_status glbe::validate_params(const glbe_params* p)
     if (p->variant < 0 || p->variant > 4) return fail(GLBE_ERR_ARG, "variant must be 0 ... 4");
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
+    if ((p->ghost_lo | p->ghost_hi) & ~1) return fail(GLBE_ERR_ARG, "ghost flags must be 0 or 1");
+    if ((p->ghost_lo && p->wall_lo[2]) || (p->ghost_hi && p->wall_hi[2]))
+        return fail(GLBE_ERR_ARG, "a z face has either a wall or a ghost plane");
+    if (p->nz - p->wall_lo[2] - p->wall_hi[2] - p->ghost_lo - p->ghost_hi < 1)
+        return fail(GLBE_ERR_ARG, "no computed z plane between the ghost and wall planes");
     return GLBE_OK;
 }
 
@@ -138,6 +143,8 @@ StepParams glbe::make_step_params(const glbe_params* p)
     s.N = (uint32_t)((size_t)p->nx * p->ny * p->nz);
     s.div_nx = make_fastdiv((uint32_t)p->nx);
     s.div_nxy = make_fastdiv((uint32_t)(p->nx * p->ny));
+    s.glo_z = p->ghost_lo;
+    s.ghi_z = p->ghost_hi;
     for (int d = 0; d < 3; ++d) {
         s.wlo[d] = p->wall_lo[d];
         s.whi[d] = p->wall_hi[d];
@@ -525,13 +532,7 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     c->tol_dev = reinterpret_cast<double*>(misc + 16);
     c->stop_dev = reinterpret_cast<int*>(misc + 24);
     c->sr_ctr = reinterpret_cast<unsigned*>(misc + 32);
-    {
-        // fluid nodes: product over the axes of the planes not on a wall
-        const long long fx = p->nx - p->wall_lo[0] - p->wall_hi[0];
-        const long long fy = p->ny - p->wall_lo[1] - p->wall_hi[1];
-        const long long fz = p->nz - p->wall_lo[2] - p->wall_hi[2];
-        c->mass0 = p->rho0 * (double)(fx * fy * fz);
-    }
+    c->mass0 = p->rho0 * (double)fluid_nodes(p);   // planes on walls and ghost planes excluded
     c->t = 0;
     c->t_snap = -1;
     c->stream = static_cast<cudaStream_t>(p->stream);
@@ -972,6 +973,142 @@ extern "C" glbe_status glbe_checkpoint_load(glbe_ctx* c, const void* h_buf, size
     GLBE_CUDA(cudaStreamSynchronize(c->stream), "restore sync");
     c->t = (long)h.t;
     c->t_snap = (long)h.t_snap;
+    return GLBE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Halo of the slab decomposition along z
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int HALO_MAX_ROWS = 16;   // (5 + 3) rows, twice for the compensated low parts
+
+// Rows of one face: row i copies P elements of esz[i] bytes from src[i] to dst[i].
+struct HaloRows {
+    const char* src[HALO_MAX_ROWS];
+    char* dst[HALO_MAX_ROWS];
+    int esz[HALO_MAX_ROWS];
+    int n;
+};
+
+__global__ void halo_copy_kernel(const HaloRows rows, size_t P)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    for (int r = 0; r < rows.n; ++r) {
+        if (rows.esz[r] == 4)
+            reinterpret_cast<uint32_t*>(rows.dst[r])[i] = reinterpret_cast<const uint32_t*>(rows.src[r])[i];
+        else
+            reinterpret_cast<uint16_t*>(rows.dst[r])[i] = reinterpret_cast<const uint16_t*>(rows.src[r])[i];
+    }
+}
+
+// D3Q19 directions with e_z = +1 and -1 (the ordering of include/glbe.h:
+// 5 = (0,0,1), 11 = (1,0,1), 12 = (-1,0,1), 15 = (0,1,1), 16 = (0,-1,1); their
+// opposites); D3Q7: 5 (+z) and 6 (-z).
+const int EZ_PLUS[5] = {5, 11, 12, 15, 16};
+const int EZ_MINUS[5] = {6, 13, 14, 17, 18};
+
+size_t halo_bytes_of(const glbe_ctx* c)
+{
+    const size_t P = (size_t)c->prm.nx * c->prm.ny;
+    const size_t rows = 5 + (c->prm.induction ? 3 : 0);
+    size_t b = rows * P * (c->prm.storage == GLBE_F32C ? 4 : storage_bytes(c->prm.storage));
+    if (c->prm.storage == GLBE_F32C) b += rows * P * 2;
+    return b;
+}
+
+// Row table between plane z of the current population buffers and a packed
+// buffer: directions `dirs` (e_z = +1 or -1) and, with induction, the D3Q7
+// direction of the same sign of each component.  to_buf: plane -> buffer.
+HaloRows halo_rows(glbe_ctx* c, int z, bool up, char* buf, bool to_buf)
+{
+    HaloRows r{};
+    const size_t N = c->N, P = (size_t)c->prm.nx * c->prm.ny, plane = (size_t)z * P;
+    const int s = (int)(c->t & 1);
+    const bool comp = c->prm.storage == GLBE_F32C;
+    const size_t es = comp ? 4 : storage_bytes(c->prm.storage);
+    const int* dirs = up ? EZ_PLUS : EZ_MINUS;
+    const int a7 = up ? 5 : 6;
+    char* f = static_cast<char*>(c->f[s]);
+    char* g = c->prm.induction ? static_cast<char*>(c->g[s]) : nullptr;
+    size_t off = 0;
+    auto add = [&](char* base, size_t row_elem, size_t esz) {
+        char* pl = base + (row_elem + plane) * esz;
+        char* bf = buf + off;
+        r.src[r.n] = to_buf ? pl : bf;
+        r.dst[r.n] = to_buf ? bf : pl;
+        r.esz[r.n] = (int)esz;
+        ++r.n;
+        off += P * esz;
+    };
+    for (int k = 0; k < 5; ++k) add(f, (size_t)dirs[k] * N, es);
+    if (g)
+        for (int j = 0; j < 3; ++j) add(g, (size_t)(j * 7 + a7) * N, es);
+    if (comp) {   // low parts: FP16 rows after the 19N (21N) high parts
+        char* fl = f + 19 * N * 4;
+        for (int k = 0; k < 5; ++k) add(fl, (size_t)dirs[k] * N, 2);
+        if (g) {
+            char* gl = g + 21 * N * 4;
+            for (int j = 0; j < 3; ++j) add(gl, (size_t)(j * 7 + a7) * N, 2);
+        }
+    }
+    return r;
+}
+
+glbe_status halo_launch(glbe_ctx* c, const HaloRows& r)
+{
+    const size_t P = (size_t)c->prm.nx * c->prm.ny;
+    const unsigned grid = (unsigned)((P + 255) / 256);
+    halo_copy_kernel<<<grid, 256, 0, c->stream>>>(r, P);
+    GLBE_CUDA(cudaGetLastError(), "halo copy");
+    return GLBE_OK;
+}
+
+}  // namespace
+
+extern "C" glbe_status glbe_halo_bytes(const glbe_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(GLBE_ERR_ARG, "ctx or bytes is NULL");
+    *bytes = halo_bytes_of(c);
+    return GLBE_OK;
+}
+
+extern "C" glbe_status glbe_halo_pack(glbe_ctx* c, int face, void* d_buf)
+{
+    if (!c || !d_buf) return fail(GLBE_ERR_ARG, "ctx or buffer is NULL");
+    if (face != 0 && face != 1) return fail(GLBE_ERR_ARG, "face must be 0 (low z) or 1 (high z)");
+    if (!(face ? c->prm.ghost_hi : c->prm.ghost_lo)) return fail(GLBE_ERR_STATE, "face %d has no ghost plane", face);
+    // face 1: e_z = +1 populations of the top computed plane; face 0: e_z = -1 of the bottom one
+    const int z = face ? c->prm.nz - 2 : 1;
+    return halo_launch(c, halo_rows(c, z, face == 1, static_cast<char*>(d_buf), true));
+}
+
+extern "C" glbe_status glbe_halo_unpack(glbe_ctx* c, int face, const void* d_buf)
+{
+    if (!c || !d_buf) return fail(GLBE_ERR_ARG, "ctx or buffer is NULL");
+    if (face != 0 && face != 1) return fail(GLBE_ERR_ARG, "face must be 0 (low z) or 1 (high z)");
+    if (!(face ? c->prm.ghost_hi : c->prm.ghost_lo)) return fail(GLBE_ERR_STATE, "face %d has no ghost plane", face);
+    // the low ghost plane receives what streams upward (e_z = +1), the high one what streams down
+    const int z = face ? c->prm.nz - 1 : 0;
+    return halo_launch(c, halo_rows(c, z, face == 0, const_cast<char*>(static_cast<const char*>(d_buf)), false));
+}
+
+extern "C" glbe_status glbe_residual_combine(const glbe_residual_info* parts, int n, glbe_residual_info* out)
+{
+    if (!parts || !out || n < 1) return fail(GLBE_ERR_ARG, "parts, out or n");
+    glbe_residual_info o{};
+    o.t = parts[0].t;
+    for (int i = 0; i < n; ++i) {
+        if (parts[i].t != o.t) return fail(GLBE_ERR_ARG, "records of levels %ld and %ld", o.t, parts[i].t);
+        o.num += parts[i].num;
+        o.den += parts[i].den;
+        o.mass += parts[i].mass;
+        for (int k = 0; k < 3; ++k) o.momentum[k] += parts[i].momentum[k];
+        o.nonfinite += parts[i].nonfinite;
+    }
+    o.r = o.den > 0.0 ? std::sqrt(o.num / o.den) : (o.num > 0.0 ? INFINITY : 0.0);
+    *out = o;
     return GLBE_OK;
 }
 

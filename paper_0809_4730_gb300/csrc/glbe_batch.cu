@@ -100,6 +100,17 @@ __device__ bool grid_barrier(BatchState* st, long long spin_limit)
     return ok;
 }
 
+// Domain of a tile (tile_start is ascending, ndom + 1 entries).
+__device__ __forceinline__ int tile_domain(const uint32_t* __restrict__ tile_start, int ndom, uint32_t tile)
+{
+    int lo = 0, hi = ndom;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tile_start[mid] <= tile) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 template <int ST, int BT>
 __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* __restrict__ doms, int ndom,
                                                    const uint32_t* __restrict__ tile_start, uint32_t ntiles,
@@ -122,13 +133,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
         const bool resid = (t % 10) == 0;
         const bool have_snap = resid && last_snap >= 0 && last_snap == t - 10;
         for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            // domain of the tile (tile_start is ascending, ndom + 1 entries)
-            int lo = 0, hi = ndom;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (tile_start[mid] <= tile) lo = mid; else hi = mid;
-            }
-            const int d = lo;
+            const int d = tile_domain(tile_start, ndom, tile);
             const BatchDomain& D = doms[d];
             const bool active = __ldcg(&ds[d].active) != 0;
             float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -303,6 +308,7 @@ glbe_status batch_layout(const glbe_params* doms, int n, std::vector<DomLayout>*
         if (s != GLBE_OK) return fail(s, "domain %d: %s", d, glbe_last_error());
         if (doms[d].storage != st) return fail(GLBE_ERR_ARG, "all domains of a batch share one storage type");
         if (doms[d].force_field) return fail(GLBE_ERR_ARG, "batch domains take a uniform force (force_field = 0)");
+        if (doms[d].ghost_lo || doms[d].ghost_hi) return fail(GLBE_ERR_ARG, "batch domains have no ghost planes");
         const size_t N = (size_t)doms[d].nx * doms[d].ny * doms[d].nz;
         const size_t ss = storage_bytes(st);
         DomLayout& L = (*lay)[d];
@@ -484,8 +490,7 @@ glbe_status glbe_batch_init(const glbe_params* doms, int n, void* d_workspace, s
         D.usnap = reinterpret_cast<float*>(b->ws + lay[d].usnap);
         D.nodes = (uint32_t)((size_t)p.nx * p.ny * p.nz);
         D.mhd = p.induction;
-        const long long fluid = (long long)(p.nx - p.wall_lo[0] - p.wall_hi[0]) * (p.ny - p.wall_lo[1] - p.wall_hi[1]) *
-                                (p.nz - p.wall_lo[2] - p.wall_hi[2]);
+        const long long fluid = fluid_nodes(&p);
         D.mass0 = p.rho0 * (double)fluid;
     }
     e = cudaMemcpyAsync(b->d_doms, b->host_doms.data(), sizeof(BatchDomain) * n, cudaMemcpyHostToDevice, b->stream);

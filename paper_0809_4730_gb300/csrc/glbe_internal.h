@@ -34,6 +34,8 @@ struct StepParams {
     uint32_t N;
     FastDiv div_nx, div_nxy;
     int wlo[3], whi[3];
+    int glo_z, ghi_z;     // ghost planes at z = 0 / z = nz - 1 (slab decomposition): not collided,
+                          // gathered from as fluid
     float rho0;
     float inv_gamma;      // 1/gamma
     float inv_gamma2;     // 1/gamma^2
@@ -156,6 +158,14 @@ cudaError_t launch_finalize(const double* partials, unsigned nblocks, double mas
 // Host helpers shared by the C-ABI translation units (glbe_api.cu).
 glbe_status fail(glbe_status s, const char* fmt, ...);       // sets the thread-local message
 glbe_status validate_params(const glbe_params* p);
+// Fluid nodes of a grid: planes on walls and ghost planes excluded.
+inline long long fluid_nodes(const glbe_params* p)
+{
+    const long long fx = p->nx - p->wall_lo[0] - p->wall_hi[0];
+    const long long fy = p->ny - p->wall_lo[1] - p->wall_hi[1];
+    const long long fz = p->nz - p->wall_lo[2] - p->wall_hi[2] - p->ghost_lo - p->ghost_hi;
+    return fx * fy * fz;
+}
 StepParams make_step_params(const glbe_params* p);
 
 // What another translation unit (the adjoint) needs of a context: its

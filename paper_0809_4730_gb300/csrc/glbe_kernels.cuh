@@ -374,8 +374,9 @@ __device__ __forceinline__ Geo make_geo(const StepParams& p, uint32_t n)
     g.z = (int)z;
     g.xm = g.x == 0 ? p.nx - 1 : g.x - 1;
     g.xp = g.x == p.nx - 1 ? 0 : g.x + 1;
+    // a ghost plane is skipped like a solid one, but its neighbours gather from it as fluid
     g.solid = plane_solid(g.x, p.nx, p.wlo[0], p.whi[0]) || plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) ||
-              plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]);
+              plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]) || plane_solid(g.z, p.nz, p.glo_z, p.ghi_z);
     g.sxm = plane_solid(g.xm, p.nx, p.wlo[0], p.whi[0]);
     g.sxp = plane_solid(g.xp, p.nx, p.wlo[0], p.whi[0]);
     row_geometry(p, g.y, g.z, g);
@@ -401,7 +402,8 @@ __device__ __forceinline__ GeoP make_geo_pair(const StepParams& p, uint32_t n0)
     g.y = (int)(zy - z * (uint32_t)p.ny);
     g.z = (int)z;
     g.xm = g.xp = 0;
-    g.solid = plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) || plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]);
+    g.solid = plane_solid(g.y, p.ny, p.wlo[1], p.whi[1]) || plane_solid(g.z, p.nz, p.wlo[2], p.whi[2]) ||
+              plane_solid(g.z, p.nz, p.glo_z, p.ghi_z);
     g.sxm = g.sxp = false;
     row_geometry(p, g.y, g.z, g);
     q.xl = g.x == 0 ? p.nx - 1 : g.x - 1;
@@ -832,6 +834,7 @@ struct Lin {
     V M1, M2;                    // e, e^2 (rows 1, 2)
     V E1, E2;                    // M1 + 11 drho and M2 - 3 drho (the parts of n_1, n_2 linear in f)
     V Qx, Qy, Qz;                // q (rows 4, 6, 8)
+    V Kx, Ky, Kz;                // (3 q + 2 m) / 5: the part of the heat-flux non-equilibrium linear in f
     V P9, P10, P11, P12, P13, P14, P15, P16, P17, P18;
 };
 
@@ -859,6 +862,9 @@ __device__ __forceinline__ Lin<V> linear_moments(const V (&d)[19])
     L.Qx = V(-4.f) * Xax + Xxy + Xxz;
     L.Qy = V(-4.f) * Yax + Yxy + Yyz;
     L.Qz = V(-4.f) * Zax + Zxz + Zyz;
+    L.Kx = V(-2.f) * Xax + Xxy + Xxz;
+    L.Ky = V(-2.f) * Yax + Yxy + Yyz;
+    L.Kz = V(-2.f) * Zax + Zxz + Zyz;
     const V two(2.f);
     const V a9 = two * Ax - Ay - Az, g9 = Gxy + Gxz - two * Gyz;     // axis and diagonal parts of rows 9, 10
     const V a11 = Ay - Az, g11 = Gxy - Gxz;                          // ... of rows 11, 12
@@ -885,11 +891,10 @@ struct NodeMoments {
 
 // D3Q19 moment-space collision change om = T^-1 [-Lambda* (f^ - f^eq,*) +
 // (I - Lambda*/2) S*] (Eqs. ppostcollision, prelax_term).  F is the total
-// force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32, (jlx, jly, jlz) the
-// remainders of that rounding (precise forms; 0 otherwise).
+// force; (jx, jy, jz) = m + F/(2 gamma) rounded to FP32.
 template <class V, bool PRECISE>
 __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMoments<V, PRECISE>& mm, V (&om)[19],
-                                             V rho_inv, V jx, V jy, V jz, V jlx, V jly, V jlz, V Fx, V Fy, V Fz)
+                                             V rho_inv, V jx, V jy, V jz, V Fx, V Fy, V Fz)
 {
     const V ig(p.inv_gamma);
     const V gri = ig * rho_inv;                   // 1/(gamma rho)
@@ -904,18 +909,19 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     // 3 rho0 to row 2 only, so the deviations' moments enter directly
     const V n1 = GLBE_NK(H.E1 - V(19.f) * jjg, L.E1);
     const V n2 = GLBE_NK(H.E2 + V(5.5f) * jjg, L.E2);
-    // heat-flux rows: n = q + (2/3) j is a near-cancellation of two values of
-    // the size of j.  The precise forms take 3 n = (3 q_h + 2 j) + (3 q_l +
-    // 2 j_l): the first sum is exact (3 q_h on the 2^-28 grid, 2 j an FP32
-    // number, nearly opposite), so n no longer carries the rounding of j --
-    // which otherwise moved the converged FP32 state by about one unit in
-    // the last place every few steps (residual floor ~1.4e-8).
+    // heat-flux rows: n = q + (2/3) j with j = m + F/(2 gamma) is a
+    // near-cancellation of two values of the size of j.  The precise forms
+    // use n = (5/3) K + F/(3 gamma), K = (3 q + 2 m)/5 a linear moment of the
+    // populations (exact on their high parts): n no longer carries the FP32
+    // rounding of j, which otherwise moved the converged state by about one
+    // unit in the last place every few steps (residual floor ~1.4e-8 on the
+    // 64^3 duct at gamma = 0.1).
     V n4, n6, n8;
     if constexpr (PRECISE) {
-        const V third(1.f / 3.f);
-        n4 = (vadd_rn(V(3.f) * H.Qx, V(2.f) * jx) + (V(3.f) * L.Qx + V(2.f) * jlx)) * third;
-        n6 = (vadd_rn(V(3.f) * H.Qy, V(2.f) * jy) + (V(3.f) * L.Qy + V(2.f) * jly)) * third;
-        n8 = (vadd_rn(V(3.f) * H.Qz, V(2.f) * jz) + (V(3.f) * L.Qz + V(2.f) * jlz)) * third;
+        const V f3(5.f / 3.f), ig3(p.inv_gamma * (1.f / 3.f));
+        n4 = vfma(f3, H.Kx + L.Kx, ig3 * Fx);
+        n6 = vfma(f3, H.Ky + L.Ky, ig3 * Fy);
+        n8 = vfma(f3, H.Kz + L.Kz, ig3 * Fz);
     } else {
         n4 = H.Qx + V(2.f / 3.f) * jx;
         n6 = H.Qy + V(2.f / 3.f) * jy;
@@ -1131,7 +1137,7 @@ __device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19
         ns.uly = (vfma(-ns.uy, ns.rho, ns.jy) + jly - ns.uy * rlo) * rho_inv;
         ns.ulz = (vfma(-ns.uz, ns.rho, ns.jz) + jlz - ns.uz * rlo) * rho_inv;
     }
-    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, jlx, jly, jlz, Fx, Fy, Fz);
+    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, Fx, Fy, Fz);
 }
 
 template <typename V>

@@ -164,8 +164,7 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
         default: e = launch_step_t<ST_F32C>(false, MODE_STEP_RESID, sp, b, fo, stream, &grid); break;
         }
     }
-    const long long fluid = (long long)(p->nx - p->wall_lo[0] - p->wall_hi[0]) *
-                            (p->ny - p->wall_lo[1] - p->wall_hi[1]) * (p->nz - p->wall_lo[2] - p->wall_hi[2]);
+    const long long fluid = fluid_nodes(p);
     if (e == cudaSuccess && have_prev)
         e = launch_finalize(partials, grid, p->rho0 * (double)fluid, t_dev, record, hist, hist_count, 1, stop, tol,
                             stream);

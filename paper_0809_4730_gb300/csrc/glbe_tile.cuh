@@ -454,6 +454,7 @@ inline bool tile_eligible(const StepParams& p, int mode)
     if (mode == MODE_FIELDS) return false;
     if (p.storage != ST_F32 && p.storage != ST_BF16 && p.storage != ST_F16) return false;
     if (p.wlo[0] || p.whi[0]) return false;                 // x periodic
+    if (p.glo_z || p.ghi_z) return false;                   // no ghost planes
     if (p.nx % TILE_W != 0) return false;
     if (p.ny - p.wlo[1] - p.whi[1] < 1 || p.nz - p.wlo[2] - p.whi[2] < 1) return false;
     const unsigned long long rows = 21ull * (unsigned long long)p.ny * (unsigned long long)p.nz;

@@ -40,6 +40,7 @@ class glbe_params(C.Structure):
         ("storage", C.c_int), ("storage_scale", C.c_double),
         ("stream", C.c_void_p),
         ("variant", C.c_int),
+        ("ghost_lo", C.c_int), ("ghost_hi", C.c_int),
     ]
 
 
@@ -88,6 +89,10 @@ _SIGNATURES = {
     "glbe_batch_destroy": (None, [C.c_void_p]),
     "glbe_step_residual_noalloc": (C.c_int, [_P(glbe_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_int, C.c_long, _P(glbe_residual_info)]),
+    "glbe_halo_bytes": (C.c_int, [C.c_void_p, _P(C.c_size_t)]),
+    "glbe_halo_pack": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "glbe_halo_unpack": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "glbe_residual_combine": (C.c_int, [_P(glbe_residual_info), C.c_int, _P(glbe_residual_info)]),
     "glbe_checkpoint_bytes": (C.c_int, [C.c_void_p, _P(C.c_size_t)]),
     "glbe_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "glbe_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -230,6 +235,28 @@ def glbe_step_residual_noalloc(p: glbe_params, d_src, d_dst, d_force, d_u, have_
                                              int(bool(have_prev)), int(t), C.byref(info)),
            "glbe_step_residual_noalloc")
     return info
+
+
+def glbe_halo_bytes(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(load().glbe_halo_bytes(ctx, C.byref(n)), "glbe_halo_bytes")
+    return n.value
+
+
+def glbe_halo_pack(ctx, face: int, d_buf):
+    _check(load().glbe_halo_pack(ctx, int(face), _ptr(d_buf)), "glbe_halo_pack")
+
+
+def glbe_halo_unpack(ctx, face: int, d_buf):
+    _check(load().glbe_halo_unpack(ctx, int(face), _ptr(d_buf)), "glbe_halo_unpack")
+
+
+def glbe_residual_combine(parts) -> glbe_residual_info:
+    """Record of a grid from the records of its slabs (host only, no device)."""
+    arr = (glbe_residual_info * len(parts))(*parts)
+    out = glbe_residual_info()
+    _check(load().glbe_residual_combine(arr, len(parts), C.byref(out)), "glbe_residual_combine")
+    return out
 
 
 def glbe_destroy(ctx):
@@ -398,7 +425,7 @@ class Solver:
                     p.s[k] = float(val[k])
             elif key == "storage":
                 p.storage = STORAGE[val] if isinstance(val, str) else int(val)
-            elif key in ("induction", "force_field", "variant"):
+            elif key in ("induction", "force_field", "variant", "ghost_lo", "ghost_hi"):
                 setattr(p, key, int(val))
             else:
                 setattr(p, key, float(val))
