@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "adjoint"], default="duct",
+    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled"], default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
     ap.add_argument("--adjoint-n", type=int, default=128)
@@ -209,13 +209,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def duct_solver(storage: str, device="cuda", variant: int = 0):
+def duct_solver(storage: str, device="cuda", variant: int = 0, collision: int = 0):
     import torch
     from paper_0809_4730_gb300.glbe import Solver
     from paper_0809_4730_gb300.inputs import duct_force_x
     d = DUCT
     G = Solver(d["nx"], d["ny"], d["nz"], wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=d["gamma"], nu=d["nu"],
-               force_field=1, storage=storage, device=device, variant=variant)
+               force_field=1, storage=storage, device=device, variant=variant, collision=collision)
     Fx = duct_force_x(d["nx"], d["ny"], d["nz"], d["F0"])[0].reshape(1, -1)
     F_host = torch.tensor(Fx, dtype=torch.float32).pin_memory()
     G.set_force(F_host.to(device))
@@ -375,6 +375,38 @@ def run_glbe(args, rank, ws):
     return line
 
 
+def run_coupled(args, rank, ws):
+    """The fused D3Q19 + D3Q7 step on the large coupled grid: the Hartmann
+    physics (Ha = 10, gamma = 0.1, Pr_m = 0.01) on nx x ny x nz (default
+    512 x 256 x 256), x periodic, walls on y and z, --storage f32 or bf16;
+    bench steps of 10 time steps as for the duct."""
+    import torch
+    stream = torch.cuda.current_stream()
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm = 6800.0
+    st = args.storage
+    G, fluid = hartmann_duct_solver(storage=st, shape=(DUCT["nx"], DUCT["ny"], DUCT["nz"]), variant=args.variant)
+    G.step(10 * args.warmup)
+    G.sync()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        total_ms, plain_ms, nplain = timed_steps(G, args.steps, stream)
+    kern_ms = plain_ms / nplain
+    bpn = bytes_per_node(st, True, 0)
+    achieved = bpn * fluid / (kern_ms * 1e-3) / 1e9
+    G.close()
+    return {"metric": "MLUPS of the fused D3Q19 + D3Q7 step (lagged Lorentz force)",
+            "value": round(10 * args.steps * fluid / (total_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Hartmann duct {DUCT['nx']}x{DUCT['ny']}x{DUCT['nz']}, Ha=10, gamma=0.1, "
+                                   f"Pr_m=0.01, {st} storage", "fluid_nodes": fluid},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "bytes_per_node": bpn, "kernel_ms": round(kern_ms, 5)},
+            "clocks": clk.summary()}
+
+
 def run_sharded(args, rank, ws):
     """One 512 x 256 x 256 duct split along z into ws slabs, slab `rank` on
     this GPU; every time step is the fused step plus the exchange of the
@@ -432,16 +464,16 @@ def run_sharded(args, rank, ws):
 def variants(args, hbm_peak, stream):
     import torch
     out = {}
-    for st, variant in (("f32", 0), ("f16", 0), ("bf16", 0), ("bf16", 2), ("f32", 2)):
+    for st, variant in (("f32", 0), ("f16", 0), ("bf16", 0), ("bf16", 2), ("f32", 2), ("f32", -1)):
         if st == args.storage and variant == 0:
             continue
-        G, _, fluid = duct_solver(st, variant=variant)
+        G, _, fluid = duct_solver(st, variant=max(variant, 0), collision=1 if variant == -1 else 0)
         G.step(30)
         G.sync()
         total_ms, plain_ms, nplain = timed_steps(G, 5, stream)
         kern_ms = plain_ms / nplain
         bpn = bytes_per_node(st, False, 1)
-        out[f"duct_{st}" + ("_paired" if variant == 2 else "")] = {
+        out[f"duct_{st}" + ("_paired" if variant == 2 else "") + ("_srt" if variant == -1 else "")] = {
                              "mlups": round(50 * fluid / (total_ms * 1e-3) / 1e6, 1),
                              "kernel_ms": round(kern_ms, 5), "bytes_per_node": bpn,
                              "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
@@ -783,6 +815,120 @@ def run_batch(args, rank, ws):
     }
 
 
+# ---------------------------------------------------------------------------
+# Stability and preconditioning sweeps (Sec. 5: Poiseuille stability,
+# Hartmann gamma_m studies), many small problems per persistent launch
+# ---------------------------------------------------------------------------
+SWEEP_NU = (0.002, 0.005, 0.02, 0.05)
+SWEEP_UMAX = (0.005, 0.01, 0.02, 0.04)
+SWEEP_GAMMA = (1.0, 0.5, 0.2, 0.1, 0.05, 0.02, 0.01, 0.005)
+
+
+def channel_params(nu: float, umax: float, gamma: float, H: int = 32, storage: str = "f32c"):
+    """Plane channel 1 x (H + 2) x 1 (walls at y = 0, H + 1; half-way walls
+    H apart), uniform F_x giving the Poiseuille maximum u_max = F H^2/(8 nu)."""
+    from paper_0809_4730_gb300.glbe import make_params
+    F = 8.0 * nu * umax / (H * H)
+    return make_params(1, H + 2, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(F, 0, 0),
+                       storage=storage)
+
+
+def stability_map(nus=SWEEP_NU, umaxs=SWEEP_UMAX, gammas=SWEEP_GAMMA, max_steps=100_000, tol=1e-8):
+    """All (nu, u_max, gamma) channels in one persistent launch.  A domain is
+    unstable when its velocity becomes non-finite; gamma_min(nu, u_max) is
+    the smallest gamma of the sweep whose channel stayed finite (None if
+    none did)."""
+    from paper_0809_4730_gb300.glbe import Batch
+    pts = [(nu, um, g) for nu in nus for um in umaxs for g in gammas]
+    B = Batch([channel_params(*q) for q in pts])
+    st, res, sec = B.solve(tol, max_steps, use_graph=True)
+    B.close()
+    cells = {}
+    for (nu, um, g), r in zip(pts, res):
+        c = cells.setdefault((nu, um), {})
+        c[g] = "diverged" if r["nonfinite"] else ("converged" if r["converged"] else "finite")
+        c[f"steps_{g}"] = r["steps"]
+    out = {"seconds": round(sec, 3), "domains": len(pts), "max_steps": max_steps, "tol": tol, "map": []}
+    for (nu, um), c in cells.items():
+        stable = [g for g in gammas if c[g] != "diverged"]
+        out["map"].append({"nu": nu, "u_max": um, "Ma": um * math.sqrt(3.0), "gamma_min": min(stable) if stable
+                           else None, "status": {str(g): c[g] for g in gammas},
+                           "steps": {str(g): c[f"steps_{g}"] for g in gammas}})
+    return out
+
+
+def hartmann_channel(Ha: float, gamma: float, gamma_m: float, H: int = 62, nu: float = 0.01,
+                     storage: str = "f32c"):
+    """Hartmann channel 1 x (H + 2) x 1 of the Hartmann workload (walls on y,
+    B0 along y, nu = eta = 0.01, chi = 0.01, F_x = 1e-6)."""
+    from paper_0809_4730_gb300.glbe import make_params
+    B0 = Ha * math.sqrt(nu * nu) / (H / 2)
+    return make_params(1, H + 2, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
+                       induction=1, gamma_m=gamma_m, eta=nu, chi=0.01, mu=1.0, B0=(0, B0, 0), storage=storage)
+
+
+GAMMA_M_SWEEP = (1.0, 0.5, 0.2, 0.1, 0.05, 0.02)
+
+
+def gamma_m_sweep(Ha: float = 10.0, gammas=(0.05, 1.0), gms=GAMMA_M_SWEEP, max_steps=2_000_000, tol=1e-8):
+    """Steps to r <= tol of the Hartmann channel for every (gamma, gamma_m)
+    pair, all in one persistent launch."""
+    from paper_0809_4730_gb300.glbe import Batch
+    pts = [(g, gm) for g in gammas for gm in gms]
+    B = Batch([hartmann_channel(Ha, g, gm) for g, gm in pts])
+    st, res, sec = B.solve(tol, max_steps, use_graph=True)
+    B.close()
+    out = {"Ha": Ha, "seconds": round(sec, 3), "tol": tol}
+    for (g, gm), r in zip(pts, res):
+        out.setdefault(f"gamma_{g}", {})[f"gamma_m_{gm}"] = (r["steps"] if r["converged"] else
+                                                            ("diverged" if r["nonfinite"] else None))
+    for g in gammas:
+        row = {k: v for k, v in out[f"gamma_{g}"].items() if isinstance(v, int)}
+        out[f"gamma_{g}"]["fastest"] = min(row, key=row.get) if row else None
+    return out
+
+
+def srt_mrt_stability(nus=(0.0005, 0.001, 0.002, 0.005, 0.01), umax=0.05, gamma=0.1, steps=50_000):
+    """The preconditioned SRT-LBE and the MRT-GLBE on the same channel at
+    decreasing viscosity (u_max = 0.05, gamma = 0.1): which stay finite."""
+    from paper_0809_4730_gb300.glbe import GLBE_ERR_DIVERGED, GlbeError, Solver
+    out = {"u_max": umax, "gamma": gamma, "steps": steps}
+    H = 32
+    for coll, name in ((0, "mrt"), (1, "srt")):
+        row = {}
+        for nu in nus:
+            F = 8.0 * nu * umax / (H * H)
+            G = Solver(1, H + 2, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(F, 0, 0),
+                       storage="f32", collision=coll)
+            G.step(steps)
+            try:
+                info = G.residual()
+                row[str(nu)] = "finite" if math.isfinite(info.r) else "diverged"
+            except GlbeError as e:
+                row[str(nu)] = "diverged" if e.status == GLBE_ERR_DIVERGED else "error"
+            G.close()
+        out[name] = row
+    for name in ("mrt", "srt"):
+        ok = [float(k) for k, v in out[name].items() if v == "finite"]
+        out[f"{name}_nu_min_stable"] = min(ok) if ok else None
+    return out
+
+
+def run_sweeps(args, rank, ws):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    smap = stability_map()
+    gms = gamma_m_sweep()
+    srt = srt_mrt_stability()
+    return {"metric": "stability and preconditioning sweeps (batched persistent launches)", "value": None,
+            "unit": None, "n_gpus": ws, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "plane channels 1x34x1 over (nu, u_max, gamma); Hartmann channel 1x64x1, "
+                                   "Ha=10, over (gamma, gamma_m); SRT vs MRT channel at u_max=0.05, gamma=0.1"},
+            "stability_map": smap, "gamma_m_sweep": gms, "srt_vs_mrt": srt,
+            "wall_s": round(time.perf_counter() - t0, 2)}
+
+
 ADJ_NU = 0.05   # nu = eta of the adjoint workload (0.01 diverged at gamma = 0.1: u_max 0.04, Re ~ 500)
 
 
@@ -916,6 +1062,10 @@ def main():
     rank, ws = dist_init(args)
     if args.workload == "batch":
         line = run_batch(args, rank, ws)
+    elif args.workload == "sweeps":
+        line = run_sweeps(args, rank, ws)
+    elif args.workload == "coupled":
+        line = run_coupled(args, rank, ws)
     elif args.workload == "adjoint":
         line = run_adjoint(args, rank, ws)
     elif ws > 1 and not args.replicas:

@@ -120,6 +120,13 @@ typedef struct {
                                  copies (needs no walls along x, nx a multiple of 128, F32, BF16 or
                                  F16 storage, not the _SR forms; else the one-node form is used); 4 = the same tiles with
                                  two x-adjacent nodes per thread in packed FP32x2 arithmetic */
+    int collision;            /* 0 (default): the MRT-GLBE (Secs. 2-3).  1: its limiting form, the preconditioned
+                                 SRT-LBE with forcing term (Sec. 3.1): all rates 1/tau* = s_nu*, equilibrium
+                                 f^eq,* and source S* of Eq. precondsourcecorrect in particle velocity space.
+                                 2: the same SRT with the naive source of Eq. precondsourceincorrect, whose
+                                 Chapman-Enskog expansion has a spurious momentum term for gamma < 1 (for
+                                 comparison).  1 and 2 take F32, F32C or BF16 storage and run one node per
+                                 thread; the batch and the adjoint take 0 */
     int ghost_lo, ghost_hi;   /* slab decomposition along z.  1: the plane z = 0 (resp. z = nz-1) is a ghost
                                  plane holding what the neighbouring slab streams across the face
                                  (glbe_halo_unpack): it is never collided, is outside every sum and

@@ -127,6 +127,9 @@ glbe_status glbe::validate_params(const glbe_params* p)
     if (p->storage_scale < 0.0 || !std::isfinite(p->storage_scale))
         return fail(GLBE_ERR_ARG, "storage_scale must be >= 0 and finite");
     if ((p->ghost_lo | p->ghost_hi) & ~1) return fail(GLBE_ERR_ARG, "ghost flags must be 0 or 1");
+    if (p->collision < 0 || p->collision > 2) return fail(GLBE_ERR_ARG, "collision must be 0 (MRT), 1 or 2 (SRT)");
+    if (p->collision && p->storage != GLBE_F32 && p->storage != GLBE_F32C && p->storage != GLBE_BF16)
+        return fail(GLBE_ERR_ARG, "the SRT collision takes F32, F32C or BF16 storage");
     if ((p->ghost_lo && p->wall_lo[2]) || (p->ghost_hi && p->wall_hi[2]))
         return fail(GLBE_ERR_ARG, "a z face has either a wall or a ghost plane");
     if (p->nz - p->wall_lo[2] - p->wall_hi[2] - p->ghost_lo - p->ghost_hi < 1)
@@ -188,6 +191,7 @@ StepParams glbe::make_step_params(const glbe_params* p)
     s.scale = (float)scale;
     s.inv_scale = (float)(1.0 / scale);
     s.variant = p->variant;
+    s.collision = p->collision;
     s.storage = p->storage;
     // interior nodes: on each axis lo = 1 + wall_lo, hi = n - 2 - wall_hi
     // (neighbours neither on a wall plane nor across the periodic seam); on

@@ -58,6 +58,7 @@ struct StepParams {
     // storage of deviations
     float scale, inv_scale;
     int variant;          // 0 automatic, 1 one node per thread, 2 two nodes per thread, 3 TMA-staged tiles
+    int collision;        // 0 MRT-GLBE; 1 preconditioned SRT-LBE; 2 SRT with the naive source
     int storage;          // Storage of the buffers (for the automatic choice)
     // interior nodes (no solid node among the 18 neighbours, no periodic wrap
     // on y and z; on an x axis without walls every x, the sources across the

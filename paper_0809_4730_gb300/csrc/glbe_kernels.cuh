@@ -1048,6 +1048,55 @@ __device__ __forceinline__ void flow_collide(const StepParams& p, const NodeMome
     }
 }
 
+// The preconditioned SRT-LBE with forcing term (Sec. 3.1), the limiting form
+// of the GLBE with all relaxation rates equal to 1/tau* (tau* = 1/s_nu*):
+// f~_a = f_a - (f_a - f^eq,*_a)/tau* + (1 - 1/(2 tau*)) S*_a in particle
+// velocity space, with
+//   f^eq,*_a = w_a rho [1 + 3 e.u + 9/(2 gamma) (e.u)^2 - 3/(2 gamma) u.u]
+// (the u.u coefficient as the moment tables of App. A fix it) and the
+// preconditioned source of Eq. precondsourcecorrect,
+//   S*_a = w_a [3 (e - u/gamma).F / gamma + 9 (e.u)(e.F) / gamma^2],
+// or, COLL = 2, the naive source of Eq. precondsourceincorrect,
+//   S_a = w_a [3 (e - u).F + 9 (e.u)(e.F)] / gamma,
+// whose Chapman-Enskog expansion carries a spurious momentum term for
+// gamma < 1 (kept for comparison).  u = j/rho with the half-force j of Eq.
+// precondhydrofields.  om receives the change of each population (precise
+// forms) or the post-collision deviation itself (16-bit forms).
+__host__ __device__ constexpr int dir_ey(int a)
+{
+    return (a == 3 || a == 7 || a == 8 || a == 15 || a == 17) ? 1
+           : (a == 4 || a == 9 || a == 10 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int dir_ez(int a)
+{
+    return (a == 5 || a == 11 || a == 12 || a == 15 || a == 16) ? 1
+           : (a == 6 || a == 13 || a == 14 || a == 17 || a == 18) ? -1 : 0;
+}
+template <class V, bool PRECISE, int COLL>
+__device__ __forceinline__ void srt_collide(const StepParams& p, const V (&d)[19], const V (&dl)[19], bool comp,
+                                            V (&om)[19], V rho, V drho, V ux, V uy, V uz, V Fx, V Fy, V Fz)
+{
+    const float ig = p.inv_gamma;
+    const V omega(p.s[9]);                      // 1/tau*, the viscous rate
+    const V keep(1.f - 0.5f * p.s[9]);          // 1 - 1/(2 tau*)
+    const V uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+    const V c2(4.5f * ig), c3(1.5f * ig);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const float ex = (float)dir_ex(a), ey = (float)dir_ey(a), ez = (float)dir_ez(a);
+        const V w(a == 0 ? 1.f / 3.f : (a <= 6 ? 1.f / 18.f : 1.f / 36.f));
+        const V eu = V(ex) * ux + V(ey) * uy + V(ez) * uz;
+        const V eF = V(ex) * Fx + V(ey) * Fy + V(ez) * Fz;
+        const V feq = w * (drho + rho * (V(3.f) * eu + c2 * eu * eu - c3 * uu));   // f^eq,* - w rho0
+        V S;
+        if constexpr (COLL == 1) S = w * (V(3.f * ig) * (eF - V(ig) * uF) + V(9.f * ig * ig) * eu * eF);
+        else S = w * V(ig) * (V(3.f) * (eF - uF) + V(9.f) * eu * eF);
+        const V f = comp ? d[a] + dl[a] : d[a];
+        const V change = omega * (feq - f) + keep * S;
+        om[a] = PRECISE ? change : d[a] + change;
+    }
+}
+
 // Post-collision deviation of one population from the gathered one (f) and
 // the collision output om of flow_collide: the precise forms add the change,
 // the 16-bit forms get f~ itself (the moment-space reconstruction).
@@ -1074,7 +1123,7 @@ struct NodeState {
 // The whole update of a node (pair) from its gathered populations: moments,
 // induction and Lorentz force, velocity, collision changes om (f) and og (g).
 // With collide = false only the macroscopic fields are formed.
-template <class V, int ST, bool MHD>
+template <class V, int ST, bool MHD, int COLL = 0>
 __device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19], const V (&dl)[19],
                                             const V (&q)[21], const V (&ql)[21], V FLpx, V FLpy, V FLpz, V Fx,
                                             V Fy, V Fz, bool collide, V (&om)[19], V (&og)[21], NodeState<V>& ns)
@@ -1137,7 +1186,10 @@ __device__ __forceinline__ void node_update(const StepParams& p, const V (&d)[19
         ns.uly = (vfma(-ns.uy, ns.rho, ns.jy) + jly - ns.uy * rlo) * rho_inv;
         ns.ulz = (vfma(-ns.uz, ns.rho, ns.jz) + jlz - ns.uz * rlo) * rho_inv;
     }
-    if (collide) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, Fx, Fy, Fz);
+    if (collide) {
+        if constexpr (COLL == 0) flow_collide<V, PRECISE>(p, mm, om, rho_inv, ns.jx, ns.jy, ns.jz, Fx, Fy, Fz);
+        else srt_collide<V, PRECISE, COLL>(p, d, dl, S::COMP, om, ns.rho, ns.drho, ns.ux, ns.uy, ns.uz, Fx, Fy, Fz);
+    }
 }
 
 template <typename V>
@@ -1259,7 +1311,7 @@ __device__ __forceinline__ NodeIn<F2> pair_inputs(const StepParams& p, const Ste
     return in;
 }
 
-template <int ST, bool MHD, int MODE, bool DIR = false>
+template <int ST, bool MHD, int MODE, bool DIR = false, int COLL = 0>
 __device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                   uint32_t n, const float (&d)[19], const float (&dl)[19],
                                                   const float (&q)[21], const float (&ql)[21],
@@ -1286,7 +1338,7 @@ __device__ __forceinline__ void load_f_interior_dir(const StepParams& p, const S
 // of MODE_STEP_RESID into acc.  Returns without work for solid nodes.
 // DIR: the per-direction bases of b are filled (kernels launched by
 // launch_mode); they serve the interior gather and the stores of f.
-template <int ST, bool MHD, int MODE, bool CG = false, bool DIR = false, bool FL_IN_F = false>
+template <int ST, bool MHD, int MODE, bool CG = false, bool DIR = false, bool FL_IN_F = false, int COLL = 0>
 __device__ __forceinline__ void scalar_node_step(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                  uint32_t i, float (&acc)[7])
 {
@@ -1316,7 +1368,8 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
         load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
         if (MHD) load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
     }
-    node_from_sources<ST, MHD, MODE, DIR>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE, FL_IN_F>(p, b, n), acc);
+    node_from_sources<ST, MHD, MODE, DIR, COLL>(p, b, fo, n, d, dl, q, ql, node_inputs<MHD, MODE, FL_IN_F>(p, b, n),
+                                                 acc);
 }
 
 // Two-pass coupled update, pass 1 (the persistent batch kernel: one update
@@ -1396,7 +1449,7 @@ __device__ __forceinline__ void coupled_induction_pass(const StepParams& p, cons
 // force and the force field, collides, writes the node's own slots of the
 // destination buffers (or the fields in MODE_FIELDS) and adds the residual
 // terms of MODE_STEP_RESID to acc.
-template <int ST, bool MHD, int MODE, bool DIR>
+template <int ST, bool MHD, int MODE, bool DIR, int COLL>
 __device__ __forceinline__ void node_from_sources(const StepParams& p, const StepBuffers& b, const FieldOut& fo,
                                                   uint32_t n, const float (&d)[19], const float (&dl)[19],
                                                   const float (&q)[21], const float (&ql)[21],
@@ -1407,7 +1460,7 @@ __device__ __forceinline__ void node_from_sources(const StepParams& p, const Ste
     const size_t N = p.N;
     float om[19], og[21];
     NodeState<float> ns;
-    node_update<float, ST, MHD>(p, d, dl, q, ql, in.FLx, in.FLy, in.FLz, in.Fx, in.Fy, in.Fz, MODE != MODE_FIELDS, om,
+    node_update<float, ST, MHD, COLL>(p, d, dl, q, ql, in.FLx, in.FLy, in.FLz, in.Fx, in.Fy, in.Fz, MODE != MODE_FIELDS, om,
                                 og, ns);
 
     if (MODE == MODE_FIELDS) {
@@ -1539,7 +1592,7 @@ __device__ __forceinline__ void prefetch_ahead(const StepParams& p, const StepBu
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
 }
 
-template <int ST, bool MHD, int MODE>
+template <int ST, bool MHD, int MODE, int COLL = 0>
 __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers& b, const FieldOut& fo)
 {
     if (b.stop != nullptr && *b.stop) return;   // converged solve: remaining steps of the chunk are skipped
@@ -1557,7 +1610,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers
     // vs 0.631 ms, F32 1.058 vs 0.898 ms and the BF16 residual step 0.914 vs
     // 0.842 ms; with induction they raise the register count past a block
     // per SM
-    scalar_node_step<ST, MHD, MODE, false, !MHD && base_storage(ST) == ST_BF16 && MODE == MODE_STEP>(p, b, fo, i, acc);
+    scalar_node_step<ST, MHD, MODE, false, COLL == 0 && !MHD && base_storage(ST) == ST_BF16 && MODE == MODE_STEP, false,
+                     COLL>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 
@@ -1565,6 +1619,15 @@ template <int ST, bool MHD, int MODE>
 __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepParams p, const StepBuffers b, const FieldOut fo)
 {
     step_body<ST, MHD, MODE>(p, b, fo);
+}
+
+// The preconditioned SRT-LBE step (Sec. 3.1; COLL = 1, or 2 with the naive
+// source), one node per thread; the collision operator of
+// glbe_params.collision = 1 or 2.
+template <int ST, bool MHD, int MODE, int COLL>
+__global__ void __launch_bounds__(STEP_THREADS) step_kernel_srt(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    step_body<ST, MHD, MODE, COLL>(p, b, fo);
 }
 
 // The plain flow step held to MINB resident blocks of 256 threads per SM:
@@ -1926,6 +1989,15 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
 {
     StepBuffers b = with_dir_bases<ST>(p, b_in);
     b.pf_ahead = 0;
+    if constexpr (MODE != MODE_FIELDS && (ST == ST_F32 || ST == ST_F32C || ST == ST_BF16)) {
+        if (p.collision != 0) {   // preconditioned SRT-LBE: one node per thread
+            const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
+            if (p.collision == 1) step_kernel_srt<ST, MHD, MODE, 1><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+            else step_kernel_srt<ST, MHD, MODE, 2><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+            if (nblocks) *nblocks = grid;
+            return cudaGetLastError();
+        }
+    }
     if constexpr (ST != ST_F32C && !Store<ST>::SR && MODE != MODE_FIELDS) {
         if (p.variant == 3 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, false>(p, b, st, nblocks);
         if (p.variant == 4 && tile_eligible(p, MODE)) return launch_tile<ST, MHD, MODE, true>(p, b, st, nblocks);

@@ -40,6 +40,7 @@ class glbe_params(C.Structure):
         ("storage", C.c_int), ("storage_scale", C.c_double),
         ("stream", C.c_void_p),
         ("variant", C.c_int),
+        ("collision", C.c_int),
         ("ghost_lo", C.c_int), ("ghost_hi", C.c_int),
     ]
 
@@ -322,7 +323,7 @@ def make_params(nx, ny, nz, **kw) -> glbe_params:
                 p.s[k] = float(val[k])
         elif key == "storage":
             p.storage = STORAGE[val] if isinstance(val, str) else int(val)
-        elif key in ("induction", "force_field", "variant"):
+        elif key in ("induction", "force_field", "variant", "ghost_lo", "ghost_hi", "collision"):
             setattr(p, key, int(val))
         else:
             setattr(p, key, float(val))
@@ -425,7 +426,7 @@ class Solver:
                     p.s[k] = float(val[k])
             elif key == "storage":
                 p.storage = STORAGE[val] if isinstance(val, str) else int(val)
-            elif key in ("induction", "force_field", "variant", "ghost_lo", "ghost_hi"):
+            elif key in ("induction", "force_field", "variant", "ghost_lo", "ghost_hi", "collision"):
                 setattr(p, key, int(val))
             else:
                 setattr(p, key, float(val))
