@@ -44,13 +44,16 @@ W19 = [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12
 
 DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 
-# DRAM bytes (read + write) per fluid node of one plain step of the kernel the
-# automatic choice launches (PLAIN_STEP_KERNEL), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
-# on the 256x128x128 duct (4,064,256 fluid nodes; profiles/step_kernel_bf16_duct.md),
-# scaled here by the fluid nodes of the timed duct: the traffic of a step is
-# proportional to its fluid nodes.  Below the algorithmic 80 / 156 B because
-# part of the written data is still in L2 when the kernel ends.
-STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (175747584 + 114489600) / 4064256, "f16": (175882752 + 119174144) / 4064256,
+# DRAM bytes (read + write) of one plain step of the kernel the automatic
+# choice launches (PLAIN_STEP_KERNEL), per fluid node, from `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum -c 1`: BF16 on one launch of the
+# timed 512 x 256 x 256 duct itself (33,032,192 fluid nodes; 79.9 B against
+# the algorithmic 80 B; profiles/step_pair_kernel_bf16_duct.md); F16 and F32
+# on the 256 x 128 x 128 duct (4,064,256 fluid nodes), whose 335 MB state
+# leaves part of the written data in L2 (below the algorithmic 80 / 156 B),
+# scaled by fluid nodes.
+STEP_TRAFFIC_B_PER_FLUID_NODE = {"bf16": (1409381888 + 1230580992) / 33032192,
+                                 "f16": (175882752 + 119174144) / 4064256,
                                  "f32": (332382976 + 267721472) / 4064256}
 # the kernels the automatic choice launches on the duct (x periodic, even nx, no induction)
 PLAIN_STEP_KERNEL = {"bf16": "step_pair_kernel_dense", "f16": "step_pair_kernel_dense", "f32": "step_kernel"}
@@ -331,7 +334,9 @@ def run_glbe(args, rank, ws):
             "frac": round(achieved / hbm_peak, 4),
             "traffic": (round(STEP_TRAFFIC_B_PER_FLUID_NODE[args.storage] * fluid)
                         if args.variant == 0 and args.storage in STEP_TRAFFIC_B_PER_FLUID_NODE else None),
-            "traffic_note": "bytes per launch, ncu capture on the 256x128x128 duct scaled by fluid nodes",
+            "traffic_note": ("bytes of one launch, ncu capture (-c 1) on this 512x256x256 duct"
+                             if args.storage == "bf16" else
+                             "bytes per launch, ncu capture on the 256x128x128 duct scaled by fluid nodes"),
             "kernel": "%s (plain fused collide+stream; %s on residual levels)" % step_kernels(args.storage,
                                                                                            args.variant),
             "bytes_per_node": bpn,

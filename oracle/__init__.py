@@ -59,6 +59,8 @@ class Params(C.Structure):
         ("induction", C.c_int),
         ("gamma_m", C.c_double), ("eta", C.c_double), ("chi", C.c_double),
         ("mu", C.c_double), ("B0", C.c_double * 3),
+        ("box", C.c_int), ("box_lo", C.c_int * 3), ("box_hi", C.c_int * 3),
+        ("U_lid", C.c_double * 3),
     ]
 
 
@@ -140,6 +142,8 @@ class Config:
     chi: float = 1.0
     mu: float = 1.0
     B0: tuple = (0.0, 0.0, 0.0)
+    box: tuple | None = None       # ((lo_x, lo_y, lo_z), (hi_x, hi_y, hi_z)): fluid box of the flow lattice
+    U_lid: tuple = (0.0, 0.0, 0.0)  # velocity of the boundary above the highest fluid z plane
 
     def params(self) -> Params:
         p = Params()
@@ -154,6 +158,11 @@ class Config:
             p.s[k] = float(self.s[k])
         p.induction = int(bool(self.induction))
         p.gamma_m, p.eta, p.chi, p.mu = self.gamma_m, self.eta, self.chi, self.mu
+        p.box = int(self.box is not None)
+        for d in range(3):
+            p.box_lo[d] = int(self.box[0][d]) if self.box is not None else 0
+            p.box_hi[d] = int(self.box[1][d]) if self.box is not None else 0
+            p.U_lid[d] = float(self.U_lid[d])
         return p
 
     @property
@@ -300,8 +309,14 @@ class Solver:
 
 
 def solid_mask(c: Config) -> np.ndarray:
-    """[N] bool: the node lies on a wall plane."""
+    """[N] bool: the node is not fluid for the flow lattice (on a wall plane,
+    or outside the fluid box)."""
     m = np.zeros((c.nz, c.ny, c.nx), dtype=bool)
+    if c.box is not None:
+        (lx, ly, lz), (hx, hy, hz) = c.box
+        inside = np.zeros_like(m)
+        inside[lz:hz + 1, ly:hy + 1, lx:hx + 1] = True
+        m |= ~inside
     for d, n in zip(range(3), (c.nx, c.ny, c.nz)):
         sl = [slice(None)] * 3
         if c.wall_lo[d]:

@@ -49,6 +49,19 @@
  *   - Residual: r(t) = ||u(t) - u(t-10)||_2 / ||u(t)||_2 over fluid nodes and
  *     all three components, evaluated when the state of time level t (a
  *     multiple of 10) is collided.
+ *   - Moving wall (Sec. 5, 3D cavity: link bounce-back with the wall's
+ *     momentum, Ladd): a post-collision population f~_a of a fluid node whose
+ *     link ends on the moving lid returns as f_abar = f~_a - 2 w_a rho0
+ *     (e_a . U)/c_s^2 = f~_a - 6 w_a rho0 (e_a . U).  The preconditioned
+ *     equilibrium keeps the unscaled linear term 3 e.j, so the wall term is
+ *     the one of the plain scheme.  The lid is the flow boundary above the
+ *     highest fluid z plane.
+ *   - Extended induction domain (Sec. 5, MHD cavity: the induced field is
+ *     zero far from the cavity): the flow lattice is fluid only inside a box
+ *     of nodes; around it, up to the wall planes of the grid, the vector
+ *     lattice continues with u = 0 and no Lorentz force (pure magnetic
+ *     diffusion), and the zero induced field is imposed at the grid's wall
+ *     planes by the same anti-bounce-back to B0 as the insulating walls.
  */
 #include <math.h>
 #include <stddef.h>
@@ -75,6 +88,9 @@ typedef struct {
     double chi;                  /* low-Pr_m scaling factor, Sec. 4.1        */
     double mu;                   /* magnetic permeability                    */
     double B0[3];                /* applied field: initial state and wall value */
+    int box;                     /* 1: the flow lattice is fluid only for box_lo <= c <= box_hi */
+    int box_lo[3], box_hi[3];    /* (inclusive, per axis); the vector lattice covers every node off the walls */
+    double U_lid[3];             /* velocity of the flow boundary above the highest fluid z plane */
 } orc_params;
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
@@ -435,6 +451,26 @@ static int wrap(int c, int n) { c %= n; return c < 0 ? c + n : c; }
 
 int orc_is_solid(const orc_params* p, int x, int y, int z) { return is_solid(p, x, y, z); }
 
+/* Solid for the flow lattice: a wall plane, or outside the fluid box. */
+static int flow_solid(const orc_params* p, int x, int y, int z)
+{
+    if (is_solid(p, x, y, z)) return 1;
+    if (!p->box) return 0;
+    int c[3] = {x, y, z};
+    for (int d = 0; d < 3; ++d)
+        if (c[d] < p->box_lo[d] || c[d] > p->box_hi[d]) return 1;
+    return 0;
+}
+
+int orc_flow_solid(const orc_params* p, int x, int y, int z) { return flow_solid(p, x, y, z); }
+
+/* Highest fluid z plane of the flow lattice (the lid lies above it). */
+static int top_fluid_z(const orc_params* p)
+{
+    if (p->box) return p->box_hi[2];
+    return p->wall_hi[2] ? p->nz - 2 : p->nz - 1;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Initial state: rest equilibrium f = w rho0, g = W B0, F_L = 0.          */
 /* ---------------------------------------------------------------------- */
@@ -468,13 +504,20 @@ void orc_fields(const orc_params* p, const double* f, const double* g, const dou
     #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx*p->ny));
-        if (is_solid(p, x, y, z)) {
+        if (flow_solid(p, x, y, z)) {
             if (rho) rho[n] = 0.0;
             for (int d = 0; d < 3; ++d) {
                 if (u) u[n*3+d] = 0.0;
                 if (B) B[n*3+d] = 0.0;
                 if (FLnew) FLnew[n*3+d] = 0.0;
             }
+            /* outside the fluid box the vector lattice still carries B */
+            if (B && p->induction && !is_solid(p, x, y, z))
+                for (int j = 0; j < 3; ++j) {
+                    double b = 0.0;
+                    for (int a = 0; a < 7; ++a) b += g[n*21+j*7+a];
+                    B[n*3+j] = b;
+                }
             continue;
         }
         double ft[19], gt[21], Fn[3], z3[3] = {0.0, 0.0, 0.0};
@@ -513,20 +556,45 @@ static void step(const orc_params* p, const double* s, double tau_m,
     for (long n = 0; n < N; ++n) {
         int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((long)nx*ny));
         if (is_solid(p, x, y, z)) continue;
+        const int fluid = !flow_solid(p, x, y, z);
         double ft[19], gt[21], Fn[3], z3[3] = {0.0, 0.0, 0.0};
-        node_force(p, Fext, n, Fn);
-        node_macro nm;
-        node_collide(p, s, tau_m, f + n*19, p->induction ? g + n*21 : NULL,
-                     p->induction ? FL + n*3 : z3, Fn, ft, gt, &nm);
-        if (uout) for (int d = 0; d < 3; ++d) uout[n*3+d] = nm.u[d];
-        if (p->induction) for (int d = 0; d < 3; ++d) FL[n*3+d] = nm.FL[d];
-        /* streaming, Eq. pstreaming: f_a(x + e_a, t+1) = f~_a(x, t) */
-        for (int a = 0; a < 19; ++a) {
-            int xt = wrap(x + E19[a][0], nx), yt = wrap(y + E19[a][1], ny), zt = wrap(z + E19[a][2], nz);
-            if (is_solid(p, xt, yt, zt))
-                fn[n*19 + opp19[a]] = ft[a];              /* half-way bounce-back */
-            else
-                fn[(((long)zt*ny + yt)*nx + xt)*19 + a] = ft[a];
+        if (fluid) {
+            node_force(p, Fext, n, Fn);
+            node_macro nm;
+            node_collide(p, s, tau_m, f + n*19, p->induction ? g + n*21 : NULL,
+                         p->induction ? FL + n*3 : z3, Fn, ft, gt, &nm);
+            if (uout) for (int d = 0; d < 3; ++d) uout[n*3+d] = nm.u[d];
+            if (p->induction) for (int d = 0; d < 3; ++d) FL[n*3+d] = nm.FL[d];
+        } else {
+            if (!p->induction) continue;
+            /* outside the fluid box: the vector lattice alone, with u = 0
+               (Eq. mcollision, g^eq of B only) and no Lorentz force */
+            double B[3] = {0.0, 0.0, 0.0}, geq[21];
+            for (int j = 0; j < 3; ++j)
+                for (int a = 0; a < 7; ++a) B[j] += g[n*21+j*7+a];
+            orc_vector_equilibrium(p, z3, B, geq);
+            for (int i = 0; i < 21; ++i) gt[i] = g[n*21+i] - (g[n*21+i] - geq[i]) / tau_m;
+            for (int d = 0; d < 3; ++d) FL[n*3+d] = 0.0;
+            if (uout) for (int d = 0; d < 3; ++d) uout[n*3+d] = 0.0;
+        }
+        /* streaming, Eq. pstreaming: f_a(x + e_a, t+1) = f~_a(x, t); a link
+           into the flow boundary is bounced back half-way, with the lid's
+           momentum when it ends above the highest fluid z plane */
+        if (fluid) {
+            const int top = top_fluid_z(p);
+            for (int a = 0; a < 19; ++a) {
+                int xt = wrap(x + E19[a][0], nx), yt = wrap(y + E19[a][1], ny), zt = wrap(z + E19[a][2], nz);
+                if (flow_solid(p, xt, yt, zt)) {
+                    double wall = 0.0;
+                    if (z + E19[a][2] > top) {
+                        double eU = E19[a][0]*p->U_lid[0] + E19[a][1]*p->U_lid[1] + E19[a][2]*p->U_lid[2];
+                        wall = 6.0 * w19(a) * p->rho0 * eU;
+                    }
+                    fn[n*19 + opp19[a]] = ft[a] - wall;
+                } else {
+                    fn[(((long)zt*ny + yt)*nx + xt)*19 + a] = ft[a];
+                }
+            }
         }
         if (p->induction) {
             /* Eq. mstreaming on D3Q7, anti-bounce-back at insulating walls */
@@ -584,7 +652,7 @@ long orc_run(const orc_params* p, double* f, double* g, double* FL, const double
                 double num = 0.0, den = 0.0, mass = 0.0, mom[3] = {0.0, 0.0, 0.0};
                 for (long n = 0; n < N; ++n) {
                     int x = (int)(n % p->nx), y = (int)((n / p->nx) % p->ny), z = (int)(n / ((long)p->nx*p->ny));
-                    if (is_solid(p, x, y, z)) continue;
+                    if (flow_solid(p, x, y, z)) continue;
                     for (int d = 0; d < 3; ++d) {
                         double du = ut[n*3+d] - usnap[n*3+d];
                         num += du*du;

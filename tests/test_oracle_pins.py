@@ -429,6 +429,79 @@ def test_hartmann_profile(orc, Ha, gamma, tol_u):
     assert np.abs(B[:, 2]).max() < 1e-15
 
 
+# ---------------------------------------------------------------------------
+# Extended induction domain (Sec. 5, MHD cavity): the flow lattice is fluid
+# only inside a box, the vector lattice continues outside with u = 0 up to
+# the grid's walls, where the induced field is zero.  For the Hartmann layer
+# (flow box |y| < L, induction domain |y| < L + e) the exterior is a medium
+# of the fluid's magnetic diffusivity at rest: b is linear there, b and b'
+# are continuous at the fluid's walls and b(+-(L + e)) = 0, i.e. the Robin
+# condition e b'(L) + b(L) = 0.  From the steady x-momentum
+# nu u'' + (B0/(mu chi rho0)) b' + F/rho0 = 0 and induction
+# eta b'' + chi B0 u' = 0 (Sec. 4.1 scalings):
+#   u(y) = K (L/Ha)^2 [1 - cosh(Ha y/L)/cosh Ha],  K = (F + B0 C1/(mu chi))/(rho0 nu),
+#   C1 = (chi B0 F/(eta rho0 nu)) (L/Ha)^2 L (1 - tanh(Ha)/Ha) / (e + L tanh(Ha)/Ha);
+# e = 0 is the insulating-wall profile above (P9b).
+# ---------------------------------------------------------------------------
+def hartmann_extended(Ha, L, e, F, nu, eta, chi, B0, y):
+    G = (L / Ha) ** 2 * L * (1 - np.tanh(Ha) / Ha)
+    C1 = chi * B0 * F / (eta * nu) * G / (e + L * np.tanh(Ha) / Ha)
+    K = (F + B0 * C1 / chi) / nu
+    return K * (L / Ha) ** 2 * (1 - np.cosh(Ha * y / L) / np.cosh(Ha))
+
+
+@pytest.mark.parametrize("e", [0, 8, 20])
+def test_hartmann_with_extended_induction_domain(orc, e):
+    Ha, nu, eta, chi, F = 5.0, 0.01, 0.01, 0.01, 1e-6
+    nf = 62                               # fluid rows; half-way walls L = 31 from the centre
+    ny = nf + 2 + 2 * e
+    L = nf / 2
+    B0 = Ha * np.sqrt(nu * eta) / L
+    cfg = orc.Config(1, ny, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=0.1, nu=nu, F=(F, 0, 0),
+                     induction=True, gamma_m=0.1, eta=eta, chi=chi, mu=1.0, B0=(0, B0, 0),
+                     box=((0, 1 + e, 0), (0, ny - 2 - e, 0)))
+    S = orc.Solver(cfg)
+    S.run(5_000_000, tol=1e-11)
+    _, u, B, _ = S.fields()
+    y = np.arange(ny) - (ny - 1) / 2
+    fl = slice(1 + e, ny - 1 - e)
+    ua = hartmann_extended(Ha, L, e, F, nu, eta, chi, B0, y)
+    err = np.abs(u[fl, 0] - ua[fl]).max() / ua[fl].max()
+    assert err < 4e-3, err
+    # outside the box the flow is at rest and the induced field decays to 0 at the grid's walls
+    assert np.abs(u[:1 + e]).max() == 0.0
+    if e > 0:
+        b = B[:, 0]
+        assert abs(b[1]) < 0.1 * np.abs(b).max()
+    # the conducting exterior changes the flow: e = 0 (insulating) vs e
+    if e > 0:
+        u0 = hartmann_extended(Ha, L, 0, F, nu, eta, chi, B0, y)
+        assert np.abs(ua[fl] - u0[fl]).max() > 20 * 4e-3 * ua[fl].max()
+
+
+# ---------------------------------------------------------------------------
+# Moving wall (Sec. 5, cavity lid; link bounce-back with the wall momentum):
+# plane Couette flow between a wall at rest and the lid moving at U is linear,
+# u_x(z) = U (z - 1/2)/H with the walls half-way, which half-way bounce-back
+# reproduces up to a residue next to the lid of O(U^2/gamma) (the quadratic
+# equilibrium terms; 1e-7 U at gamma = 1, 6e-6 U at gamma = 0.1 for
+# U = 0.01); preconditioning does not change the steady state otherwise.  A
+# wrong sign or factor of the wall term is an O(1) error.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+def test_couette_under_the_moving_lid_is_exact(orc, gamma):
+    H, U = 24, 0.01
+    cfg = orc.Config(1, 1, H + 2, wall_lo=(0, 0, 1), wall_hi=(0, 0, 1), gamma=gamma, nu=0.05, U_lid=(U, 0, 0))
+    S = orc.Solver(cfg)
+    S.run(5_000_000, tol=1e-13)
+    _, u, _, _ = S.fields()
+    z = np.arange(H + 2)
+    want = U * (z - 0.5) / H
+    fl = slice(1, H + 1)
+    assert np.abs(u[fl, 0] - want[fl]).max() < 1e-5 * U
+    assert np.abs(u[fl, 1:]).max() < 1e-12 * U
+
+
 def test_hartmann_second_order(orc):
     _, e64, b64, *_ = hartmann(orc, 10, 0.1, 64, 1e-6)
     _, e128, b128, *_ = hartmann(orc, 10, 0.1, 128, 1e-6 * (31.0 / 63.0) ** 2)
