@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled"], default="duct",
+    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity"], default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
     ap.add_argument("--adjoint-n", type=int, default=128)
@@ -934,6 +934,89 @@ def run_sweeps(args, rank, ws):
             "wall_s": round(time.perf_counter() - t0, 2)}
 
 
+# ---------------------------------------------------------------------------
+# 3D lid-driven cavity (Sec. 5): 64^3 fluid nodes (W = 64 between half-way
+# walls), lid along x at U0 = 0.0235, nu = 0.015 (Re = 100); MHD case with B0
+# along y (parallel to the lid, normal to its motion), Ha = 45
+# (B0 = Ha sqrt(nu eta)/(W/2)), eta = 0.015, Pr_m = chi nu/eta = 5.625e-7, on
+# an extended magnetic domain of CAV_EXT nodes around the cavity
+# ---------------------------------------------------------------------------
+CAV_W, CAV_U, CAV_NU, CAV_EXT = 64, 0.0235, 0.015, 16
+
+
+def cavity_solver(gamma: float, mhd: bool, storage: str = "f32c", nu: float = CAV_NU, collision: int = 0):
+    from paper_0809_4730_gb300.glbe import Solver
+    if not mhd:
+        n = CAV_W + 2
+        return Solver(n, n, n, wall_lo=(1, 1, 1), wall_hi=(1, 1, 1), gamma=gamma, nu=nu, U_lid=(CAV_U, 0, 0),
+                      storage=storage, collision=collision), n ** 3
+    n = CAV_W + 2 + 2 * CAV_EXT
+    lo, hi = 1 + CAV_EXT, n - 2 - CAV_EXT
+    eta, Ha = 0.015, 45.0
+    B0 = Ha * math.sqrt(nu * eta) / (CAV_W / 2)
+    G = Solver(n, n, n, wall_lo=(1, 1, 1), wall_hi=(1, 1, 1), gamma=gamma, nu=nu, U_lid=(CAV_U, 0, 0),
+               box=((lo, lo, lo), (hi, hi, hi)), induction=1, gamma_m=gamma, eta=eta, chi=5.625e-7 * eta / nu,
+               mu=1.0, B0=(0, B0, 0), storage=storage, collision=collision)
+    return G, n ** 3
+
+
+def run_cavity(args, rank, ws):
+    """Convergence of the cavity against gamma (Sec. 5: without and with the
+    magnetic field, gamma = gamma_m), F32C storage, steps and device time to
+    r <= 1e-6 (the FP32 collide arithmetic at the lid edges keeps r near
+    1e-7), and the stability of the preconditioned SRT-LBE against the
+    GLBE at decreasing viscosity on the MHD cavity."""
+    import torch
+    from paper_0809_4730_gb300.glbe import GLBE_ERR_DIVERGED, GlbeError
+    stream = torch.cuda.current_stream()
+    out = {"metric": "cavity: steps and device time to r <= 1e-6 against gamma; SRT vs GLBE stability",
+           "n_gpus": ws, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+           "config": {"workload": f"lid-driven cavity {CAV_W}^3 fluid nodes, U0={CAV_U}, nu={CAV_NU} (Re=100); "
+                                  f"MHD: Ha=45, eta=0.015, Pr_m=5.625e-7, B0 along y, extended magnetic domain "
+                                  f"of {CAV_EXT} nodes"}}
+    for mhd, gammas in ((False, (1.0, 0.5, 0.2, 0.1)), (True, (1.0, 0.2, 0.1, 0.05))):
+        res = {}
+        for g in gammas:
+            G, nodes = cavity_solver(g, mhd)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            try:
+                st, steps, r = G.solve(1e-6, 600_000)
+            except GlbeError as e:          # a diverged march is a result, not a failure of the bench
+                st, steps, r = e.status, G.t, float("nan")
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            res[f"gamma_{g}"] = {"status": st, "steps": steps, "r": r, "seconds": round(sec, 3),
+                                 "mlups": round(nodes * steps / max(sec, 1e-9) / 1e6, 1)}
+            print(f"cavity {'mhd' if mhd else 'hydro'} gamma {g}: {res[f'gamma_{g}']}", file=sys.stderr, flush=True)
+            G.close()
+        base = res["gamma_1.0"]
+        for g in gammas[1:]:
+            a = res[f"gamma_{g}"]
+            if a["status"] == 0 and base["status"] == 0:
+                a["gain_steps_vs_gamma_1"] = round(base["steps"] / max(1, a["steps"]), 2)
+                a["gain_time_vs_gamma_1"] = round(base["seconds"] / max(a["seconds"], 1e-9), 2)
+        out["mhd" if mhd else "hydro"] = res
+    stab = {}
+    for coll, name, gam in ((0, "glbe_mrt", 1.0), (1, "srt", 1.0), (0, "glbe_mrt", 0.1), (1, "srt", 0.1)):
+        row = {}
+        for nu in (0.005, 0.015, 0.05, 0.166):
+            G, _ = cavity_solver(gam, True, storage="f32", nu=nu, collision=coll)
+            G.step(20_000)
+            try:
+                info = G.residual()
+                row[str(nu)] = "finite" if math.isfinite(info.r) else "diverged"
+            except GlbeError as e:
+                row[str(nu)] = "diverged" if e.status == GLBE_ERR_DIVERGED else "error"
+            print(f"cavity stability {name} gamma {gam} nu {nu}: {row[str(nu)]}", file=sys.stderr, flush=True)
+            G.close()
+        stab[f"{name}_gamma_{gam}"] = row
+    out["stability_mhd_cavity_20000_steps"] = stab
+    return out
+
+
 ADJ_NU = 0.05   # nu = eta of the adjoint workload (0.01 diverged at gamma = 0.1: u_max 0.04, Re ~ 500)
 
 
@@ -1071,6 +1154,8 @@ def main():
         line = run_sweeps(args, rank, ws)
     elif args.workload == "coupled":
         line = run_coupled(args, rank, ws)
+    elif args.workload == "cavity":
+        line = run_cavity(args, rank, ws)
     elif args.workload == "adjoint":
         line = run_adjoint(args, rank, ws)
     elif ws > 1 and not args.replicas:

@@ -127,6 +127,19 @@ typedef struct {
                                  Chapman-Enskog expansion has a spurious momentum term for gamma < 1 (for
                                  comparison).  1 and 2 take F32, F32C or BF16 storage and run one node per
                                  thread; the batch and the adjoint take 0 */
+    int box;                  /* 1: the flow lattice is fluid only on nodes with box_lo <= c <= box_hi (per axis,
+                                 inclusive; outside, up to the wall planes, the induction lattice
+                                 continues at rest: an extended magnetic domain whose wall planes
+                                 hold the induced field at zero, Sec. 5, MHD cavity).  0: the whole
+                                 grid off the wall planes is fluid */
+    int box_lo[3], box_hi[3];
+    double U_lid[3];          /* velocity of the flow boundary above the highest fluid z plane (the
+                                 moving lid of the cavity, Sec. 5): a link bounced there returns
+                                 with 6 w_a rho0 (e_a . U_lid) added (Ladd's moving-wall rule).
+                                 A box or a non-zero lid runs the one-node cavity kernel (F32,
+                                 F32C or BF16 storage; the MRT or, with F32, the SRT collision);
+                                 glbe_get_state / glbe_set_state, the batch and the adjoint do not
+                                 take it */
     int ghost_lo, ghost_hi;   /* slab decomposition along z.  1: the plane z = 0 (resp. z = nz-1) is a ghost
                                  plane holding what the neighbouring slab streams across the face
                                  (glbe_halo_unpack): it is never collided, is outside every sum and

@@ -307,6 +307,7 @@ glbe_status check_adjoint_args(const CtxView& v, const void* d_work, size_t byte
         return fail(GLBE_ERR_ARG, "the adjoint needs F32 or F32C storage (FP32 state)");
     if (v.prm.ghost_lo || v.prm.ghost_hi) return fail(GLBE_ERR_ARG, "the adjoint runs on a whole grid (no ghost planes)");
     if (v.prm.collision) return fail(GLBE_ERR_ARG, "the adjoint differentiates the MRT collision");
+    if (v.sp.cavity) return fail(GLBE_ERR_ARG, "the adjoint does not take a fluid box or a moving lid");
     if (!d_work) return fail(GLBE_ERR_ARG, "workspace is NULL");
     if ((reinterpret_cast<uintptr_t>(d_work) % ALIGN) != 0)
         return fail(GLBE_ERR_ARG, "workspace must be %zu-byte aligned", ALIGN);

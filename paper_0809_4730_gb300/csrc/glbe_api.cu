@@ -130,6 +130,22 @@ glbe_status glbe::validate_params(const glbe_params* p)
     if (p->collision < 0 || p->collision > 2) return fail(GLBE_ERR_ARG, "collision must be 0 (MRT), 1 or 2 (SRT)");
     if (p->collision && p->storage != GLBE_F32 && p->storage != GLBE_F32C && p->storage != GLBE_BF16)
         return fail(GLBE_ERR_ARG, "the SRT collision takes F32, F32C or BF16 storage");
+    if (p->box != 0 && p->box != 1) return fail(GLBE_ERR_ARG, "box must be 0 or 1");
+    const bool lid = p->U_lid[0] != 0.0 || p->U_lid[1] != 0.0 || p->U_lid[2] != 0.0;
+    if (p->box || lid) {
+        if (p->storage != GLBE_F32 && p->storage != GLBE_F32C && p->storage != GLBE_BF16)
+            return fail(GLBE_ERR_ARG, "a fluid box or a moving lid takes F32, F32C or BF16 storage");
+        if (p->collision == 2 || (p->collision == 1 && p->storage != GLBE_F32))
+            return fail(GLBE_ERR_ARG, "the cavity kernel runs the MRT or, with F32 storage, the SRT collision");
+        if (p->ghost_lo || p->ghost_hi) return fail(GLBE_ERR_ARG, "a cavity is not split into slabs");
+        if (p->box)
+            for (int d = 0; d < 3; ++d)
+                if (p->box_lo[d] < 0 || p->box_hi[d] >= n[d] || p->box_lo[d] > p->box_hi[d])
+                    return fail(GLBE_ERR_ARG, "box axis %d: need 0 <= box_lo <= box_hi < n", d);
+        if (fluid_nodes(p) < 1) return fail(GLBE_ERR_ARG, "the fluid box holds no node off the walls");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(p->U_lid[d])) return fail(GLBE_ERR_ARG, "U_lid must be finite");
+    }
     if ((p->ghost_lo && p->wall_lo[2]) || (p->ghost_hi && p->wall_hi[2]))
         return fail(GLBE_ERR_ARG, "a z face has either a wall or a ghost plane");
     if (p->nz - p->wall_lo[2] - p->wall_hi[2] - p->ghost_lo - p->ghost_hi < 1)
@@ -148,6 +164,25 @@ StepParams glbe::make_step_params(const glbe_params* p)
     s.div_nxy = make_fastdiv((uint32_t)(p->nx * p->ny));
     s.glo_z = p->ghost_lo;
     s.ghi_z = p->ghost_hi;
+    s.box = p->box;
+    for (int d = 0; d < 3; ++d) {
+        s.blo[d] = p->box ? p->box_lo[d] : 0;
+        s.bhi[d] = p->box ? p->box_hi[d] : (d == 0 ? p->nx : d == 1 ? p->ny : p->nz) - 1;
+    }
+    s.top_z = p->box ? p->box_hi[2] : (p->wall_hi[2] ? p->nz - 2 : p->nz - 1);
+    {
+        // moving-wall term of the lid, 6 w_a rho0 (e_a . U_lid), in the ordering of include/glbe.h
+        static const int E[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                     {1, 1, 0},  {-1, 1, 0}, {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1},
+                                     {-1, 0, -1}, {0, 1, 1}, {0, -1, 1}, {0, 1, -1}, {0, -1, -1}};
+        for (int a = 0; a < 19; ++a) {
+            const double w = a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+            const double eU = E[a][0] * p->U_lid[0] + E[a][1] * p->U_lid[1] + E[a][2] * p->U_lid[2];
+            s.lid_corr[a] = (float)(6.0 * w * p->rho0 * eU);
+        }
+        const bool lid = p->U_lid[0] != 0.0 || p->U_lid[1] != 0.0 || p->U_lid[2] != 0.0;
+        s.cavity = (p->box || lid) ? 1 : 0;
+    }
     for (int d = 0; d < 3; ++d) {
         s.wlo[d] = p->wall_lo[d];
         s.whi[d] = p->wall_hi[d];
@@ -206,6 +241,23 @@ StepParams glbe::make_step_params(const glbe_params* p)
         if (hi < lo) s.interior_ok = 0;
         s.ilo[d] = (uint32_t)lo;
         s.ispan[d] = hi >= lo ? (uint32_t)(hi - lo) : 0u;
+    }
+    if (s.cavity) {
+        // interior nodes of a cavity: inside the box with a margin of one node
+        // (no bounced link, none to the lid); on an axis the box spans whole
+        // without walls the periodic-seam rule of the plain grid stays
+        const int n[3] = {p->nx, p->ny, p->nz};
+        s.interior_ok = 1;
+        for (int d = 0; d < 3; ++d) {
+            if (p->box && p->box_lo[d] == 0 && p->box_hi[d] == n[d] - 1 && !p->wall_lo[d] && !p->wall_hi[d]) continue;
+            int lo = (p->box ? p->box_lo[d] : 0) + 1, hi = (p->box ? p->box_hi[d] : n[d] - 1) - 1;
+            if (lo < 1 + p->wall_lo[d]) lo = 1 + p->wall_lo[d];
+            if (hi > n[d] - 2 - p->wall_hi[d]) hi = n[d] - 2 - p->wall_hi[d];
+            if (d == 2 && hi > s.top_z - 1) hi = s.top_z - 1;
+            if (hi < lo) s.interior_ok = 0;
+            s.ilo[d] = (uint32_t)lo;
+            s.ispan[d] = hi >= lo ? (uint32_t)(hi - lo) : 0u;
+        }
     }
     // D3Q19 directions in the order of include/glbe.h
     static const int E[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
@@ -550,6 +602,11 @@ glbe_status glbe_init(const glbe_params* p, void* d_workspace, size_t bytes, glb
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c->ws + L.usnap, 0, snap_rows(p->storage) * c->N * sizeof(float), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sr_ctr, 0, 2 * sizeof(unsigned), c->stream);
+    if (e == cudaSuccess && c->sp.cavity) {   // the lid's links of the first gather (see lid_init_kernel)
+        if (p->storage == GLBE_F32) e = launch_lid_init_t<ST_F32>(c->sp, c->f[0], c->stream);
+        else if (p->storage == GLBE_F32C) e = launch_lid_init_t<ST_F32C>(c->sp, c->f[0], c->stream);
+        else e = launch_lid_init_t<ST_BF16>(c->sp, c->f[0], c->stream);
+    }
     if (e == cudaSuccess) {
         misc_set_kernel<<<1, 1, 0, c->stream>>>(c->t_dev, 10, c->stop_dev, 0, c->tol_dev, 0.0, c->record,
                                                 c->hist_count, 1);
@@ -804,6 +861,7 @@ glbe_status glbe_fields(glbe_ctx* c, float* d_rho, float* d_u, float* d_B)
 glbe_status glbe_get_state(glbe_ctx* c, float* d_df, float* d_dg, float* d_FL)
 {
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
+    if (c->sp.cavity) return fail(GLBE_ERR_STATE, "state transfer does not take a fluid box or a moving lid");
     const int s = (int)(c->t & 1);
     const bool mhd = c->prm.induction;
     cudaError_t e;
@@ -821,6 +879,7 @@ glbe_status glbe_get_state(glbe_ctx* c, float* d_df, float* d_dg, float* d_FL)
 
 glbe_status glbe_set_state(glbe_ctx* c, const float* d_df, const float* d_dg, const float* d_FL, long t)
 {
+    if (c && c->sp.cavity) return fail(GLBE_ERR_STATE, "state transfer does not take a fluid box or a moving lid");
     if (!c) return fail(GLBE_ERR_ARG, "ctx is NULL");
     if (t < 0) return fail(GLBE_ERR_ARG, "t must be >= 0");
     const int s = (int)(t & 1);

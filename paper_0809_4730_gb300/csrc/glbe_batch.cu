@@ -310,6 +310,7 @@ glbe_status batch_layout(const glbe_params* doms, int n, std::vector<DomLayout>*
         if (doms[d].force_field) return fail(GLBE_ERR_ARG, "batch domains take a uniform force (force_field = 0)");
         if (doms[d].ghost_lo || doms[d].ghost_hi) return fail(GLBE_ERR_ARG, "batch domains have no ghost planes");
         if (doms[d].collision) return fail(GLBE_ERR_ARG, "batch domains use the MRT collision");
+        if (make_step_params(&doms[d]).cavity) return fail(GLBE_ERR_ARG, "batch domains have no box or lid");
         const size_t N = (size_t)doms[d].nx * doms[d].ny * doms[d].nz;
         const size_t ss = storage_bytes(st);
         DomLayout& L = (*lay)[d];

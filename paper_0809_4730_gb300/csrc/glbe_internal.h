@@ -36,6 +36,11 @@ struct StepParams {
     int wlo[3], whi[3];
     int glo_z, ghi_z;     // ghost planes at z = 0 / z = nz - 1 (slab decomposition): not collided,
                           // gathered from as fluid
+    int cavity;           // 1: box and / or lid (the cavity kernel)
+    int box;              // the flow lattice is fluid only inside [blo, bhi]
+    int blo[3], bhi[3];
+    int top_z;            // highest fluid z plane of the flow lattice
+    float lid_corr[19];   // 6 w_a rho0 (e_a . U_lid): added to a link bounced above top_z
     float rho0;
     float inv_gamma;      // 1/gamma
     float inv_gamma2;     // 1/gamma^2
@@ -141,6 +146,10 @@ cudaError_t launch_get_state_t(bool mhd, const StepParams& p, const void* fsrc, 
 // the last call (the flag is then cleared); one flag per storage type.
 template <int ST>
 int tile_wait_error_t();
+// Initial state of a context with a moving lid (F32, F32C and BF16 storage):
+// see lid_init_kernel.
+template <int ST>
+cudaError_t launch_lid_init_t(const StepParams& p, void* fbuf, cudaStream_t st);
 template <int ST>
 cudaError_t launch_set_state_t(bool mhd, const StepParams& p, void* fsrc, void* gsrc, float* FL, const float* df,
                                const float* dg, const float* dFL, cudaStream_t st);
@@ -162,10 +171,21 @@ glbe_status validate_params(const glbe_params* p);
 // Fluid nodes of a grid: planes on walls and ghost planes excluded.
 inline long long fluid_nodes(const glbe_params* p)
 {
-    const long long fx = p->nx - p->wall_lo[0] - p->wall_hi[0];
-    const long long fy = p->ny - p->wall_lo[1] - p->wall_hi[1];
-    const long long fz = p->nz - p->wall_lo[2] - p->wall_hi[2] - p->ghost_lo - p->ghost_hi;
-    return fx * fy * fz;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    long long count = 1;
+    for (int d = 0; d < 3; ++d) {
+        int lo = p->wall_lo[d], hi = n[d] - 1 - p->wall_hi[d];
+        if (d == 2) {
+            lo += p->ghost_lo;
+            hi -= p->ghost_hi;
+        }
+        if (p->box) {
+            lo = lo > p->box_lo[d] ? lo : p->box_lo[d];
+            hi = hi < p->box_hi[d] ? hi : p->box_hi[d];
+        }
+        count *= hi >= lo ? hi - lo + 1 : 0;
+    }
+    return count;
 }
 StepParams make_step_params(const glbe_params* p);
 

@@ -1947,6 +1947,7 @@ __global__ void __launch_bounds__(STEP_THREADS) set_state_kernel(const StepParam
 // ---------------------------------------------------------------------------
 }  // namespace glbe
 #include "glbe_tile.cuh"
+#include "glbe_cavity.cuh"
 namespace glbe {
 
 // b with its per-direction bases filled (addresses formed as integers: a
@@ -1989,6 +1990,18 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
 {
     StepBuffers b = with_dir_bases<ST>(p, b_in);
     b.pf_ahead = 0;
+    if constexpr (ST == ST_F32 || ST == ST_F32C || ST == ST_BF16) {
+        if (p.cavity) {   // fluid box and / or moving lid: the one-node cavity kernel
+            const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
+            if (MODE != MODE_FIELDS && p.collision == 1) {
+                if constexpr (ST == ST_F32) cavity_kernel<ST, MHD, MODE, 1><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+            } else {
+                cavity_kernel<ST, MHD, MODE, 0><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+            }
+            if (nblocks) *nblocks = grid;
+            return cudaGetLastError();
+        }
+    }
     if constexpr (MODE != MODE_FIELDS && (ST == ST_F32 || ST == ST_F32C || ST == ST_BF16)) {
         if (p.collision != 0) {   // preconditioned SRT-LBE: one node per thread
             const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);

@@ -113,6 +113,8 @@ extern "C" glbe_status glbe_step_residual_noalloc(const glbe_params* p, const vo
     glbe_status st = validate_params(p);
     if (st != GLBE_OK) return st;
     if (p->induction) return fail(GLBE_ERR_ARG, "the allocation-free step covers the D3Q19 flow lattice only");
+    if (make_step_params(p).cavity)
+        return fail(GLBE_ERR_ARG, "the allocation-free step takes no fluid box or moving lid");
     if (!d_src || !d_dst || !d_u || !out) return fail(GLBE_ERR_ARG, "src, dst, u or out is NULL");
     if (d_src == d_dst) return fail(GLBE_ERR_ARG, "src and dst must be different buffers");
     if (p->force_field && !d_force) return fail(GLBE_ERR_ARG, "force_field > 0 needs a force field");

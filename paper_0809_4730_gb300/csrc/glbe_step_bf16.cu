@@ -11,4 +11,5 @@ template cudaError_t launch_get_state_t<ST_BF16>(bool, const StepParams&, const 
 template cudaError_t launch_set_state_t<ST_BF16>(bool, const StepParams&, void*, void*, float*, const float*,
                                                 const float*, const float*, cudaStream_t);
 template int tile_wait_error_t<ST_BF16>();
+template cudaError_t launch_lid_init_t<ST_BF16>(const StepParams&, void*, cudaStream_t);
 }  // namespace glbe

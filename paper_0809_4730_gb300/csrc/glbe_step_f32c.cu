@@ -11,4 +11,5 @@ template cudaError_t launch_get_state_t<ST_F32C>(bool, const StepParams&, const 
 template cudaError_t launch_set_state_t<ST_F32C>(bool, const StepParams&, void*, void*, float*, const float*,
                                                 const float*, const float*, cudaStream_t);
 template int tile_wait_error_t<ST_F32C>();
+template cudaError_t launch_lid_init_t<ST_F32C>(const StepParams&, void*, cudaStream_t);
 }  // namespace glbe

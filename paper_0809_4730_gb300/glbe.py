@@ -41,6 +41,7 @@ class glbe_params(C.Structure):
         ("stream", C.c_void_p),
         ("variant", C.c_int),
         ("collision", C.c_int),
+        ("box", C.c_int), ("box_lo", C.c_int * 3), ("box_hi", C.c_int * 3), ("U_lid", C.c_double * 3),
         ("ghost_lo", C.c_int), ("ghost_hi", C.c_int),
     ]
 
@@ -314,10 +315,15 @@ def make_params(nx, ny, nz, **kw) -> glbe_params:
     p = glbe_params_default()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for key, val in kw.items():
-        if key in ("wall_lo", "wall_hi", "F", "B0"):
+        if key in ("wall_lo", "wall_hi", "F", "B0", "U_lid"):
             arr = getattr(p, key)
             for d in range(3):
                 arr[d] = type(arr[d])(val[d])
+        elif key == "box":
+            p.box = int(val is not None)
+            for d in range(3):
+                p.box_lo[d] = int(val[0][d]) if val is not None else 0
+                p.box_hi[d] = int(val[1][d]) if val is not None else 0
         elif key == "s":
             for k in range(19):
                 p.s[k] = float(val[k])
@@ -417,10 +423,15 @@ class Solver:
         p = glbe_params_default()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         for key, val in kw.items():
-            if key in ("wall_lo", "wall_hi", "F", "B0"):
+            if key in ("wall_lo", "wall_hi", "F", "B0", "U_lid"):
                 arr = getattr(p, key)
                 for d in range(3):
                     arr[d] = type(arr[d])(val[d])
+            elif key == "box":
+                p.box = int(val is not None)
+                for d in range(3):
+                    p.box_lo[d] = int(val[0][d]) if val is not None else 0
+                    p.box_hi[d] = int(val[1][d]) if val is not None else 0
             elif key == "s":
                 for k in range(19):
                     p.s[k] = float(val[k])
