@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity"], default="duct",
+    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity", "tts"], default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
     ap.add_argument("--adjoint-n", type=int, default=128)
@@ -960,6 +960,70 @@ def cavity_solver(gamma: float, mhd: bool, storage: str = "f32c", nu: float = CA
     return G, n ** 3
 
 
+def run_tts(args, rank, ws):
+    """Time to r <= 1e-8 on the full 512 x 256 x 256 duct (F32C storage, the
+    duct's nu = 0.5) at gamma = 1, 0.5, 0.1 and 0.05: steps, device time,
+    and (CPU leg) the error of the converged field against the FP64 oracle
+    on the 1 x 256 x 256 column at gamma = 0.1 -- the duct's steady state is
+    x-invariant, so the column is the same discrete problem."""
+    import numpy as np
+    import torch
+    from paper_0809_4730_gb300.glbe import Solver
+    from paper_0809_4730_gb300.inputs import duct_force_x
+    stream = torch.cuda.current_stream()
+    d = DUCT
+    Fx = torch.tensor(duct_force_x(d["nx"], d["ny"], d["nz"], d["F0"])[0].reshape(1, -1), dtype=torch.float32,
+                      device="cuda")
+    out = {"metric": "steps and device time to r <= 1e-8, 512x256x256 duct, F32C", "n_gpus": ws,
+           "higher_is_better": False, "data": "synthetic", "dtype": "f32"}
+    fields = {}
+    for gamma in (1.0, 0.5, 0.1, 0.05):
+        G = Solver(d["nx"], d["ny"], d["nz"], wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=gamma, nu=d["nu"],
+                   force_field=1, storage="f32c")
+        G.set_force(Fx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st, steps, r = G.solve(1e-8, 400_000)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        out[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r, "seconds": round(sec, 3)}
+        print(f"tts gamma {gamma}: {out[f'gamma_{gamma}']}", file=sys.stderr, flush=True)
+        if gamma == 0.1:
+            _, u, _ = G.fields()
+            fields[gamma] = u[0].reshape(d["nz"], d["ny"], d["nx"]).double().cpu().numpy()
+        G.close()
+    base = out["gamma_1.0"]
+    for gamma in (0.5, 0.1, 0.05):
+        a = out[f"gamma_{gamma}"]
+        if a["status"] == 0 and base["status"] == 0:
+            a["gain_steps_vs_gamma_1"] = round(base["steps"] / a["steps"], 2)
+            a["gain_time_vs_gamma_1"] = round(base["seconds"] / a["seconds"], 2)
+    if not args.no_cpu_baseline:
+        # CPU leg: the oracle on the x-invariant column at gamma = 0.1
+        import oracle
+        oracle.set_threads(os.cpu_count() or 1)
+        ny, nz = d["ny"], d["nz"]
+        F = duct_force_x(1, ny, nz, d["F0"])[0].reshape(-1)
+        Fext = np.zeros((ny * nz, 3))
+        Fext[:, 0] = F
+        S = oracle.Solver(oracle.Config(1, ny, nz, wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=0.1, nu=d["nu"]),
+                          Fext=Fext)
+        t0 = time.perf_counter()
+        S.run(3_000_000, tol=1e-8)
+        t8, w8 = S.t, time.perf_counter() - t0
+        S.run(3_000_000, tol=1e-11)
+        _, ou, _, _ = S.fields()
+        col = ou[:, 0].reshape(nz, ny)[1:-1, 1:-1]
+        ux = fields[0.1][1:-1, 1:-1, :]
+        out["gamma_0.1"]["error_vs_oracle"] = float(np.abs(ux - col[:, :, None]).max() / np.abs(col).max())
+        out["cpu_baseline"] = {"kind": "oracle", "cores": oracle.get_threads(), "sample": "1x256x256 column, gamma 0.1",
+                               "steps_1e-8": t8, "seconds_1e-8": round(w8, 2),
+                               "value": round(ny * nz * t8 / w8 / 1e6, 3), "unit": "MLUPS"}
+    return out
+
+
 def run_cavity(args, rank, ws):
     """Convergence of the cavity against gamma (Sec. 5: without and with the
     magnetic field, gamma = gamma_m), F32C storage, steps and device time to
@@ -1156,6 +1220,8 @@ def main():
         line = run_coupled(args, rank, ws)
     elif args.workload == "cavity":
         line = run_cavity(args, rank, ws)
+    elif args.workload == "tts":
+        line = run_tts(args, rank, ws)
     elif args.workload == "adjoint":
         line = run_adjoint(args, rank, ws)
     elif ws > 1 and not args.replicas:
