@@ -22,3 +22,10 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def orc2():
+    from oracle import d2
+    d2.build()
+    return d2
