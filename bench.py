@@ -82,7 +82,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity", "tts"], default="duct",
+    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity", "tts", "2d",
+                                           "cpu-configs"],
+                    default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
     ap.add_argument("--adjoint-n", type=int, default=128)
@@ -99,6 +101,9 @@ def parse():
     ap.add_argument("--batch-tol", type=float, default=1e-8)
     ap.add_argument("--replicas", action="store_true",
                     help="with N > 1: N independent replicas of the duct instead of one duct split into N slabs")
+    ap.add_argument("--forms2d", default="f32_mhd,bf16_mhd,f32c_mhd,f32_flow,bf16_flow",
+                    help="2d workload: storage forms timed (storage_mhd or storage_flow)")
+    ap.add_argument("--no-tts", action="store_true", help="2d workload: skip the time-to-solution part")
     ap.add_argument("--nx", type=int, default=None, help="override the duct size (profiling of a small case)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
@@ -516,6 +521,20 @@ def variants(args, hbm_peak, stream):
         torch.cuda.empty_cache()
     out["batch_64_ducts_bounded"] = batch_bounded(hbm_peak)
     out["time_to_1e-8_hartmann_64x64x8"] = time_to_solution()
+    # the 2D lattices: the fused D2Q9 + D2Q5 step on the 4096^2 Hartmann channel
+    for st in ("f32", "bf16"):
+        G, fluid = channel2d_solver(st, True)
+        G.step(30)
+        G.sync()
+        total_ms, plain_ms, nplain = timed_steps(G, 3, stream)
+        kern_ms = plain_ms / nplain
+        bpn = bytes_per_node_2d(st, True)
+        out[f"d2q9_d2q5_4096x4096_{st}"] = {
+            "mlups": round(30 * fluid / (total_ms * 1e-3) / 1e6, 1), "kernel_ms": round(kern_ms, 5),
+            "bytes_per_node": bpn, "hbm_frac": round(bpn * fluid / (kern_ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        G.close()
+        del G
+        torch.cuda.empty_cache()
     return out
 
 
@@ -1024,6 +1043,58 @@ def run_tts(args, rank, ws):
     return out
 
 
+def cpu_configs():
+    """CPU baseline of the small configurations, the FP64 oracle on this
+    host: the 4 x 32 x 4 Poiseuille channel (gamma = 0.1, tau = 0.8 on the
+    stress rows, i.e. nu = gamma (tau - 1/2)/3; gamma = 1 at the same nu) to
+    r <= 1e-10, and the 64 x 64 x 8 Hartmann duct (walls on y, periodic x
+    and z: its steady state is the 1 x 64 x 1 column's) at Ha = 5, 10, 20,
+    gamma = gamma_m in {1, 0.1}, Pr_m = 0.01, to r <= 1e-8.  Steps, wall
+    time, MLUPS of the column, error against the closed forms.  One thread
+    (the problems are a few hundred nodes)."""
+    import numpy as np
+    import oracle
+    oracle.set_threads(1)
+    out = {"kind": "oracle", "cores": 1}
+    nu1 = 0.1 * (0.8 - 0.5) / 3
+    rows = {}
+    for gamma in (1.0, 0.1):
+        cfg = oracle.Config(4, 32, 4, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu1, F=(1e-6, 0, 0))
+        S = oracle.Solver(cfg)
+        t0 = time.perf_counter()
+        S.run(20_000_000, tol=1e-10)
+        w = time.perf_counter() - t0
+        _, u, _, _ = S.fields()
+        y = np.arange(32, dtype=float)
+        ana = 1e-6 * (y - 0.5) * (30.5 - y) / (2 * nu1)
+        ux = u.reshape(4, 32, 4, 3)[0, 1:-1, 0, 0]
+        rows[f"gamma_{gamma}"] = {"steps": S.t, "seconds": round(w, 3), "mlups": round(512 * S.t / w / 1e6, 2),
+                                  "err_vs_analytic": float(np.abs(ux - ana[1:-1]).max() / ana.max())}
+    out["poiseuille_4x32x4_to_1e-10"] = rows
+    rows = {}
+    for Ha in (5.0, 10.0, 20.0):
+        for gamma in (1.0, 0.1):
+            nu = eta = 0.01
+            ny = 64
+            L = (ny - 2) / 2
+            B0 = Ha * nu / L
+            cfg = oracle.Config(1, ny, 1, wall_lo=(0, 1, 0), wall_hi=(0, 1, 0), gamma=gamma, nu=nu, F=(1e-6, 0, 0),
+                                induction=True, gamma_m=gamma, eta=eta, chi=0.01, mu=1.0, B0=(0, B0, 0))
+            S = oracle.Solver(cfg)
+            t0 = time.perf_counter()
+            S.run(20_000_000, tol=1e-8)
+            w = time.perf_counter() - t0
+            _, u, _, _ = S.fields()
+            yy = np.arange(ny) - (ny - 1) / 2
+            A = 1e-6 * L ** 2 / (nu * Ha * np.tanh(Ha))
+            ua = A * (1 - np.cosh(Ha * yy / L) / np.cosh(Ha))
+            rows[f"Ha_{Ha:g}_gamma_{gamma}"] = {
+                "steps": S.t, "seconds": round(w, 3), "mlups": round(62 * S.t / w / 1e6, 2),
+                "err_vs_analytic": float(np.abs(u[1:-1, 0] - ua[1:-1]).max() / ua.max())}
+    out["hartmann_64x64x8_column_to_1e-8"] = rows
+    return out
+
+
 def run_cavity(args, rank, ws):
     """Convergence of the cavity against gamma (Sec. 5: without and with the
     magnetic field, gamma = gamma_m), F32C storage, steps and device time to
@@ -1079,6 +1150,147 @@ def run_cavity(args, rank, ws):
         stab[f"{name}_gamma_{gam}"] = row
     out["stability_mhd_cavity_20000_steps"] = stab
     return out
+
+
+# ---------------------------------------------------------------------------
+# two-dimensional lattices (D2Q9 + D2Q5)
+# ---------------------------------------------------------------------------
+D2 = {"nx": 4096, "ny": 4096}
+
+
+def channel2d_solver(storage: str, mhd: bool, nx: int = D2["nx"], ny: int = D2["ny"], Ha: float = 10.0,
+                     gamma: float = 0.1, nu: float = 0.01, F: float = 1e-6, variant: int = 0):
+    """2D Hartmann channel (the Sec. 5 physics on the D2Q9 + D2Q5 lattices):
+    x periodic, walls on y, B0 along y, nu = eta, chi = 0.01, uniform F_x."""
+    from paper_0809_4730_gb300.glbe import Solver2D
+    kw = dict(wall_lo=(0, 1), wall_hi=(0, 1), gamma=gamma, nu=nu, F=(F, 0.0), storage=storage, variant=variant)
+    if mhd:
+        L = (ny - 2) / 2
+        kw.update(induction=1, gamma_m=gamma, eta=nu, chi=0.01, mu=1.0, B0=(0.0, Ha * nu / L))
+    return Solver2D(nx, ny, **kw), nx * (ny - 2)
+
+
+def bytes_per_node_2d(storage: str, mhd: bool) -> int:
+    vb = {"f32": 4, "bf16": 2, "f32c": 6}[storage]
+    return 9 * vb * 2 + ((10 * vb * 2 + 2 * 4 * 2) if mhd else 0)
+
+
+def cpu_baseline_2d(target_s: float = 10.0):
+    """The 2D oracle on a bounded sample: a 512 x 130 coupled channel."""
+    from oracle import d2
+    cores = os.cpu_count() or 1
+    S = d2.Solver2(d2.Config2(512, 130, wall_lo=(0, 1), wall_hi=(0, 1), gamma=0.1, nu=0.01, F=(1e-6, 0),
+                              induction=True, gamma_m=0.1, eta=0.01, chi=0.01, mu=1.0, B0=(0, 10 * 0.01 / 64)))
+    t0 = time.perf_counter()
+    S.run(10)
+    dt = max(1e-6, time.perf_counter() - t0)
+    n = max(10, min(20_000, int(target_s / (dt / 10))))
+    t0 = time.perf_counter()
+    S.run(n)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * 512 * 128 / dt / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"512x130 coupled D2Q9+D2Q5 channel, {n} time steps, {dt:.1f} s"}
+
+
+def run_2d(args, rank, ws):
+    """The 2D forms (D2Q9 GLBE + D2Q5 induction): MLUPS and HBM roofline of
+    the fused step on a 4096 x 4096 Hartmann channel (F32, BF16, F32C; with
+    and without the induction lattice), and steps and device time to
+    r <= 1e-8 on the 64 x 64 Hartmann cross-section of config 2 at
+    gamma = 1, 0.1, 0.05 (F32C) with the error against the analytic profile
+    and, in the CPU leg, against the converged FP64 oracle."""
+    from paper_0809_4730_gb300.glbe import GlbeError
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm = 6800.0
+    forms = {}
+    nx2, ny2 = args.nx or D2["nx"], args.ny or D2["ny"]
+    for key in args.forms2d.split(","):
+        parts = key.split("_")          # storage_kind[_vN]
+        st, mhd = parts[0], parts[1] == "mhd"
+        var = int(parts[2][1:]) if len(parts) > 2 else 0
+        G, fluid = channel2d_solver(st, mhd, nx=nx2, ny=ny2, variant=var)
+        G.step(10 * args.warmup)
+        G.sync()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            total_ms, plain_ms, nplain = timed_steps(G, args.steps, stream)
+        kern_ms = plain_ms / nplain
+        bpn = bytes_per_node_2d(st, mhd)
+        achieved = bpn * fluid / (kern_ms * 1e-3) / 1e9
+        forms[key] = {
+            "mlups": round(10 * args.steps * fluid / (total_ms * 1e-3) / 1e6, 1),
+            "ms_per_step": round(total_ms / args.steps, 4), "kernel_ms": round(kern_ms, 5),
+            "bytes_per_node": bpn, "achieved_gbs": round(achieved, 1), "frac": round(achieved / hbm, 4),
+            "clocks": clk.summary()}
+        print(f"2d {key}: {forms[key]}", file=sys.stderr, flush=True)
+        G.close()
+    head = forms.get("f32_mhd") or next(iter(forms.values()))
+    kernels = {k: ("step2d_pair_kernel" if (k.split("_")[0] in ("f32", "bf16") and k.endswith("_v2"))
+                   else "step2d_kernel") for k in forms}
+    line = {"metric": "MLUPS of the fused D2Q9 + D2Q5 step (lagged Lorentz force)", "value": head["mlups"],
+            "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": f"2D Hartmann channel {nx2}x{ny2}, Ha=10, gamma=0.1, Pr_m=0.01, "
+                                   f"F32 storage", "l2": "state larger than L2 (2.9 GB at 4096x4096), no flush"},
+            "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": head["frac"], "bytes_per_node": head["bytes_per_node"],
+                         "kernel_ms": head["kernel_ms"], "traffic": None,
+                         "kernel": kernels.get("f32_mhd", "step2d_kernel")},
+            "gpu_launches": 11 * args.steps, "clocks": head["clocks"], "forms": forms}
+    if args.no_tts:
+        return line
+    # time to r <= 1e-8 on the 2D cross-section of the Hartmann duct of
+    # config 2 (64 x 64, walls on y, Ha = 10, Pr_m = 0.01; x-invariant steady state)
+    ny, Ha = 64, 10.0
+    L = (ny - 2) / 2
+    y = np.arange(ny) - (ny - 1) / 2
+    A = 1e-6 * L ** 2 / (0.01 * Ha * np.tanh(Ha))
+    ua = A * (1 - np.cosh(Ha * y / L) / np.cosh(Ha))
+    tts, cols = {}, {}
+    for gamma in (1.0, 0.1, 0.05):
+        G, _ = channel2d_solver("f32c", True, nx=64, ny=ny, gamma=gamma)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        try:
+            st, steps, r = G.solve(1e-8, 2_000_000)
+        except GlbeError as e:            # a diverged march is a result, not a failure of the bench
+            st, steps, r = e.status, G.t, float("nan")
+        e1.record(stream)
+        e1.synchronize()
+        _, u, _ = G.fields()
+        ux = u[0].reshape(ny, 64).double().cpu().numpy()
+        cols[gamma] = ux
+        err = float(np.abs(ux[1:-1] - ua[1:-1, None]).max() / ua.max())
+        tts[f"gamma_{gamma}"] = {"status": st, "steps": steps, "r": r,
+                                 "seconds": round(e0.elapsed_time(e1) / 1e3, 4), "error_vs_analytic": err}
+        print(f"2d tts gamma {gamma}: {tts[f'gamma_{gamma}']}", file=sys.stderr, flush=True)
+        G.close()
+    for gamma in (0.1, 0.05):
+        a, b = tts[f"gamma_{gamma}"], tts["gamma_1.0"]
+        if a["status"] == 0 and b["status"] == 0:
+            a["gain_steps_vs_gamma_1"] = round(b["steps"] / a["steps"], 2)
+            a["gain_time_vs_gamma_1"] = round(b["seconds"] / a["seconds"], 2)
+    line["time_to_1e-8_hartmann_64x64"] = tts
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import d2
+        line["cpu_baseline"] = cpu_baseline_2d()
+        S = d2.Solver2(d2.Config2(1, ny, wall_lo=(0, 1), wall_hi=(0, 1), gamma=0.1, nu=0.01, F=(1e-6, 0),
+                                  induction=True, gamma_m=0.1, eta=0.01, chi=0.01, mu=1.0, B0=(0, Ha * 0.01 / L)))
+        t0 = time.perf_counter()
+        S.run(3_000_000, tol=1e-8)
+        t8, w8 = S.t, time.perf_counter() - t0
+        S.run(3_000_000, tol=1e-12)
+        _, ou, _ = S.fields()
+        ref = ou[1:-1, 0]
+        tts["gamma_0.1"]["error_vs_oracle"] = float(np.abs(cols[0.1][1:-1] - ref[:, None]).max() / np.abs(ref).max())
+        tts["oracle_column_gamma_0.1"] = {"steps_1e-8": t8, "seconds_1e-8": round(w8, 3)}
+    return line
 
 
 ADJ_NU = 0.05   # nu = eta of the adjoint workload (0.01 diverged at gamma = 0.1: u_max 0.04, Re ~ 500)
@@ -1224,6 +1436,11 @@ def main():
         line = run_tts(args, rank, ws)
     elif args.workload == "adjoint":
         line = run_adjoint(args, rank, ws)
+    elif args.workload == "2d":
+        line = run_2d(args, rank, ws)
+    elif args.workload == "cpu-configs":
+        line = {"metric": "FP64 oracle on the small configurations (CPU baseline)", "data": "synthetic",
+                "cpu_baseline": cpu_configs()}
     elif ws > 1 and not args.replicas:
         line = run_sharded(args, rank, ws)
     else:

@@ -1,4 +1,5 @@
-"""Python binding of the C-ABI in include/glbe.h (argument marshalling only).
+"""Python binding of the C-ABI in include/glbe.h and include/glbe2d.h
+(argument marshalling only).
 
 Every step of the time march runs in the CUDA library ``libglbe.so``; this
 module loads it with ctypes, mirrors its structs and exposes the entry points
@@ -58,7 +59,23 @@ class glbe_batch_result(C.Structure):
                 ("nonfinite", C.c_int)]
 
 
-# Every symbol include/glbe.h declares, with (restype, argtypes).
+class glbe2d_params(C.Structure):
+    """Mirror of glbe2d_params (include/glbe2d.h)."""
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("wall_lo", C.c_int * 2), ("wall_hi", C.c_int * 2),
+        ("rho0", C.c_double), ("gamma", C.c_double), ("nu", C.c_double),
+        ("s", C.c_double * 9), ("F", C.c_double * 2),
+        ("force_field", C.c_int), ("induction", C.c_int),
+        ("gamma_m", C.c_double), ("eta", C.c_double), ("chi", C.c_double), ("mu", C.c_double),
+        ("B0", C.c_double * 2),
+        ("storage", C.c_int),
+        ("stream", C.c_void_p),
+        ("variant", C.c_int),
+    ]
+
+
+# Every symbol include/glbe.h and include/glbe2d.h declare, with (restype, argtypes).
 _P = C.POINTER
 _SIGNATURES = {
     "glbe_params_default": (None, [_P(glbe_params)]),
@@ -103,6 +120,20 @@ _SIGNATURES = {
                                       C.c_void_p, _P(C.c_long), _P(C.c_double)]),
     "glbe_adjoint_unrolled": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_long, C.c_void_p, C.c_size_t,
                                         C.c_void_p]),
+    "glbe2d_params_default": (None, [_P(glbe2d_params)]),
+    "glbe2d_workspace_bytes": (C.c_int, [_P(glbe2d_params), _P(C.c_size_t)]),
+    "glbe2d_init": (C.c_int, [_P(glbe2d_params), C.c_void_p, C.c_size_t, _P(C.c_void_p)]),
+    "glbe2d_set_force": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "glbe2d_step_n": (C.c_int, [C.c_void_p, C.c_long]),
+    "glbe2d_residual": (C.c_int, [C.c_void_p, _P(glbe_residual_info)]),
+    "glbe2d_history": (C.c_int, [C.c_void_p, _P(glbe_residual_info), C.c_long, _P(C.c_long)]),
+    "glbe2d_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_long, _P(C.c_long), _P(C.c_double)]),
+    "glbe2d_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "glbe2d_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "glbe2d_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_long]),
+    "glbe2d_time": (C.c_int, [C.c_void_p, _P(C.c_long)]),
+    "glbe2d_sync": (C.c_int, [C.c_void_p]),
+    "glbe2d_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -307,6 +338,179 @@ def glbe_adjoint_unrolled(ctx, d_w, nsteps: int, K: int, work, d_dQdF):
     _check(load().glbe_adjoint_unrolled(ctx, _ptr(d_w), int(nsteps), int(K), _ptr(work),
                                         work.numel() * work.element_size(), _ptr(d_dQdF)),
            "glbe_adjoint_unrolled")
+
+
+# -- two-dimensional lattices (include/glbe2d.h) ------------------------------
+def glbe2d_params_default() -> glbe2d_params:
+    p = glbe2d_params()
+    load().glbe2d_params_default(C.byref(p))
+    return p
+
+
+def glbe2d_workspace_bytes(p: glbe2d_params) -> int:
+    n = C.c_size_t(0)
+    _check(load().glbe2d_workspace_bytes(C.byref(p), C.byref(n)), "glbe2d_workspace_bytes")
+    return n.value
+
+
+def glbe2d_init(p: glbe2d_params, workspace) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(load().glbe2d_init(C.byref(p), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              C.byref(ctx)), "glbe2d_init")
+    return ctx
+
+
+def glbe2d_set_force(ctx, d_F):
+    _check(load().glbe2d_set_force(ctx, _ptr(d_F)), "glbe2d_set_force")
+
+
+def glbe2d_step_n(ctx, n: int):
+    _check(load().glbe2d_step_n(ctx, int(n)), "glbe2d_step_n")
+
+
+def glbe2d_residual(ctx) -> glbe_residual_info:
+    info = glbe_residual_info()
+    _check(load().glbe2d_residual(ctx, C.byref(info)), "glbe2d_residual")
+    return info
+
+
+def glbe2d_history(ctx, cap: int = 4096):
+    arr = (glbe_residual_info * cap)()
+    n = C.c_long(0)
+    _check(load().glbe2d_history(ctx, arr, cap, C.byref(n)), "glbe2d_history")
+    return [arr[i] for i in range(n.value)]
+
+
+def glbe2d_solve(ctx, tol: float, max_steps: int):
+    """Returns (status, steps, r); GLBE_ERR_TIMEOUT is returned, not raised."""
+    steps, r = C.c_long(0), C.c_double(0.0)
+    st = load().glbe2d_solve(ctx, float(tol), int(max_steps), C.byref(steps), C.byref(r))
+    if st not in (GLBE_OK, GLBE_ERR_TIMEOUT):
+        _check(st, "glbe2d_solve")
+    return st, steps.value, r.value
+
+
+def glbe2d_fields(ctx, d_rho, d_u, d_B):
+    _check(load().glbe2d_fields(ctx, _ptr(d_rho), _ptr(d_u), _ptr(d_B)), "glbe2d_fields")
+
+
+def glbe2d_get_state(ctx, d_df, d_dg, d_FL):
+    _check(load().glbe2d_get_state(ctx, _ptr(d_df), _ptr(d_dg), _ptr(d_FL)), "glbe2d_get_state")
+
+
+def glbe2d_set_state(ctx, d_df, d_dg, d_FL, t: int):
+    _check(load().glbe2d_set_state(ctx, _ptr(d_df), _ptr(d_dg), _ptr(d_FL), int(t)), "glbe2d_set_state")
+
+
+def glbe2d_time(ctx) -> int:
+    t = C.c_long(0)
+    _check(load().glbe2d_time(ctx, C.byref(t)), "glbe2d_time")
+    return t.value
+
+
+def glbe2d_sync(ctx):
+    _check(load().glbe2d_sync(ctx), "glbe2d_sync")
+
+
+def glbe2d_destroy(ctx):
+    if ctx:
+        load().glbe2d_destroy(ctx)
+
+
+def make_params2d(nx, ny, **kw) -> glbe2d_params:
+    """glbe2d_params from keyword arguments named as its fields (storage may
+    be "f32", "bf16" or "f32c"; s overrides the 9 rates)."""
+    p = glbe2d_params_default()
+    p.nx, p.ny = int(nx), int(ny)
+    for key, val in kw.items():
+        if key in ("wall_lo", "wall_hi", "F", "B0"):
+            arr = getattr(p, key)
+            for d in range(2):
+                arr[d] = type(arr[d])(val[d])
+        elif key == "s":
+            for k in range(9):
+                p.s[k] = float(val[k])
+        elif key == "storage":
+            p.storage = STORAGE[val] if isinstance(val, str) else int(val)
+        elif key in ("induction", "force_field", "variant"):
+            setattr(p, key, int(val))
+        else:
+            setattr(p, key, float(val))
+    return p
+
+
+class Solver2D:
+    """One D2Q9 (+ D2Q5) lattice context on a CUDA device; keyword arguments
+    as the fields of ``glbe2d_params``."""
+
+    def __init__(self, nx, ny, *, device="cuda", stream=None, **kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        p = make_params2d(nx, ny, **kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        p.stream = C.c_void_p(self.stream.cuda_stream)
+        self.params = p
+        self.N = p.nx * p.ny
+        self.workspace = torch.empty(glbe2d_workspace_bytes(p), dtype=torch.uint8, device=self.device)
+        self.ctx = glbe2d_init(p, self.workspace)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            glbe2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def induction(self) -> bool:
+        return bool(self.params.induction)
+
+    def set_force(self, F):
+        glbe2d_set_force(self.ctx, F.contiguous())
+
+    def step(self, n: int):
+        glbe2d_step_n(self.ctx, n)
+
+    def residual(self) -> glbe_residual_info:
+        return glbe2d_residual(self.ctx)
+
+    def history(self, cap: int = 4096):
+        return glbe2d_history(self.ctx, cap)
+
+    def solve(self, tol: float, max_steps: int):
+        return glbe2d_solve(self.ctx, tol, max_steps)
+
+    @property
+    def t(self) -> int:
+        return glbe2d_time(self.ctx)
+
+    def fields(self):
+        torch = self.torch
+        rho = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        u = torch.empty(2, self.N, dtype=torch.float32, device=self.device)
+        B = torch.empty(2, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        glbe2d_fields(self.ctx, rho, u, B)
+        return rho, u, B
+
+    def get_state(self):
+        torch = self.torch
+        df = torch.empty(9, self.N, dtype=torch.float32, device=self.device)
+        dg = torch.empty(10, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        FL = torch.empty(2, self.N, dtype=torch.float32, device=self.device) if self.induction else None
+        glbe2d_get_state(self.ctx, df, dg, FL)
+        return df, dg, FL
+
+    def set_state(self, df, dg=None, FL=None, t: int = 0):
+        glbe2d_set_state(self.ctx, df.contiguous(), None if dg is None else dg.contiguous(),
+                         None if FL is None else FL.contiguous(), t)
+
+    def sync(self):
+        glbe2d_sync(self.ctx)
 
 
 def make_params(nx, ny, nz, **kw) -> glbe_params:

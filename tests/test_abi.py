@@ -11,10 +11,10 @@ import pytest
 from conftest import ROOT
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "glbe.h")).read()
+def declared_functions(header="glbe.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(glbe_[a-z_0-9]+)\s*\(", src)
+    names = re.findall(r"\b(glbe(?:2d)?_[a-z_0-9]+)\s*\(", src)
     return sorted(set(names))
 
 
@@ -30,6 +30,15 @@ def test_library_exports_every_declared_symbol(lib):
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), f"{n} declared in glbe.h but not exported"
+        assert n in glbe._SIGNATURES, f"{n} has no Python binding"
+
+
+def test_library_exports_every_2d_symbol(lib):
+    from paper_0809_4730_gb300 import glbe
+    names = declared_functions("glbe2d.h")
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in glbe2d.h but not exported"
         assert n in glbe._SIGNATURES, f"{n} has no Python binding"
 
 
@@ -107,3 +116,61 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.glbe_step_n(None, 1) == glbe.GLBE_ERR_ARG
     assert lib.glbe_sync(None) == glbe.GLBE_ERR_ARG
     lib.glbe_destroy(None)
+
+
+# -- the 2D entry points (include/glbe2d.h) -----------------------------------
+def _params2d(**kw):
+    from paper_0809_4730_gb300 import glbe
+    return glbe.make_params2d(kw.pop("nx", 12), kw.pop("ny", 10), nu=kw.pop("nu", 0.05), **kw)
+
+
+def test_2d_struct_and_defaults(lib):
+    from paper_0809_4730_gb300 import glbe
+    p = glbe.glbe2d_params_default()
+    assert list(p.s) == [1.0, 1.63, 1.14, 1.0, 1.92, 1.0, 1.92, 1.0, 1.0]
+    assert p.rho0 == 1.0 and p.gamma == 1.0 and p.gamma_m == 1.0 and p.storage == glbe.GLBE_F32
+    assert p.chi == 1.0 and p.mu == 1.0 and p.induction == 0 and p.force_field == 0
+
+
+def test_2d_workspace_bytes_scales_with_storage_and_induction(lib):
+    from paper_0809_4730_gb300 import glbe
+    N = 12 * 10
+    b32 = glbe.glbe2d_workspace_bytes(_params2d())
+    b16 = glbe.glbe2d_workspace_bytes(_params2d(storage="bf16"))
+    bc = glbe.glbe2d_workspace_bytes(_params2d(storage="f32c"))
+    bm = glbe.glbe2d_workspace_bytes(_params2d(induction=1, gamma_m=0.5, eta=0.01, chi=0.1))
+    bf = glbe.glbe2d_workspace_bytes(_params2d(force_field=2))
+    assert b32 >= 2 * 9 * N * 4 + 4 * N * 4
+    assert b32 - b16 >= 2 * 9 * N * 2 - 1024
+    assert bc - b32 >= 2 * 9 * N * 2 - 1024
+    assert bm - b32 >= 2 * 10 * N * 4 + 2 * N * 4
+    assert bf - b32 >= 2 * N * 4
+
+
+@pytest.mark.parametrize("bad", [
+    dict(gamma=0.0), dict(gamma=1.5), dict(nu=0.0), dict(nx=0),
+    dict(wall_lo=(0, 1), wall_hi=(0, 1), ny=2), dict(wall_lo=(1, 0), wall_hi=(1, 0), nx=2),
+    dict(induction=1, gamma_m=0.5, eta=0.0, chi=1.0), dict(induction=1, gamma_m=1.5, eta=0.1),
+    dict(induction=1, gamma_m=0.5, eta=0.01, chi=0.0), dict(force_field=1), dict(force_field=3),
+    dict(storage=2), dict(storage=4), dict(s=[1.0, 2.0, 1.14, 1.0, 1.92, 1.0, 1.92, 1.0, 1.0]),
+])
+def test_2d_invalid_parameters_are_rejected(lib, bad):
+    from paper_0809_4730_gb300 import glbe
+    with pytest.raises(glbe.GlbeError) as ei:
+        glbe.glbe2d_workspace_bytes(_params2d(**bad))
+    assert ei.value.status == glbe.GLBE_ERR_ARG
+    assert lib.glbe_last_error()
+
+
+def test_2d_init_rejects_null_and_small_workspace_and_null_context(lib):
+    from paper_0809_4730_gb300 import glbe
+    p = _params2d()
+    ctx = C.c_void_p()
+    assert lib.glbe2d_init(C.byref(p), None, 1 << 20, C.byref(ctx)) == glbe.GLBE_ERR_ARG
+    assert not ctx.value
+    assert lib.glbe2d_init(C.byref(p), C.c_void_p(0x1001), 1 << 30, C.byref(ctx)) == glbe.GLBE_ERR_ARG
+    assert lib.glbe2d_init(C.byref(p), C.c_void_p(0x100000), 16, C.byref(ctx)) == glbe.GLBE_ERR_ARG
+    assert lib.glbe2d_step_n(None, 1) == glbe.GLBE_ERR_ARG
+    assert lib.glbe2d_sync(None) == glbe.GLBE_ERR_ARG
+    assert lib.glbe2d_set_force(None, None) == glbe.GLBE_ERR_ARG
+    lib.glbe2d_destroy(None)

@@ -39,7 +39,7 @@ MUTATIONS = [
      "double coef = 1.0 / (p->mu * p->chi * orc_tau_m(p) * THETA_M);", "current_density"),
     ("Lorentz force operands transposed", "FL[0] = J[1]*B[2] - J[2]*B[1];", "FL[0] = J[2]*B[1] - J[1]*B[2];",
      "hartmann_profile"),
-    ("bounce-back into the same slot", "fn[n*19 + opp19[a]] = ft[a];", "fn[n*19 + a] = ft[a];",
+    ("bounce-back into the same slot", "fn[n*19 + opp19[a]] = ft[a] - wall;", "fn[n*19 + a] = ft[a] - wall;",
      "poiseuille_exact or mrt_with_equal_rates"),
     ("anti-bounce-back sign", "gn[n*21 + j*7 + opp7[a]] = -gt[j*7+a] + 2.0*W7(a)*p->B0[j];",
      "gn[n*21 + j*7 + opp7[a]] = gt[j*7+a];", "hartmann_profile"),
