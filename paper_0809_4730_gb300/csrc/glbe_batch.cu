@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
     // with the error flag set instead of hanging
     if ((int)blockIdx.x == absent_block) return;
     __shared__ StepParams sp;
-    __shared__ int cur_dom;
-    if (threadIdx.x == 0) cur_dom = -1;
+    // the domain whose parameters sp holds: the same in every thread (a tile
+    // belongs to one domain), so the check needs no shared flag and a block
+    // synchronises only when it moves to another domain
+    int cur_dom = -1;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start_ns = globaltimer_ns();
     long long last_snap = snap_level;
     for (long long s = 0; s < nsteps; ++s) {
@@ -138,15 +140,16 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
             const bool active = __ldcg(&ds[d].active) != 0;
             float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (active) {
-                __syncthreads();
                 if (cur_dom != d) {
-                    // the block's copy of the domain's step parameters
+                    // the block's copy of the domain's step parameters (after
+                    // every thread is done with the previous domain's)
+                    __syncthreads();
                     const int words = (int)(sizeof(StepParams) / 4);
                     for (int w = threadIdx.x; w < words; w += BT)
                         reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&D.p)[w];
+                    __syncthreads();
+                    cur_dom = d;
                 }
-                __syncthreads();
-                if (threadIdx.x == 0) cur_dom = d;
                 StepBuffers b{};
                 const int par = (int)(t & 1);
                 b.fsrc = D.f[par];
