@@ -1647,6 +1647,26 @@ constexpr int step_dense_blocks()
     return (base_storage(ST) == ST_BF16 || base_storage(ST) == ST_F16) ? 5 : 0;   // 0: the free kernel
 }
 
+// The coupled compensated step in two passes per thread (the batch's form):
+// pass 1 gathers f and g, runs the induction part and writes g~ and this
+// step's Lorentz force; pass 2 gathers f again (from L1 / L2) and runs the
+// flow update with F = F_ext + F_L.  The arithmetic and its order are the
+// one-pass update's, so the result is bit for bit the same, but the
+// registers of the two parts are not live together: 172 registers in one
+// pass (one block of 256 per SM) against at most 128 here.
+template <int ST, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS, 2)
+    step_kernel_coupled2(const StepParams p, const StepBuffers b, const FieldOut fo)
+{
+    if (b.stop != nullptr && *b.stop) return;
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
+    coupled_induction_pass<ST, false>(p, b, i);
+    scalar_node_step<ST, false, MODE, false, false, true>(p, b, fo, i, acc);
+    if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
+}
+
 // The update of the fluid node pair (n0, n0 + 1) from its gathered
 // pre-collision populations (packed FP32x2): the counterpart of
 // node_from_sources for two nodes; adds the pair's residual terms to acc.
@@ -2035,6 +2055,9 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             static const long long wave = resident_wave(step_kernel_dense<ST, MINB>, STEP_THREADS);
             b.pf_ahead = wave;
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+        } else if (MHD && ST == ST_F32C && MODE != MODE_FIELDS && p.variant == 0) {
+            if constexpr (MHD && ST == ST_F32C && MODE != MODE_FIELDS)
+                step_kernel_coupled2<ST, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         } else {
             static const long long wave = resident_wave(step_kernel<ST, MHD, MODE>, STEP_THREADS);
             b.pf_ahead = (MHD || MODE == MODE_STEP_RESID) ? wave / 2 : wave;

@@ -227,6 +227,31 @@ def test_tile_kernel_matches_one_node_kernel_bitwise(orc, nx, storage, mhd):
     assert abs(r1.mass - r3.mass) <= 1e-9 * r1.mass
 
 
+# The coupled compensated step runs in two passes per thread (induction,
+# then flow with this step's Lorentz force) under the automatic choice: the
+# one-pass arithmetic in the same order, bit for bit, with walls on y and z
+# (general-path nodes), the x seam, a force field and two residual levels.
+@pytest.mark.parametrize("nx,walls", [(37, ((0, 1, 1), (0, 1, 0))), (64, ((1, 1, 0), (0, 1, 1)))])
+def test_coupled_two_pass_matches_one_pass_bitwise(orc, nx, walls):
+    from paper_0809_4730_gb300.inputs import random_force
+    cfg = _cfg(orc, True, gamma=0.3, nx=nx, ny=11, nz=9, wall_lo=walls[0], wall_hi=walls[1])
+    Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=31)
+    S, G0 = make_pair(orc, cfg, Fext=Fext, storage="f32c", variant=0)
+    _, G1 = make_pair(orc, cfg, Fext=Fext, storage="f32c", variant=1)
+    _perturb(S, 29)
+    push_oracle_state(S, G0)
+    push_oracle_state(S, G1)
+    G0.step(23)
+    G1.step(23)
+    for a, b in zip(gpu_state(G0), gpu_state(G1)):
+        assert np.array_equal(a, b)
+    r0, r1 = G0.residual(), G1.residual()
+    assert r0.t == r1.t == 20
+    assert (r0.num, r0.den, r0.mass) == (r1.num, r1.den, r1.mass)
+    for a, b in zip(gpu_fields(G0), gpu_fields(G1)):
+        assert np.array_equal(a, b)
+
+
 # Variant 4: the tile kernel with two x-adjacent nodes per consumer thread
 # runs the paired kernel's packed FP32x2 update on the same gathered values:
 # bit-identical to variant 2.
