@@ -100,17 +100,6 @@ __device__ bool grid_barrier(BatchState* st, long long spin_limit)
     return ok;
 }
 
-// Domain of a tile (tile_start is ascending, ndom + 1 entries).
-__device__ __forceinline__ int tile_domain(const uint32_t* __restrict__ tile_start, int ndom, uint32_t tile)
-{
-    int lo = 0, hi = ndom;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (tile_start[mid] <= tile) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 template <int ST, int BT>
 __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* __restrict__ doms, int ndom,
                                                    const uint32_t* __restrict__ tile_start, uint32_t ntiles,
@@ -134,24 +123,22 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
         const long long t = t0 + s;
         const bool resid = (t % 10) == 0;
         const bool have_snap = resid && last_snap >= 0 && last_snap == t - 10;
+        const int par = (int)(t & 1);
+        // the block's tiles ascend, and so do the domains' tile ranges: the
+        // domain of the next tile is found by advancing a cursor, and the
+        // domain's buffers and active flag (which changes only between
+        // levels) are read once per domain and level
+        int d = 0, lvl_dom = -1;
+        bool active = false;
+        StepBuffers b{};
+        uint32_t tile0 = 0;
+        bool mhd = false;
         for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int d = tile_domain(tile_start, ndom, tile);
-            const BatchDomain& D = doms[d];
-            const bool active = __ldcg(&ds[d].active) != 0;
-            float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (active) {
-                if (cur_dom != d) {
-                    // the block's copy of the domain's step parameters (after
-                    // every thread is done with the previous domain's)
-                    __syncthreads();
-                    const int words = (int)(sizeof(StepParams) / 4);
-                    for (int w = threadIdx.x; w < words; w += BT)
-                        reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&D.p)[w];
-                    __syncthreads();
-                    cur_dom = d;
-                }
-                StepBuffers b{};
-                const int par = (int)(t & 1);
+            while (__ldg(tile_start + d + 1) <= tile) ++d;
+            if (d != lvl_dom) {
+                lvl_dom = d;
+                const BatchDomain& D = doms[d];
+                active = __ldcg(&ds[d].active) != 0;
                 b.fsrc = D.f[par];
                 b.fdst = D.f[par ^ 1];
                 b.gsrc = D.g[par];
@@ -160,14 +147,29 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
                 b.usnap = D.usnap;
                 b.snap_lo = 1;
                 b.have_snap = have_snap ? 1 : 0;
+                tile0 = __ldg(tile_start + d);
+                mhd = D.mhd != 0;
+            }
+            float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (active) {
+                if (cur_dom != d) {
+                    // the block's copy of the domain's step parameters (after
+                    // every thread is done with the previous domain's)
+                    __syncthreads();
+                    const int words = (int)(sizeof(StepParams) / 4);
+                    for (int w = threadIdx.x; w < words; w += BT)
+                        reinterpret_cast<int*>(&sp)[w] = reinterpret_cast<const int*>(&doms[d].p)[w];
+                    __syncthreads();
+                    cur_dom = d;
+                }
                 const FieldOut fo{nullptr, nullptr, nullptr};
-                const uint32_t i = (tile - tile_start[d]) * BT + threadIdx.x;
+                const uint32_t i = (tile - tile0) * BT + threadIdx.x;
                 // populations written by other blocks earlier in this launch:
                 // coherent (L2) loads.  A coupled node is updated in two passes
                 // (induction, then flow with this step's Lorentz force), each
                 // within the kernel's register budget; the one-pass update
                 // spilled over a kilobyte per thread.
-                if (D.mhd) {
+                if (mhd) {
                     coupled_induction_pass<ST, true>(sp, b, i);
                     if (resid) scalar_node_step<ST, false, MODE_STEP_RESID, true, false, true>(sp, b, fo, i, acc);
                     else scalar_node_step<ST, false, MODE_STEP, true, false, true>(sp, b, fo, i, acc);
