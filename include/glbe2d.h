@@ -77,11 +77,13 @@ typedef struct {
     double B0[2];             /* applied in-plane field: initial state and wall value */
     int storage;              /* GLBE_F32, GLBE_BF16 or GLBE_F32C (glbe_storage)      */
     void* stream;             /* cudaStream_t owned by the caller                    */
-    int variant;              /* kernel form: 0 = automatic (one node per thread); 1 = one node per
-                                 thread; 2 = two x-adjacent nodes per thread with vector loads and
+    int variant;              /* kernel form: 0 = automatic (one node per thread, the plain step held
+                                 to more resident blocks where that measured faster); 1 = one node
+                                 per thread, free register allocation; 2 = two x-adjacent nodes per
+                                 thread with vector loads and
                                  lane shuffles where x is periodic, nx even and the storage F32 or
-                                 BF16 (else one node).  Both forms give the same state bit for bit;
-                                 the residual sums agree to FP32 round-off */
+                                 BF16 (else one node).  All forms give the same state bit for bit;
+                                 the residual sums of form 2 agree to FP32 round-off */
 } glbe2d_params;
 
 /* Defaults: rho0 = 1, gamma = gamma_m = 1, chi = mu = 1, the D2Q9 kinetic

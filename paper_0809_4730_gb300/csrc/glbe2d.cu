@@ -574,7 +574,7 @@ __device__ __forceinline__ void block_partials2(const float (&acc)[7], double* p
 
 // One node per thread: any geometry.
 template <int ST, bool MHD, int MODE>
-__global__ void __launch_bounds__(T2D) step2d_kernel(const P2 p, const B2 b, const Out2 o)
+__device__ __forceinline__ void step2d_body(const P2& p, const B2& b, const Out2& o)
 {
     if (b.stop && *b.stop) return;   // the march converged in an earlier launch of this chunk
     const int n = blockIdx.x * T2D + threadIdx.x;
@@ -645,6 +645,31 @@ __global__ void __launch_bounds__(T2D) step2d_kernel(const P2 p, const B2 b, con
         }
     }
     if constexpr (MODE == M2_RESID) block_partials2(acc, b.partials);
+}
+
+template <int ST, bool MHD, int MODE>
+__global__ void __launch_bounds__(T2D) step2d_kernel(const P2 p, const B2 b, const Out2 o)
+{
+    step2d_body<ST, MHD, MODE>(p, b, o);
+}
+
+// The plain step held to MINB resident blocks of 256 per SM (measured on the
+// 4096^2 channel against the free allocation): F32 coupled 4 (64 registers,
+// 36 B spilled; 0.86 against 0.78 of HBM), F32 flow 6 (40 registers, 20 B;
+// 0.80 against 0.78), F32C coupled 3 (80 registers, 64 B; 0.80 against
+// 0.70), F32C flow 5 (48 registers, 24 B; 0.77 against 0.76), BF16 flow 8
+// (32 registers, 16 B; 0.55 against 0.52).  BF16 coupled stays free (held to
+// 5 blocks it measured the same).  A kernel of its own: stating a minimum
+// changes the register allocation of the forms left free.
+template <int ST, bool MHD, int MINB>
+__global__ void __launch_bounds__(T2D, MINB) step2d_kernel_dense(const P2 p, const B2 b, const Out2 o)
+{
+    step2d_body<ST, MHD, M2_STEP>(p, b, o);
+}
+template <int ST, bool MHD>
+constexpr int dense2d_blocks()
+{
+    return ST == GLBE_F32 ? (MHD ? 4 : 6) : (ST == GLBE_BF16 ? (MHD ? 0 : 8) : (MHD ? 3 : 5));
 }
 
 // Two x-adjacent nodes per thread (x periodic, even nx; FP32 or BF16
@@ -1086,8 +1111,24 @@ cudaError_t launch2_t(glbe2d_ctx* c, int mode, const B2& b, const Out2& o, cudaS
         }
     }
     if (mode == M2_STEP) {
-        if (mhd) step2d_kernel<ST, true, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
-        else step2d_kernel<ST, false, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
+        constexpr int MBM = dense2d_blocks<ST, true>(), MBF = dense2d_blocks<ST, false>();
+        if (mhd) {
+            if constexpr (MBM > 0) {
+                if (c->prm.variant == 0) {
+                    step2d_kernel_dense<ST, true, MBM><<<nb, T2D, 0, st>>>(c->p, b, o);
+                    return cudaGetLastError();
+                }
+            }
+            step2d_kernel<ST, true, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
+        } else {
+            if constexpr (MBF > 0) {
+                if (c->prm.variant == 0) {
+                    step2d_kernel_dense<ST, false, MBF><<<nb, T2D, 0, st>>>(c->p, b, o);
+                    return cudaGetLastError();
+                }
+            }
+            step2d_kernel<ST, false, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
+        }
     } else if (mode == M2_RESID) {
         if (mhd) step2d_kernel<ST, true, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
         else step2d_kernel<ST, false, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);

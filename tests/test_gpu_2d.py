@@ -185,6 +185,28 @@ def test_pair_kernel_matches_one_node_kernel_bitwise(orc2, storage, mhd, nx, ny,
     assert rel_linf(df, odf, fluid) < (3e-2 if storage == "bf16" else 3e-5)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f32c", "bf16"])
+@pytest.mark.parametrize("mhd", [False, True])
+def test_dense_plain_step_matches_free_kernel_bitwise(orc2, storage, mhd):
+    """The automatic form's plain step held to more resident blocks (its
+    own kernel, the same body) against the free one-node kernel: the same
+    state and residual record bit for bit."""
+    cfg = _cfg(orc2, mhd, nx=70, ny=33, wall_lo=(1, 1), wall_hi=(0, 1))
+    F = _force(cfg, 9)
+    S, G0 = _pair(orc2, cfg, Fext=F, storage=storage, variant=0)
+    _, G1 = _pair(orc2, cfg, Fext=F, storage=storage, variant=1)
+    _perturb(S, 41)
+    _push(S, G0)
+    _push(S, G1)
+    G0.step(23)
+    G1.step(23)
+    for a, b in zip(_gpu_state(G0), _gpu_state(G1)):
+        if a is not None:
+            assert np.array_equal(a, b)
+    r0, r1 = G0.residual(), G1.residual()
+    assert (r0.t, r0.num, r0.den, r0.mass) == (r1.t, r1.num, r1.den, r1.mass)
+
+
 def test_step_parity_bf16(orc2):
     cfg = _cfg(orc2, True, gamma=0.5)
     S, G = _pair(orc2, cfg, Fext=_force(cfg, 3), storage="bf16")
