@@ -1644,7 +1644,9 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
 template <int ST>
 constexpr int step_dense_blocks()
 {
-    return (base_storage(ST) == ST_BF16 || base_storage(ST) == ST_F16) ? 5 : 0;   // 0: the free kernel
+    // 16-bit: 5 blocks (48 registers); F32C: 3 (80 registers, 32 B spilled);
+    // 0: the free kernel
+    return (base_storage(ST) == ST_BF16 || base_storage(ST) == ST_F16) ? 5 : (ST == ST_F32C ? 3 : 0);
 }
 
 // The coupled compensated step in two passes per thread (the batch's form):
