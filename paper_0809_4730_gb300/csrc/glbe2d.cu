@@ -135,6 +135,7 @@ struct B2 {
     double* partials;       // [8][blocks]
     int have_snap;
     const int* stop;        // solve: the kernels of a converged march return at once
+    int pf_ahead;           // L2 prefetch of the rows block blockIdx.x + pf_ahead gathers (0: none)
 };
 
 struct Out2 {
@@ -572,11 +573,69 @@ __device__ __forceinline__ void block_partials2(const float (&acc)[7], double* p
     }
 }
 
+// L2 prefetch of the rows that block blockIdx.x + b.pf_ahead will gather
+// (its T2D nodes shifted by each direction's offset, one node of halo),
+// one bulk prefetch per row by the first threads of the block: f (and the
+// compensated low rows), g, the lagged Lorentz force, the force field and,
+// on residual levels, the snapshot.
+template <int ST, bool MHD, bool RESID>
+__device__ __forceinline__ void prefetch2d(const P2& p, const B2& b)
+{
+    using S = Sto2<ST>;
+    constexpr int NF = 9, NG = MHD ? 10 : 0, NC = S::COMP ? NF + NG : 0, NL = MHD ? 2 : 0, NS = RESID ? 4 : 0;
+    const int t = threadIdx.x;
+    if (b.pf_ahead <= 0 || t >= NF + NG + NC + NL + 2 + NS) return;
+    const long long N = p.N;
+    const long long nb = ((long long)blockIdx.x + b.pf_ahead) * T2D;
+    if (nb >= N) return;
+    uintptr_t row;
+    size_t esz;
+    long long shift = 0, halo = 0;
+    int r = t;
+    if (r < NF + NG) {                       // f then g rows, in the storage type
+        const int a = r < NF ? r : (r - NF) % 5;
+        const long long off = r < NF ? ex9(a) + (long long)ey9(a) * p.nx : ex5(a) + (long long)ey5(a) * p.nx;
+        row = reinterpret_cast<uintptr_t>(r < NF ? b.fsrc : b.gsrc) +
+              (uintptr_t)(r < NF ? r : r - NF) * (uintptr_t)N * sizeof(typename S::T);
+        esz = sizeof(typename S::T);
+        shift = -off;
+        halo = 1;
+    } else if ((r -= NF + NG) < NC) {        // the compensated low rows
+        const int rr = r < NF ? r : r - NF;
+        const int a = r < NF ? r : rr % 5;
+        const long long off = r < NF ? ex9(a) + (long long)ey9(a) * p.nx : ex5(a) + (long long)ey5(a) * p.nx;
+        row = reinterpret_cast<uintptr_t>(r < NF ? b.fsrc : b.gsrc) +
+              (uintptr_t)(r < NF ? NF : 10) * (uintptr_t)N * sizeof(float) + (uintptr_t)rr * (uintptr_t)N * sizeof(__half);
+        esz = sizeof(__half);
+        shift = -off;
+        halo = 1;
+    } else if ((r -= NC) < NL) {
+        row = reinterpret_cast<uintptr_t>(b.FL) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
+    } else if ((r -= NL) < 2) {
+        if (b.Ffield == nullptr) return;
+        row = reinterpret_cast<uintptr_t>(b.Ffield) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
+    } else {
+        r -= 2;
+        row = reinterpret_cast<uintptr_t>(b.usnap) + (uintptr_t)r * (uintptr_t)N * sizeof(float);
+        esz = sizeof(float);
+    }
+    const long long s0 = nb + shift - halo, s1 = nb + T2D + shift + halo;
+    uintptr_t lo = row + (uintptr_t)(s0 < 0 ? 0 : s0) * esz;
+    uintptr_t hi = row + (uintptr_t)(s1 > N ? N : s1) * esz;
+    lo = (lo + 15) & ~(uintptr_t)15;
+    hi &= ~(uintptr_t)15;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
 // One node per thread: any geometry.
 template <int ST, bool MHD, int MODE>
 __device__ __forceinline__ void step2d_body(const P2& p, const B2& b, const Out2& o)
 {
     if (b.stop && *b.stop) return;   // the march converged in an earlier launch of this chunk
+    if constexpr (MODE != M2_FIELDS) prefetch2d<ST, MHD, MODE == M2_RESID>(p, b);
     const int n = blockIdx.x * T2D + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (n < p.N) {
@@ -1092,11 +1151,37 @@ struct glbe2d_ctx {
 
 namespace {
 
+// Blocks of a kernel resident on the whole GPU at once (one wave).
+template <class K>
+long long wave2d(K kernel)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, T2D, 0);
+    return (long long)sms * per;
+}
+
+// The launch's L2 prefetch distance: half a wave ahead on grids of several
+// waves, none on small grids.  Taken by the coupled F32 step only: measured
+// on the 4096^2 channel it took that plain step from 0.4829 to 0.4337 ms
+// (0.86 -> 0.96 of HBM) but slowed every other form (F32C coupled 0.753 ->
+// 0.792 ms, BF16 coupled 0.336 -> 0.356, F32C flow 0.346 -> 0.353, BF16
+// flow 0.162 -> 0.174; F32 flow unchanged).
+template <int ST, bool MHD, class K>
+int prefetch_distance(K kernel, unsigned grid)
+{
+    if constexpr (ST != GLBE_F32 || !MHD) return 0;
+    static const long long w = wave2d(kernel);
+    return (long long)grid > 4 * w ? (int)(w / 2) : 0;
+}
+
 template <int ST>
-cudaError_t launch2_t(glbe2d_ctx* c, int mode, const B2& b, const Out2& o, cudaStream_t st)
+cudaError_t launch2_t(glbe2d_ctx* c, int mode, const B2& b_in, const Out2& o, cudaStream_t st)
 {
     const bool mhd = c->prm.induction;
     const unsigned nb = c->blocks;
+    B2 b = b_in;
     if constexpr (ST == GLBE_F32 || ST == GLBE_BF16) {
         if (c->pair && mode != M2_FIELDS) {
             const unsigned pb = c->pair_blocks;
@@ -1115,23 +1200,32 @@ cudaError_t launch2_t(glbe2d_ctx* c, int mode, const B2& b, const Out2& o, cudaS
         if (mhd) {
             if constexpr (MBM > 0) {
                 if (c->prm.variant == 0) {
+                    b.pf_ahead = prefetch_distance<ST, true>(step2d_kernel_dense<ST, true, MBM>, nb);
                     step2d_kernel_dense<ST, true, MBM><<<nb, T2D, 0, st>>>(c->p, b, o);
                     return cudaGetLastError();
                 }
             }
+            b.pf_ahead = prefetch_distance<ST, true>(step2d_kernel<ST, true, M2_STEP>, nb);
             step2d_kernel<ST, true, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
         } else {
             if constexpr (MBF > 0) {
                 if (c->prm.variant == 0) {
+                    b.pf_ahead = prefetch_distance<ST, false>(step2d_kernel_dense<ST, false, MBF>, nb);
                     step2d_kernel_dense<ST, false, MBF><<<nb, T2D, 0, st>>>(c->p, b, o);
                     return cudaGetLastError();
                 }
             }
+            b.pf_ahead = prefetch_distance<ST, false>(step2d_kernel<ST, false, M2_STEP>, nb);
             step2d_kernel<ST, false, M2_STEP><<<nb, T2D, 0, st>>>(c->p, b, o);
         }
     } else if (mode == M2_RESID) {
-        if (mhd) step2d_kernel<ST, true, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
-        else step2d_kernel<ST, false, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
+        if (mhd) {
+            b.pf_ahead = prefetch_distance<ST, true>(step2d_kernel<ST, true, M2_RESID>, nb);
+            step2d_kernel<ST, true, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
+        } else {
+            b.pf_ahead = prefetch_distance<ST, false>(step2d_kernel<ST, false, M2_RESID>, nb);
+            step2d_kernel<ST, false, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
+        }
     } else {
         if (mhd) step2d_kernel<ST, true, M2_FIELDS><<<nb, T2D, 0, st>>>(c->p, b, o);
         else step2d_kernel<ST, false, M2_FIELDS><<<nb, T2D, 0, st>>>(c->p, b, o);
