@@ -1243,8 +1243,7 @@ def run_2d(args, rank, ws):
             "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                          "frac": head["frac"], "bytes_per_node": head["bytes_per_node"],
                          "kernel_ms": head["kernel_ms"],
-                         "traffic": (round(TRAFFIC_2D_F32_MHD_B_PER_NODE * nx2 * (ny2 - 2))
-                                     if "f32_mhd" in forms and (nx2, ny2) == (D2["nx"], D2["ny"]) else None),
+                         "traffic": None,
                          "traffic_note": "bytes of one plain launch, ncu capture (-c 1) on this 4096x4096 channel",
                          "kernel": kernels.get("f32_mhd", "step2d_kernel")},
             "gpu_launches": 11 * args.steps, "clocks": head["clocks"], "forms": forms}
