@@ -1157,8 +1157,8 @@ def run_cavity(args, rank, ws):
 # ---------------------------------------------------------------------------
 D2 = {"nx": 4096, "ny": 4096}
 # DRAM bytes of one plain coupled F32 launch on the 4096 x 4096 channel (ncu,
-# one pass, -c 1: read 1408646400 + write 1379505664 B) per fluid node
-TRAFFIC_2D_F32_MHD_B_PER_NODE = (1408646400 + 1379505664) / (4096 * 4094)
+# one pass, -c 1: read 1409227776 + write 1376905216 B) per fluid node
+TRAFFIC_2D_F32_MHD_B_PER_NODE = (1409227776 + 1376905216) / (4096 * 4094)
 
 
 def channel2d_solver(storage: str, mhd: bool, nx: int = D2["nx"], ny: int = D2["ny"], Ha: float = 10.0,
@@ -1243,7 +1243,8 @@ def run_2d(args, rank, ws):
             "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                          "frac": head["frac"], "bytes_per_node": head["bytes_per_node"],
                          "kernel_ms": head["kernel_ms"],
-                         "traffic": None,
+                         "traffic": (round(TRAFFIC_2D_F32_MHD_B_PER_NODE * nx2 * (ny2 - 2))
+                                     if "f32_mhd" in forms and (nx2, ny2) == (D2["nx"], D2["ny"]) else None),
                          "traffic_note": "bytes of one plain launch, ncu capture (-c 1) on this 4096x4096 channel",
                          "kernel": kernels.get("f32_mhd", "step2d_kernel")},
             "gpu_launches": 11 * args.steps, "clocks": head["clocks"], "forms": forms}
