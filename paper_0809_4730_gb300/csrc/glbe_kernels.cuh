@@ -1872,6 +1872,7 @@ template <int ST, int MODE>
 constexpr int pair_dense_blocks()
 {
     if (base_storage(ST) == ST_F16) return MODE == MODE_STEP ? 8 : 7;
+    if (ST == ST_F32) return MODE == MODE_STEP ? 4 : 0;   // 128 registers, 56 B spilled
     return base_storage(ST) == ST_BF16 ? 7 : 0;   // 0: the free kernel
 }
 
@@ -1888,7 +1889,7 @@ inline bool pair_eligible(const StepParams& p, bool mhd, int mode)
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0] || mode == MODE_FIELDS) return false;
     if (p.variant == 2) return true;
     if (p.variant != 0 || mhd) return false;
-    return base_storage(p.storage) == ST_F16 || base_storage(p.storage) == ST_BF16;
+    return base_storage(p.storage) == ST_F16 || base_storage(p.storage) == ST_BF16 || p.storage == ST_F32;
 }
 
 // ---------------------------------------------------------------------------
