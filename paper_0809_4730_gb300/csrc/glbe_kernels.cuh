@@ -1872,7 +1872,9 @@ template <int ST, int MODE>
 constexpr int pair_dense_blocks()
 {
     if (base_storage(ST) == ST_F16) return MODE == MODE_STEP ? 8 : 7;
-    if (ST == ST_F32) return MODE == MODE_STEP ? 4 : 0;   // 128 registers, 56 B spilled
+    // F32: plain step 4 (128 registers, 56 B spilled); the residual step stays
+    // free (held to 4 it spills 176 B: 10 levels took 8.59 against 8.37 ms)
+    if (ST == ST_F32) return MODE == MODE_STEP ? 4 : 0;
     return base_storage(ST) == ST_BF16 ? 7 : 0;   // 0: the free kernel
 }
 
@@ -1881,9 +1883,11 @@ constexpr int pair_dense_blocks()
 // steps, where it measured faster on the 512 x 256 x 256 duct: its interior
 // rows issue about 310 instructions per node against 538 for the one-node
 // kernel.  Plain step, BF16 0.485 against 0.598 ms, F16 0.509 against 0.631
-// ms; residual step, BF16 0.655 against 0.838 ms.  F32 stays on one node per
-// thread: paired, its 142 registers leave 8 warps per SM (1.17 against 0.89
-// ms).  The coupled forms and F32C have no interior pair path.
+// ms; residual step, BF16 0.655 against 0.838 ms.  F32 takes it too since
+// the interior pair path: held to 4 blocks of 128 (128 registers) the plain
+// step is 0.801 against 0.938 ms for one node per thread (at 142 registers,
+// 3 blocks, it had measured 1.17 against 0.89 ms before that path).  The
+// coupled forms and F32C have no interior pair path.
 inline bool pair_eligible(const StepParams& p, bool mhd, int mode)
 {
     if ((p.nx % 2 != 0) || p.wlo[0] || p.whi[0] || mode == MODE_FIELDS) return false;
