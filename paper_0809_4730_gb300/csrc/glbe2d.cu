@@ -725,6 +725,13 @@ __global__ void __launch_bounds__(T2D, MINB) step2d_kernel_dense(const P2 p, con
 {
     step2d_body<ST, MHD, M2_STEP>(p, b, o);
 }
+// The coupled F32 residual step held likewise (4 blocks: 64 registers, 52 B
+// spilled).
+template <int ST, int MINB>
+__global__ void __launch_bounds__(T2D, MINB) step2d_kernel_dense_resid(const P2 p, const B2 b, const Out2 o)
+{
+    step2d_body<ST, true, M2_RESID>(p, b, o);
+}
 template <int ST, bool MHD>
 constexpr int dense2d_blocks()
 {
@@ -1220,6 +1227,13 @@ cudaError_t launch2_t(glbe2d_ctx* c, int mode, const B2& b_in, const Out2& o, cu
         }
     } else if (mode == M2_RESID) {
         if (mhd) {
+            if constexpr (ST == GLBE_F32) {
+                if (c->prm.variant == 0) {
+                    b.pf_ahead = prefetch_distance<ST, true>(step2d_kernel_dense_resid<ST, 4>, nb);
+                    step2d_kernel_dense_resid<ST, 4><<<nb, T2D, 0, st>>>(c->p, b, o);
+                    return cudaGetLastError();
+                }
+            }
             b.pf_ahead = prefetch_distance<ST, true>(step2d_kernel<ST, true, M2_RESID>, nb);
             step2d_kernel<ST, true, M2_RESID><<<nb, T2D, 0, st>>>(c->p, b, o);
         } else {
