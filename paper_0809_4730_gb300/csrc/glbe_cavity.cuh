@@ -150,6 +150,53 @@ __global__ void __launch_bounds__(STEP_THREADS) cavity_kernel(const StepParams p
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
 
+// The coupled cavity step in two passes per thread (the FP32 forms; the
+// one-pass coupled F32C update needs 172 registers, one block per SM):
+// pass 1 gathers f and g of a box node, forms rho and m and runs the
+// induction part (g~ and this step's Lorentz force; a node outside the box
+// relaxes g at rest); pass 2 gathers f again and runs the flow update with
+// F = F_ext + F_L.  The one-pass arithmetic in the same order, bit for bit.
+template <int ST, int MODE>
+__global__ void __launch_bounds__(STEP_THREADS, 2) cavity_kernel_coupled2(const StepParams p, const StepBuffers b,
+                                                                           const FieldOut fo)
+{
+    using T = typename Store<ST>::T;
+    if (b.stop != nullptr && *b.stop) return;
+    const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool box_node = false, interior = false;
+    int wp = 0, wm = 0;
+    Geo g{};
+    if (i < p.N) {
+        const uint32_t n = i;
+        g = make_geo(p, n);
+        if (!g.solid) {
+            float q[21], ql[21];
+            interior = is_interior(p, n, wp, wm);
+            if (interior) load_g_interior<ST>(p, static_cast<const T*>(b.gsrc), n, wp, wm, q, ql);
+            else load_g<ST>(p, static_cast<const T*>(b.gsrc), g, q, ql);
+            box_node = in_box(p, g.x, g.y, g.z);
+            if (box_node) {
+                float d[19], dl[19];
+                if (interior) load_f_interior<ST>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
+                else load_f_box<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+                induction_from_sources<ST>(p, b, n, d, dl, q, ql);
+            } else {
+                induction_at_rest<ST, MODE>(p, b, fo, n, q, ql);
+            }
+        }
+    }
+    if (box_node) {
+        const uint32_t n = i;
+        float d[19], dl[19], q[21], ql[21];
+        if (interior) load_f_interior<ST>(p, static_cast<const T*>(b.fsrc), n, wp, wm, d, dl);
+        else load_f_box<ST>(p, static_cast<const T*>(b.fsrc), g, d, dl);
+        node_from_sources<ST, false, MODE, false, 0>(p, b, fo, n, d, dl, q, ql, node_inputs<false, MODE, true>(p, b, n),
+                                                     acc);
+    }
+    if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
+}
+
 // Initial state under a moving lid.  A pull gathers from the other buffer as
 // from the post-collision values of the previous step, so a link bounced off
 // the lid returns with the lid term added.  For the first step to gather the

@@ -1381,6 +1381,11 @@ __device__ __forceinline__ void scalar_node_step(const StepParams& p, const Step
 // false, true>: it gathers f again (from L2) and runs the flow update with
 // F = F_ext + b.FL, which is the one-pass update's arithmetic in the same
 // order, so the result is bit for bit the same.
+template <int ST>
+__device__ __forceinline__ void induction_from_sources(const StepParams& p, const StepBuffers& b, uint32_t n,
+                                                      const float (&d)[19], const float (&dl)[19],
+                                                      const float (&q)[21], const float (&ql)[21]);
+
 template <int ST, bool CG>
 __device__ __forceinline__ void coupled_induction_pass(const StepParams& p, const StepBuffers& b, uint32_t i)
 {
@@ -1401,6 +1406,21 @@ __device__ __forceinline__ void coupled_induction_pass(const StepParams& p, cons
         load_f<ST, CG>(p, static_cast<const T*>(b.fsrc), g, d, dl);
         load_g<ST, CG>(p, static_cast<const T*>(b.gsrc), g, q, ql);
     }
+    induction_from_sources<ST>(p, b, n, d, dl, q, ql);
+}
+
+// Pass 1 of the two-pass coupled update from the gathered populations of
+// node n: rho and m, the induction part, and the stores of g~ and of this
+// step's Lorentz force.
+template <int ST>
+__device__ __forceinline__ void induction_from_sources(const StepParams& p, const StepBuffers& b, uint32_t n,
+                                                      const float (&d)[19], const float (&dl)[19],
+                                                      const float (&q)[21], const float (&ql)[21])
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    constexpr bool PRECISE = (ST == ST_F32 || ST == ST_F32C);
+    const size_t N = p.N;
     const NodeIn<float> in = node_inputs<true, MODE_STEP>(p, b, n);
     // rho and m as node_update forms them
     NodeMoments<float, PRECISE> mm;
@@ -2038,6 +2058,9 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             const unsigned grid = (unsigned)(((size_t)p.N + STEP_THREADS - 1) / STEP_THREADS);
             if (MODE != MODE_FIELDS && p.collision == 1) {
                 if constexpr (ST == ST_F32) cavity_kernel<ST, MHD, MODE, 1><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
+            } else if (MHD && (ST == ST_F32 || ST == ST_F32C) && MODE != MODE_FIELDS && p.variant == 0) {
+                if constexpr (MHD && (ST == ST_F32 || ST == ST_F32C) && MODE != MODE_FIELDS)
+                    cavity_kernel_coupled2<ST, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
             } else {
                 cavity_kernel<ST, MHD, MODE, 0><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
             }
