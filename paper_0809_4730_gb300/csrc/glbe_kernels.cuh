@@ -2047,6 +2047,17 @@ long long resident_wave(K kernel, int threads)
     return (long long)sms * per_sm;
 }
 
+// Blocks of the one-pass coupled one-node kernel resident at once.  The
+// two-pass form pays off on grids of several such waves; on a grid of about
+// one wave its second gather only adds latency (F32C, 64 x 64 x 8 duct:
+// 10.4 against 8.5 us per step; 64^3: 37.0 against 39.2 us).
+template <int ST, int MODE>
+long long one_pass_wave()
+{
+    static const long long w = resident_wave(step_kernel<ST, true, MODE>, STEP_THREADS);
+    return w;
+}
+
 template <int ST, bool MHD, int MODE>
 cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const FieldOut& fo, cudaStream_t st,
                         unsigned* nblocks)
@@ -2102,7 +2113,7 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             b.pf_ahead = wave;
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
         } else if (MHD && (ST == ST_F32C || (ST == ST_F32 && MODE == MODE_STEP_RESID)) && MODE != MODE_FIELDS &&
-                   p.variant == 0) {
+                   p.variant == 0 && grid > 2 * one_pass_wave<ST, MODE>()) {
             // F32C: both steps; F32: the residual step only (its one-pass form
             // spills; the plain F32 step keeps one pass, 1.853 against 1.894 ms
             // on the 512 x 256 x 256 coupled duct, while the residual level
