@@ -1320,15 +1320,21 @@ def adjoint_duct(n: int, storage: str = "f32c"):
 # dram__bytes_read.sum,dram__bytes_write.sum -k regex:adjoint_kernel -s 40 -c 1` on the 96^3 coupled
 # duct (848,256 fluid nodes; profiles/adjoint_kernel_hartmann_duct.md).  The captured launch was a
 # convergence-check iteration, which also reads and writes the 12 B gradient snapshot per node.
-ADJ_TRAFFIC_B_PER_FLUID_NODE = (381026304 + 147569408) / 848256
+# DRAM bytes of one steady-adjoint launch per fluid node (ncu, 96^3 duct);
+# None until taken for the current kernel
+ADJ_TRAFFIC_B_PER_FLUID_NODE = None
 
 
-def adjoint_bytes_per_node(mhd: bool, storage: str = "f32c") -> int:
-    """Algorithmic bytes of one adjoint step per fluid node: forward gather
+def adjoint_bytes_per_node(mhd: bool, storage: str = "f32c", steady: bool = True) -> int:
+    """Algorithmic bytes of one adjoint step per fluid node.  Steady form:
+    the linearisation rows of the fixed state (16 x 4 B with the induction
+    lattice, 7 x 4 B without), cotangent gather and store 43 x 4 B each
+    (19 without), gradient 3 x 4 B.  Unrolled form: the forward gather
     (19 f + 21 g) x 4 B (F32) or 6 B (F32C), lagged Lorentz force and force
-    field 3 x 4 B each, cotangent gather and store 43 x 4 B each, gradient
-    3 x 4 B."""
+    field 3 x 4 B each in place of the rows."""
     vb = 6 if storage == "f32c" else 4
+    if steady:
+        return (16 * 4 + 43 * 4 * 2 + 12) if mhd else (7 * 4 + 19 * 4 * 2 + 12)
     if mhd:
         return 40 * vb + 12 + 12 + 43 * 4 * 2 + 12
     return 19 * vb + 12 + 19 * 4 * 2 + 12
@@ -1412,7 +1418,9 @@ def run_adjoint(args, rank, ws):
         "unrolled_adjoint": {"steps": args.adjoint_unrolled_steps, "K": args.adjoint_K, "seconds": round(unr_s, 3),
                              "max_abs_dQdF": float(dQu.abs().max())},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 3), "traffic": round(ADJ_TRAFFIC_B_PER_FLUID_NODE * fluid),
+                     "frac": round(achieved / hbm, 3),
+                     "traffic": None if ADJ_TRAFFIC_B_PER_FLUID_NODE is None
+                     else round(ADJ_TRAFFIC_B_PER_FLUID_NODE * fluid),
                      "note": "per iteration of glbe_adjoint_steady (adjoint kernel + finalize every 10 + host "
                              f"polling), {bpn} B per fluid node, peak of measured; traffic: bytes per launch, ncu "
                              "capture of a convergence-check launch on the 96^3 duct scaled by fluid nodes"},

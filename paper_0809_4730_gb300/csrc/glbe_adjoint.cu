@@ -54,6 +54,9 @@ struct AdjArgs {
     const void* gsrc;
     const float* FL;          // [3][N] lagged Lorentz force at level t
     const float* Ffield;      // [force_ncomp][N] or null
+    // linearisation rows of the same state ([LIN_ROWS][N], NodeLin order);
+    // read by the LIN launches in place of fsrc, gsrc, FL and Ffield
+    const float* lin;
     // cotangents: in = level t+1, out = level t; [19][N] f, [21][N] g, [3][N] F_L
     const float* lam_in;
     float* lam_out;
@@ -70,7 +73,10 @@ struct AdjArgs {
     const int* stop;          // null or a device flag: when set the launch does nothing
 };
 
-template <int ST, bool MHD, bool RESID>
+// One adjoint step.  LIN: the linearisation point comes from a.lin (the
+// steady adjoint, whose state is fixed); else from the forward gather of the
+// state at fsrc/gsrc/FL.
+template <int ST, bool MHD, bool RESID, bool LIN>
 __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParams p, const AdjArgs a)
 {
     using S = Store<ST>;
@@ -103,11 +109,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
     if (inb && is_interior(p, n, wp, wm)) {
         // every link is a plain one: slot o of the node x + e_o at the fixed
         // offset toff[o] (x-seam targets corrected like the sources of opp(o))
-        load_f_interior<ST>(p, static_cast<const T*>(a.fsrc), n, wp, wm, d, dl);
-        fold_lo(d, dl);
-        if (MHD) {
-            load_g_interior<ST>(p, static_cast<const T*>(a.gsrc), n, wp, wm, q, ql);
-            fold_lo(q, ql);
+        if (!LIN) {
+            load_f_interior<ST>(p, static_cast<const T*>(a.fsrc), n, wp, wm, d, dl);
+            fold_lo(d, dl);
+            if (MHD) {
+                load_g_interior<ST>(p, static_cast<const T*>(a.gsrc), n, wp, wm, q, ql);
+                fold_lo(q, ql);
+            }
         }
         const float* __restrict__ l0 = lf + n;
 #pragma unroll
@@ -124,11 +132,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
         const Geo g = make_geo(p, n);
         fluid = inb && !g.solid;
         if (fluid) {
-            load_f<ST>(p, static_cast<const T*>(a.fsrc), g, d, dl);
-            fold_lo(d, dl);
-            if (MHD) {
-                load_g<ST>(p, static_cast<const T*>(a.gsrc), g, q, ql);
-                fold_lo(q, ql);
+            if (!LIN) {
+                load_f<ST>(p, static_cast<const T*>(a.fsrc), g, d, dl);
+                fold_lo(d, dl);
+                if (MHD) {
+                    load_g<ST>(p, static_cast<const T*>(a.gsrc), g, q, ql);
+                    fold_lo(q, ql);
+                }
             }
             vf[0] = lf[n];
 #define GLBE_ADJF(a_, o_, src, sol) vf[o_] = (sol) ? lf[(size_t)(a_) * N + n] : lf[(size_t)(o_) * N + (src)];
@@ -160,20 +170,35 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
                 for (int k = 0; k < 3; ++k) a.dsnap[(size_t)k * N + n] = 0.f;
         }
     } else {
-        float FLp[3] = {0.f, 0.f, 0.f};
-        if (MHD) {
-            FLp[0] = a.FL[n];
-            FLp[1] = a.FL[N + n];
-            FLp[2] = a.FL[2 * N + n];
-        } else {
+        NodeLin lp;
+        if (LIN) {
+            const float* __restrict__ ln = a.lin + n;
+            lp.ri = ln[0];
 #pragma unroll
-            for (int k = 0; k < 21; ++k) q[k] = 0.f;
-        }
-        float Fext[3] = {p.F[0], p.F[1], p.F[2]};
-        if (p.force_ncomp >= 1) Fext[0] += __ldg(a.Ffield + n);
-        if (p.force_ncomp == 3) {
-            Fext[1] += __ldg(a.Ffield + N + n);
-            Fext[2] += __ldg(a.Ffield + 2 * N + n);
+            for (int c = 0; c < 3; ++c) {
+                lp.j[c] = ln[(size_t)(1 + c) * N];
+                lp.F[c] = ln[(size_t)(4 + c) * N];
+                lp.B[c] = MHD ? ln[(size_t)(7 + c) * N] : 0.f;
+                lp.u0[c] = MHD ? ln[(size_t)(10 + c) * N] : 0.f;
+                lp.Jv[c] = MHD ? ln[(size_t)(13 + c) * N] : 0.f;
+            }
+        } else {
+            float FLp[3] = {0.f, 0.f, 0.f};
+            if (MHD) {
+                FLp[0] = a.FL[n];
+                FLp[1] = a.FL[N + n];
+                FLp[2] = a.FL[2 * N + n];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 21; ++k) q[k] = 0.f;
+            }
+            float Fext[3] = {p.F[0], p.F[1], p.F[2]};
+            if (p.force_ncomp >= 1) Fext[0] += __ldg(a.Ffield + n);
+            if (p.force_ncomp == 3) {
+                Fext[1] += __ldg(a.Ffield + N + n);
+                Fext[2] += __ldg(a.Ffield + 2 * N + n);
+            }
+            lp = node_linearise<MHD>(p, d, q, FLp, Fext);
         }
         float vFL[3] = {0.f, 0.f, 0.f};
         if (MHD) {
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
         if (RESID && a.have_snap)
             for (int k = 0; k < 3; ++k) snap[k] = a.dsnap[(size_t)k * N + n];
         NodeAdjoint r;
-        node_reverse<MHD>(p, d, q, FLp, Fext, vf, vg, vFL, wu, r);
+        node_reverse_at<MHD>(p, lp, vf, vg, vFL, wu, r);
 #pragma unroll
         for (int k = 0; k < 19; ++k) of[(size_t)k * N + n] = r.d[k];
         if (MHD) {
@@ -228,13 +253,96 @@ __global__ void __launch_bounds__(ADJ_THREADS, 4) adjoint_kernel(const StepParam
     if (RESID) block_partials<ADJ_THREADS>(acc, a.partials);
 }
 
+// The linearisation rows of the state at fsrc/gsrc/FL (with the force
+// field): NodeLin of every fluid node, 0 on solid nodes.  One launch per
+// steady adjoint solve.
+template <int ST, bool MHD>
+__global__ void __launch_bounds__(ADJ_THREADS) adjoint_lin_kernel(const StepParams p, const AdjArgs a, float* lin)
+{
+    using S = Store<ST>;
+    using T = typename S::T;
+    const uint32_t i = blockIdx.x * ADJ_THREADS + threadIdx.x;
+    if (i >= p.N) return;
+    const size_t N = p.N;
+    float d[19], dl[19], q[21], ql[21];
+    int wp = 0, wm = 0;
+    bool fluid = true;
+    if (is_interior(p, i, wp, wm)) {
+        load_f_interior<ST>(p, static_cast<const T*>(a.fsrc), i, wp, wm, d, dl);
+        if (MHD) load_g_interior<ST>(p, static_cast<const T*>(a.gsrc), i, wp, wm, q, ql);
+    } else {
+        const Geo g = make_geo(p, i);
+        fluid = !g.solid;
+        if (fluid) {
+            load_f<ST>(p, static_cast<const T*>(a.fsrc), g, d, dl);
+            if (MHD) load_g<ST>(p, static_cast<const T*>(a.gsrc), g, q, ql);
+        }
+    }
+    constexpr int R = MHD ? LIN_ROWS_MHD : LIN_ROWS_FLOW;
+    if (!fluid) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) lin[(size_t)k * N + i] = 0.f;
+        return;
+    }
+    if constexpr (S::COMP) {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) d[k] += dl[k];
+        if (MHD) {
+#pragma unroll
+            for (int k = 0; k < 21; ++k) q[k] += ql[k];
+        }
+    }
+    float FLp[3] = {0.f, 0.f, 0.f};
+    if (MHD) {
+        FLp[0] = a.FL[i];
+        FLp[1] = a.FL[N + i];
+        FLp[2] = a.FL[2 * N + i];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 21; ++k) q[k] = 0.f;
+    }
+    float Fext[3] = {p.F[0], p.F[1], p.F[2]};
+    if (p.force_ncomp >= 1) Fext[0] += __ldg(a.Ffield + i);
+    if (p.force_ncomp == 3) {
+        Fext[1] += __ldg(a.Ffield + N + i);
+        Fext[2] += __ldg(a.Ffield + 2 * N + i);
+    }
+    const NodeLin L = node_linearise<MHD>(p, d, q, FLp, Fext);
+    float* __restrict__ o = lin + i;
+    o[0] = L.ri;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o[(size_t)(1 + c) * N] = L.j[c];
+        o[(size_t)(4 + c) * N] = L.F[c];
+        if (MHD) {
+            o[(size_t)(7 + c) * N] = L.B[c];
+            o[(size_t)(10 + c) * N] = L.u0[c];
+            o[(size_t)(13 + c) * N] = L.Jv[c];
+        }
+    }
+}
+
 template <int ST, bool MHD>
 cudaError_t launch_adj2(bool resid, const StepParams& p, const AdjArgs& a, cudaStream_t st, unsigned* nblocks)
 {
     const unsigned grid = (unsigned)(((size_t)p.N + ADJ_THREADS - 1) / ADJ_THREADS);
-    if (resid) adjoint_kernel<ST, MHD, true><<<grid, ADJ_THREADS, 0, st>>>(p, a);
-    else adjoint_kernel<ST, MHD, false><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+    if (a.lin) {
+        // no state gather: one instantiation serves both storage forms
+        if (resid) adjoint_kernel<ST_F32, MHD, true, true><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+        else adjoint_kernel<ST_F32, MHD, false, true><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+    } else {
+        if (resid) adjoint_kernel<ST, MHD, true, false><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+        else adjoint_kernel<ST, MHD, false, false><<<grid, ADJ_THREADS, 0, st>>>(p, a);
+    }
     if (nblocks) *nblocks = grid;
+    return cudaGetLastError();
+}
+
+template <int ST, bool MHD>
+cudaError_t launch_lin2(const StepParams& p, const AdjArgs& a, float* lin, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)(((size_t)p.N + ADJ_THREADS - 1) / ADJ_THREADS);
+    adjoint_lin_kernel<ST, MHD><<<grid, ADJ_THREADS, 0, st>>>(p, a, lin);
     return cudaGetLastError();
 }
 
@@ -246,6 +354,12 @@ cudaError_t launch_adjoint(int storage, bool mhd, bool resid, const StepParams& 
                    : launch_adj2<ST_F32, false>(resid, p, a, st, nblocks);
     return mhd ? launch_adj2<ST_F32C, true>(resid, p, a, st, nblocks)
                : launch_adj2<ST_F32C, false>(resid, p, a, st, nblocks);
+}
+
+cudaError_t launch_linearise(int storage, bool mhd, const StepParams& p, const AdjArgs& a, float* lin, cudaStream_t st)
+{
+    if (storage == GLBE_F32) return mhd ? launch_lin2<ST_F32, true>(p, a, lin, st) : launch_lin2<ST_F32, false>(p, a, lin, st);
+    return mhd ? launch_lin2<ST_F32C, true>(p, a, lin, st) : launch_lin2<ST_F32C, false>(p, a, lin, st);
 }
 
 __global__ void adj_misc_kernel(long long* t_dev, long long t, int* stop, double* tol, double tol_v, double* record,
@@ -263,6 +377,7 @@ __global__ void adj_misc_kernel(long long* t_dev, long long t, int* stop, double
 struct AdjLayout {
     size_t lam[2];            // cotangent buffers: [19][N] f, [21][N] g, [3][N] F_L (g and F_L unused without induction)
     size_t dsnap, partials, record, hist, misc;
+    size_t lin;               // steady form: the linearisation rows [LIN_ROWS][N]
     size_t state_bytes;       // one stored state: f buffer, g buffer, F_L
     size_t state_f, state_g, state_FL;   // offsets inside a stored state
     size_t cp;                // checkpoints
@@ -291,6 +406,7 @@ AdjLayout adj_layout(const glbe_params* p, long nsteps, long K)
     L.state_g = align_up(19 * N * vb);
     L.state_FL = L.state_g + (p->induction ? align_up(21 * N * vb) : 0);
     L.state_bytes = L.state_FL + (p->induction ? align_up(3 * N * sizeof(float)) : 0);
+    if (nsteps == 0) L.lin = take((size_t)(p->induction ? LIN_ROWS_MHD : LIN_ROWS_FLOW) * N * sizeof(float));
     if (nsteps > 0) {
         L.ncp = (nsteps + K - 1) / K;
         L.nseg = K < nsteps ? K : nsteps;
@@ -422,6 +538,11 @@ glbe_status glbe_adjoint_steady(glbe_ctx* ctx, const float* d_w, double tol, lon
     a.accumulate = 0;
     a.dsnap = reinterpret_cast<float*>(ws + L.dsnap);
     a.partials = partials;
+    // the state is fixed: its linearisation rows once, then every iteration
+    // reads them in place of the state
+    float* lin = reinterpret_cast<float*>(ws + L.lin);
+    ADJ_CUDA(launch_linearise(v.prm.storage, v.prm.induction, v.sp, a, lin, st), "adjoint linearisation");
+    a.lin = lin;
     ADJ_CUDA(cudaMemsetAsync(lam[0], 0, 43 * N * sizeof(float), st), "adjoint init");
     adj_misc_kernel<<<1, 1, 0, st>>>(t_dev, 10, stop, tol_dev, tol, record, hist_count);
     ADJ_CUDA(cudaGetLastError(), "adjoint init");

@@ -71,18 +71,32 @@ __device__ __forceinline__ void apply_Tt(const float (&y)[19], float (&out)[19])
     }
 }
 
-// Reverse of the whole node update (node_update + the stores f~ = d + om,
-// g~ = q + og, F_L stored) at the linearisation point (d, q, FLp, Fext).
-// vf, vg, vFL: cotangents of f~, g~ and the stored F_L; wu: cotangent of the
-// node's velocity u (the objective's weight, 0 for a plain step).
+// Forward quantities of one node that its reverse step needs, at the
+// linearisation point: 1/rho, j = m + F/(2 gamma), the total force F and,
+// with the induction lattice, B, u0 and the current J.  The reverse step is
+// linear in the cotangents with coefficients formed from these 16 values
+// alone, so a fixed linearisation point (the steady adjoint) can keep them
+// resident instead of gathering the 40 populations again every iteration.
+struct NodeLin {
+    float ri;
+    float j[3];
+    float F[3];
+    float B[3], u0[3], Jv[3];   // induction lattice only
+};
+
+// Rows of NodeLin stored per node ([rows][N] FP32): ri, j, F; + B, u0, J.
+constexpr int LIN_ROWS_FLOW = 7;
+constexpr int LIN_ROWS_MHD = 16;
+
+// The forward part of the node update at (d, q, FLp, Fext): the moments, the
+// induction lattice's B, u0, J and the Lorentz force, and j.
 template <bool MHD>
-__device__ __forceinline__ void node_reverse(const StepParams& p, const float (&d)[19], const float (&q)[21],
-                                             const float (&FLp)[3], const float (&Fext)[3], const float (&vf)[19],
-                                             const float (&vg)[21], const float (&vFL)[3], const float (&wu)[3],
-                                             NodeAdjoint& out)
+__device__ __forceinline__ NodeLin node_linearise(const StepParams& p, const float (&d)[19], const float (&q)[21],
+                                                  const float (&FLp)[3], const float (&Fext)[3])
 {
-    // ---- forward intermediates (the precise FP32 moments of the forward
-    // step are not needed here: the reverse is linear in the cotangents)
+    // (the precise FP32 moments of the forward step are not needed here: the
+    // reverse is linear in the cotangents)
+    NodeLin L;
     float drho = 0.f;
 #pragma unroll
     for (int a = 0; a < 19; ++a) drho += d[a];
@@ -94,7 +108,6 @@ __device__ __forceinline__ void node_reverse(const StepParams& p, const float (&
     float F[3] = {Fext[0], Fext[1], Fext[2]};
     // induction forward
     float B[3] = {0.f, 0.f, 0.f}, u0[3] = {0.f, 0.f, 0.f}, Jv[3] = {0.f, 0.f, 0.f};
-    float Lxy = 0.f, Lxz = 0.f, Lyz = 0.f;
     if (MHD) {
         float b[3] = {0.f, 0.f, 0.f};
         for (int j = 0; j < 3; ++j)
@@ -104,9 +117,9 @@ __device__ __forceinline__ void node_reverse(const StepParams& p, const float (&
         u0[1] = (my + hg * (Fext[1] + FLp[1])) * ri;
         u0[2] = (mz + hg * (Fext[2] + FLp[2])) * ri;
         const float c = p.conv_coef;
-        Lxy = c * (u0[0] * B[1] - B[0] * u0[1]);
-        Lxz = c * (u0[0] * B[2] - B[0] * u0[2]);
-        Lyz = c * (u0[1] * B[2] - B[1] * u0[2]);
+        const float Lxy = c * (u0[0] * B[1] - B[0] * u0[1]);
+        const float Lxz = c * (u0[0] * B[2] - B[0] * u0[2]);
+        const float Lyz = c * (u0[1] * B[2] - B[1] * u0[2]);
         const float Nxy = (q[8] - q[9]) - Lxy, Nyx = (q[3] - q[4]) + Lxy;
         const float Nxz = (q[15] - q[16]) - Lxz, Nzx = (q[5] - q[6]) + Lxz;
         const float Nyz = (q[17] - q[18]) - Lyz, Nzy = (q[12] - q[13]) + Lyz;
@@ -117,7 +130,36 @@ __device__ __forceinline__ void node_reverse(const StepParams& p, const float (&
         F[1] += Jv[2] * B[0] - Jv[0] * B[2];
         F[2] += Jv[0] * B[1] - Jv[1] * B[0];
     }
-    const float j[3] = {mx + hg * F[0], my + hg * F[1], mz + hg * F[2]};
+    L.ri = ri;
+    L.j[0] = mx + hg * F[0];
+    L.j[1] = my + hg * F[1];
+    L.j[2] = mz + hg * F[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        L.F[c] = F[c];
+        L.B[c] = B[c];
+        L.u0[c] = u0[c];
+        L.Jv[c] = Jv[c];
+    }
+    return L;
+}
+
+// Reverse of the whole node update (node_update + the stores f~ = d + om,
+// g~ = q + og, F_L stored) at the linearisation point L.
+// vf, vg, vFL: cotangents of f~, g~ and the stored F_L; wu: cotangent of the
+// node's velocity u (the objective's weight, 0 for a plain step).
+template <bool MHD>
+__device__ __forceinline__ void node_reverse_at(const StepParams& p, const NodeLin& L, const float (&vf)[19],
+                                                const float (&vg)[21], const float (&vFL)[3], const float (&wu)[3],
+                                                NodeAdjoint& out)
+{
+    const float ri = L.ri;
+    const float hg = 0.5f * p.inv_gamma;
+    const float F[3] = {L.F[0], L.F[1], L.F[2]};
+    const float B[3] = {L.B[0], L.B[1], L.B[2]};
+    const float u0[3] = {L.u0[0], L.u0[1], L.u0[2]};
+    const float Jv[3] = {L.Jv[0], L.Jv[1], L.Jv[2]};
+    const float j[3] = {L.j[0], L.j[1], L.j[2]};
     const float u[3] = {j[0] * ri, j[1] * ri, j[2] * ri};
     const float ig = p.inv_gamma, ig2 = p.inv_gamma2, gri = ig * ri;
     const float jj = j[0] * j[0] + j[1] * j[1] + j[2] * j[2];
@@ -275,6 +317,17 @@ __device__ __forceinline__ void node_reverse(const StepParams& p, const float (&
         out.FLp[c2] = FLpbar[c2];
         out.F[c2] = Fextbar[c2];
     }
+}
+
+// Reverse of the node update at (d, q, FLp, Fext): node_reverse_at at the
+// linearisation point node_linearise gives there.
+template <bool MHD>
+__device__ __forceinline__ void node_reverse(const StepParams& p, const float (&d)[19], const float (&q)[21],
+                                             const float (&FLp)[3], const float (&Fext)[3], const float (&vf)[19],
+                                             const float (&vg)[21], const float (&vFL)[3], const float (&wu)[3],
+                                             NodeAdjoint& out)
+{
+    node_reverse_at<MHD>(p, node_linearise<MHD>(p, d, q, FLp, Fext), vf, vg, vFL, wu, out);
 }
 
 }  // namespace glbe
