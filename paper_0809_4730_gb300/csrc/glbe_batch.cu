@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(BT, 512 / BT) batch_kernel(const BatchDomain* 
                 const FieldOut fo{nullptr, nullptr, nullptr};
                 const uint32_t i = (tile - tile0) * BT + threadIdx.x;
                 // populations written by other blocks earlier in this launch:
-                // coherent (L2) loads.  A coupled node is updated in two passes
+                // coherent loads (CG), cached in L1 within a level.  A coupled
+                // node is updated in two passes
                 // (induction, then flow with this step's Lorentz force), each
                 // within the kernel's register budget; the one-pass update
                 // spilled over a kilobyte per thread.
