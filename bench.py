@@ -1320,9 +1320,9 @@ def adjoint_duct(n: int, storage: str = "f32c"):
 # dram__bytes_read.sum,dram__bytes_write.sum -k regex:adjoint_kernel -s 40 -c 1` on the 96^3 coupled
 # duct (848,256 fluid nodes; profiles/adjoint_kernel_hartmann_duct.md).  The captured launch was a
 # convergence-check iteration, which also reads and writes the 12 B gradient snapshot per node.
-# DRAM bytes of one steady-adjoint launch per fluid node (ncu, 96^3 duct);
-# None until taken for the current kernel
-ADJ_TRAFFIC_B_PER_FLUID_NODE = None
+# DRAM bytes of one plain steady-adjoint launch per fluid node: ncu on the
+# 128^3 bench duct (2,032,128 fluid nodes), read + write
+ADJ_TRAFFIC_B_PER_FLUID_NODE = (479625472 + 339030016) / 2032128
 
 
 def adjoint_bytes_per_node(mhd: bool, storage: str = "f32c", steady: bool = True) -> int:
@@ -1422,8 +1422,8 @@ def run_adjoint(args, rank, ws):
                      "traffic": None if ADJ_TRAFFIC_B_PER_FLUID_NODE is None
                      else round(ADJ_TRAFFIC_B_PER_FLUID_NODE * fluid),
                      "note": "per iteration of glbe_adjoint_steady (adjoint kernel + finalize every 10 + host "
-                             f"polling), {bpn} B per fluid node, peak of measured; traffic: bytes per launch, ncu "
-                             "capture of a convergence-check launch on the 96^3 duct scaled by fluid nodes"},
+                             f"polling), {bpn} B per fluid node, peak of measured; traffic: bytes of one plain launch, ncu "
+                             "capture on the 128^3 duct scaled by fluid nodes"},
         "full_size_check": fd, "clocks": clk.summary(),
     }
 

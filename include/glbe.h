@@ -377,8 +377,11 @@ void glbe_batch_destroy(glbe_batch* b);
 
 /* Workspace bytes of glbe_adjoint_steady (nsteps = 0) or of
  * glbe_adjoint_unrolled(nsteps, K): two cotangent buffers of 43N floats plus,
- * for the unrolled form, ceil(nsteps/K) checkpoints and min(K, nsteps)
- * recomputed states (each a population buffer pair and the Lorentz force). */
+ * for the steady form, the linearisation rows of the fixed state (16N floats
+ * with induction, 7N without: the forward quantities the transposed update
+ * needs, written once per call), and for the unrolled form ceil(nsteps/K)
+ * checkpoints and min(K, nsteps) recomputed states (each a population buffer
+ * pair and the Lorentz force). */
 glbe_status glbe_adjoint_workspace_bytes(const glbe_params* p, long nsteps, long K, size_t* bytes);
 
 /* Steady adjoint at the context's current state, which should be a converged
