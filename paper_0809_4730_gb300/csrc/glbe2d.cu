@@ -504,6 +504,181 @@ __device__ __forceinline__ void node_update2(const P2& p, const float (&d)[9], c
     if (COLLIDE) collide9(p, H, L, nd, Fx, Fy, om);
 }
 
+// ---------------------------------------------------------------------------
+// The BF16 node update, written once for one node (V = float) and for two
+// x-adjacent nodes at once (V = V2: packed FP32x2 instructions, one
+// instruction for both nodes).  Every operation is explicit and rounded on
+// its own -- nothing is left to the compiler to contract -- so the two-node
+// form gives the one-node form's values bit for bit.  Same moments, fields,
+// collision (Sec. 3, App. A) and induction part (Sec. 4) as node_update2
+// without the exact split.
+// ---------------------------------------------------------------------------
+struct V2 {
+    float2 v;
+    __device__ __forceinline__ V2() {}
+    __device__ __forceinline__ V2(float c) : v(make_float2(c, c)) {}
+    __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ V2 vadd(V2 a, V2 b)
+{
+    V2 r;
+    r.v = __fadd2_rn(a.v, b.v);
+    return r;
+}
+// a - b = fma(b, -1, a), rounded once like the scalar subtraction
+__device__ __forceinline__ V2 vsub(V2 a, V2 b)
+{
+    V2 r;
+    r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v);
+    return r;
+}
+__device__ __forceinline__ V2 vmul(V2 a, V2 b)
+{
+    V2 r;
+    r.v = __fmul2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c)
+{
+    V2 r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+}
+__device__ __forceinline__ V2 vdiv(V2 a, V2 b) { return V2(__fdiv_rn(a.v.x, b.v.x), __fdiv_rn(a.v.y, b.v.y)); }
+template <class V>
+__device__ __forceinline__ V vneg(V a) { return vmul(V(-1.f), a); }
+
+template <class V>
+struct Mom9V {
+    V drho, e, e2, mx, qx, my, qy, pxx, pxy;
+};
+template <class V>
+__device__ __forceinline__ Mom9V<V> moments9v(const V (&d)[9])
+{
+    Mom9V<V> m;
+    const V ax = vadd(d[1], d[3]), ay = vadd(d[2], d[4]);
+    const V dg = vadd(vadd(d[5], d[6]), vadd(d[7], d[8]));
+    const V sx = vsub(d[1], d[3]), sy = vsub(d[2], d[4]);
+    const V gx = vadd(vsub(d[5], d[6]), vsub(d[8], d[7]));
+    const V gy = vsub(vadd(d[5], d[6]), vadd(d[7], d[8]));
+    const V axy = vadd(ax, ay);
+    m.drho = vadd(vadd(d[0], axy), dg);
+    m.e = vfma(V(2.f), dg, vsub(vmul(V(-4.f), d[0]), axy));
+    m.e2 = vadd(vfma(V(-2.f), axy, vmul(V(4.f), d[0])), dg);
+    m.mx = vadd(sx, gx);
+    m.qx = vfma(V(-2.f), sx, gx);
+    m.my = vadd(sy, gy);
+    m.qy = vfma(V(-2.f), sy, gy);
+    m.pxx = vsub(ax, ay);
+    m.pxy = vadd(vsub(d[5], d[6]), vsub(d[7], d[8]));
+    return m;
+}
+
+template <class V>
+struct Node2V {
+    V rho, jx, jy, ux, uy;
+    V Bx, By, FLx, FLy;
+};
+
+template <class V, bool COLLIDE>
+__device__ __forceinline__ void induction2v(const P2& p, const V (&q)[10], V u0x, V u0y, Node2V<V>& nd, V (&og)[10])
+{
+    const V dBx = vadd(vadd(vadd(q[0], q[1]), vadd(q[2], q[3])), q[4]);
+    const V dBy = vadd(vadd(vadd(q[5], q[6]), vadd(q[7], q[8])), q[9]);
+    nd.Bx = vadd(V(p.B0x), dBx);
+    nd.By = vadd(V(p.B0y), dBy);
+    // E = u_x B_y - u_y B_x; the equilibrium's part of (+x) - (-x) of B_y is ceq E / 3
+    const V cE = vmul(V(p.ceq), vsub(vmul(u0x, nd.By), vmul(u0y, nd.Bx)));
+    const V cE3 = vmul(cE, V(1.f / 3.f));
+    const V Lxy = vsub(vsub(q[6], q[7]), cE3);
+    const V Lyx = vadd(vsub(q[3], q[4]), cE3);
+    const V nJz = vmul(V(p.cJ), vsub(Lxy, Lyx));      // -J_z
+    nd.FLx = vmul(nJz, nd.By);                        // -J_z B_y
+    nd.FLy = vneg(vmul(nJz, nd.Bx));                  //  J_z B_x
+    if (COLLIDE) {
+        constexpr float W0 = 1.f / 3.f, W1 = 1.f / 6.f;
+        V geq[10];
+        geq[0] = vmul(V(W0), dBx);
+        geq[1] = vmul(V(W1), dBx);
+        geq[2] = geq[1];
+        geq[3] = vmul(V(W1), vsub(dBx, cE));
+        geq[4] = vmul(V(W1), vadd(dBx, cE));
+        geq[5] = vmul(V(W0), dBy);
+        geq[6] = vmul(V(W1), vadd(dBy, cE));
+        geq[7] = vmul(V(W1), vsub(dBy, cE));
+        geq[8] = vmul(V(W1), dBy);
+        geq[9] = geq[8];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) og[i] = vmul(vsub(geq[i], q[i]), V(p.inv_tau_m));
+    }
+}
+
+template <class V>
+__device__ __forceinline__ void collide9v(const P2& p, const Mom9V<V>& H, const Node2V<V>& nd, V Fx, V Fy,
+                                          V (&om)[9])
+{
+    const V rg = vdiv(V(p.inv_gamma), nd.rho);
+    const V jj3 = vmul(vmul(V(3.f), vfma(nd.jx, nd.jx, vmul(nd.jy, nd.jy))), rg);
+    const V Fu = vfma(Fx, nd.ux, vmul(Fy, nd.uy));
+    const V ne = vsub(vfma(V(2.f), H.drho, H.e), jj3);
+    const V ne2 = vadd(vsub(H.e2, H.drho), jj3);
+    const V nqx = vfma(V(p.half_inv_gamma), Fx, vadd(H.qx, H.mx));
+    const V nqy = vfma(V(p.half_inv_gamma), Fy, vadd(H.qy, H.my));
+    const V npxx = vsub(H.pxx, vmul(vfma(nd.jx, nd.jx, vneg(vmul(nd.jy, nd.jy))), rg));
+    const V npxy = vsub(H.pxy, vmul(vmul(nd.jx, nd.jy), rg));
+    const V d1 = vfma(V(p.a1), ne, vmul(V(p.b1), Fu));
+    const V d2 = vfma(V(p.a2), ne2, vmul(V(p.b2), Fu));
+    const V d3 = vmul(V(p.c3), Fx);
+    const V d4 = vfma(V(p.a4), nqx, vmul(V(p.b4), Fx));
+    const V d5 = vmul(V(p.c3), Fy);
+    const V d6 = vfma(V(p.a6), nqy, vmul(V(p.b6), Fy));
+    const V d7 = vfma(V(p.a7), npxx, vmul(V(p.b7), vfma(Fx, nd.ux, vneg(vmul(Fy, nd.uy)))));
+    const V d8 = vfma(V(p.a8), npxy, vmul(V(p.b8), vfma(Fx, nd.uy, vmul(Fy, nd.ux))));
+    const V A = vneg(vfma(V(2.f), d2, d1));          // axis directions: e = -1, e^2 = -2
+    const V Dg = vfma(V(2.f), d1, d2);               // diagonals: e = 2, e^2 = 1
+    const V X1 = vfma(V(-2.f), d4, d3), Y1 = vfma(V(-2.f), d6, d5);
+    const V X2 = vadd(d3, d4), Y2 = vadd(d5, d6);
+    om[0] = vmul(V(4.f), vsub(d2, d1));
+    om[1] = vadd(vadd(A, X1), d7);
+    om[3] = vadd(vsub(A, X1), d7);
+    om[2] = vsub(vadd(A, Y1), d7);
+    om[4] = vsub(vsub(A, Y1), d7);
+    om[5] = vadd(vadd(vadd(Dg, X2), Y2), d8);
+    om[6] = vsub(vadd(vsub(Dg, X2), Y2), d8);
+    om[7] = vadd(vsub(vsub(Dg, X2), Y2), d8);
+    om[8] = vsub(vsub(vadd(Dg, X2), Y2), d8);
+}
+
+template <class V, bool MHD, bool COLLIDE>
+__device__ __forceinline__ void node_update2v(const P2& p, const V (&d)[9], const V (&q)[10], V Fex, V Fey, V FLpx,
+                                              V FLpy, Node2V<V>& nd, V& Fx, V& Fy, V (&om)[9], V (&og)[10])
+{
+    const Mom9V<V> H = moments9v(d);
+    nd.rho = vadd(V(p.rho0), H.drho);
+    const V rinv = vdiv(V(1.f), nd.rho);
+    nd.Bx = nd.By = nd.FLx = nd.FLy = V(0.f);
+    if (MHD) {
+        const V u0x = vmul(vfma(V(p.half_inv_gamma), vadd(Fex, FLpx), H.mx), rinv);
+        const V u0y = vmul(vfma(V(p.half_inv_gamma), vadd(Fey, FLpy), H.my), rinv);
+        induction2v<V, COLLIDE>(p, q, u0x, u0y, nd, og);
+        Fx = vadd(Fex, nd.FLx);
+        Fy = vadd(Fey, nd.FLy);
+    } else {
+        Fx = Fex;
+        Fy = Fey;
+    }
+    nd.jx = vfma(V(p.half_inv_gamma), Fx, H.mx);
+    nd.jy = vfma(V(p.half_inv_gamma), Fy, H.my);
+    nd.ux = vmul(nd.jx, rinv);
+    nd.uy = vmul(nd.jy, rinv);
+    if (COLLIDE) collide9v(p, H, nd, Fx, Fy, om);
+}
+
 // u of a residual level as a double-float pair: the sums of the deviations
 // (with their low parts) carried with their rounding errors, so that the
 // residual resolves changes of u below one unit in the last place of its
@@ -672,7 +847,13 @@ __device__ __forceinline__ void step2d_body(const P2& p, const B2& b, const Out2
             const float FLpx = MHD ? b.FL[n] : 0.f, FLpy = MHD ? b.FL[p.N + n] : 0.f;
             Node2 nd;
             float Fx, Fy, om[9], og[10];
-            node_update2<ST, MHD, MODE != M2_FIELDS>(p, d, dl, q, ql, Fex, Fey, FLpx, FLpy, nd, Fx, Fy, om, og);
+            if constexpr (ST == GLBE_BF16) {
+                Node2V<float> v;
+                node_update2v<float, MHD, MODE != M2_FIELDS>(p, d, q, Fex, Fey, FLpx, FLpy, v, Fx, Fy, om, og);
+                nd = Node2{v.rho, v.jx, v.jy, v.ux, v.uy, v.Bx, v.By, v.FLx, v.FLy};
+            } else {
+                node_update2<ST, MHD, MODE != M2_FIELDS>(p, d, dl, q, ql, Fex, Fey, FLpx, FLpy, nd, Fx, Fy, om, og);
+            }
             if constexpr (MODE == M2_FIELDS) {
                 if (o.rho) o.rho[n] = nd.rho;
                 if (o.u) {
@@ -765,7 +946,10 @@ template <> struct Pair2<GLBE_BF16> {
     // is widened from one 32-bit load by a shift and a mask (exact)
     static __device__ __forceinline__ float2 ld(const void* base, size_t k)
     {
-        const uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(static_cast<const __nv_bfloat16*>(base) + k));
+        uint32_t u;
+        asm("ld.global.nc.L2::256B.b32 %0, [%1];"
+            : "=r"(u)
+            : "l"(static_cast<const __nv_bfloat16*>(base) + k));
         return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
     }
     static __device__ __forceinline__ float ld1(const void* base, size_t k)
@@ -781,50 +965,59 @@ template <> struct Pair2<GLBE_BF16> {
 
 // Gathers the pair's values of the populations rows[0..R) (direction a_r of
 // the lattice EXR/EYR; bounced from row opp_r; sign of the bounce +1 for f,
-// -1 for g).  All loads are issued first -- the aligned pairs and, at a warp
-// edge or the x seam, the lane's own value -- and the lane shuffles follow,
-// so that no load waits for another.
-template <int ST, int R, class DIR>
-__device__ __forceinline__ void gather_pairs(const P2& p, const void* buf, bool live, int y, int x0, int n0, int lane,
-                                             float sign, float (&v0)[R], float (&v1)[R])
-{
-    const size_t N = p.N;
+// -1 for g) in two phases, so that every load of a step -- f and g -- is
+// issued before the first lane shuffle waits for one: pair_loads issues the
+// aligned pairs and, at a warp edge or the x seam, the lane's own value;
+// pair_shuffles forms the x-shifted sources.
+template <int R>
+struct PairGather {
     float2 P[R];
     float E[R];
     bool bounce[R];
+};
+template <int ST, int R, class DIR>
+__device__ __forceinline__ void pair_loads(const P2& p, const void* buf, bool live, int y, int x0, int n0, int lane,
+                                           PairGather<R>& G)
+{
+    const size_t N = p.N;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int ex = DIR::ex(r), ey = DIR::ey(r);
         int ys = y - ey;
         if (ey != 0) ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-        bounce[r] = ey != 0 && ((p.wly && ys == 0) || (p.why && ys == p.ny - 1));
+        G.bounce[r] = ey != 0 && ((p.wly && ys == 0) || (p.why && ys == p.ny - 1));
         const size_t rb = (size_t)DIR::row(r) * N + (size_t)ys * p.nx;
         const bool edge = ex == 1 ? (lane == 0 || x0 == 0) : (ex == -1 ? (lane == 31 || x0 + 2 == p.nx) : false);
         const int xe = ex == 1 ? (x0 == 0 ? p.nx - 1 : x0 - 1) : (x0 + 2 == p.nx ? 0 : x0 + 2);
-        P[r] = make_float2(0.f, 0.f);
-        E[r] = 0.f;
+        G.P[r] = make_float2(0.f, 0.f);
+        G.E[r] = 0.f;
         if (live) {
-            P[r] = Pair2<ST>::ld(buf, bounce[r] ? (size_t)DIR::opp(r) * N + n0 : rb + x0);
-            if (ex != 0 && edge && !bounce[r]) E[r] = Pair2<ST>::ld1(buf, rb + xe);
+            G.P[r] = Pair2<ST>::ld(buf, G.bounce[r] ? (size_t)DIR::opp(r) * N + n0 : rb + x0);
+            if (ex != 0 && edge && !G.bounce[r]) G.E[r] = Pair2<ST>::ld1(buf, rb + xe);
         }
     }
+}
+template <int R, class DIR>
+__device__ __forceinline__ void pair_shuffles(const P2& p, int x0, int lane, float sign, const PairGather<R>& G,
+                                              float (&v0)[R], float (&v1)[R])
+{
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int ex = DIR::ex(r);
         // every lane takes part in the shuffles (uniform control flow)
         float sh = 0.f;
-        if (ex == 1) sh = __shfl_up_sync(0xffffffffu, P[r].y, 1);
-        if (ex == -1) sh = __shfl_down_sync(0xffffffffu, P[r].x, 1);
+        if (ex == 1) sh = __shfl_up_sync(0xffffffffu, G.P[r].y, 1);
+        if (ex == -1) sh = __shfl_down_sync(0xffffffffu, G.P[r].x, 1);
         const bool edge = ex == 1 ? (lane == 0 || x0 == 0) : (ex == -1 ? (lane == 31 || x0 + 2 == p.nx) : false);
-        if (edge) sh = E[r];
-        if (ex == 0 || bounce[r]) {
-            v0[r] = bounce[r] ? sign * P[r].x : P[r].x;
-            v1[r] = bounce[r] ? sign * P[r].y : P[r].y;
+        if (edge) sh = G.E[r];
+        if (ex == 0 || G.bounce[r]) {
+            v0[r] = G.bounce[r] ? sign * G.P[r].x : G.P[r].x;
+            v1[r] = G.bounce[r] ? sign * G.P[r].y : G.P[r].y;
         } else if (ex == 1) {                // sources x0 - 1 and x0
             v0[r] = sh;
-            v1[r] = P[r].x;
+            v1[r] = G.P[r].x;
         } else {                             // sources x0 + 1 and x0 + 2
-            v0[r] = P[r].y;
+            v0[r] = G.P[r].y;
             v1[r] = sh;
         }
     }
@@ -859,8 +1052,12 @@ __global__ void __launch_bounds__(T2D) step2d_pair_kernel(const P2 p, const B2 b
     // take part in the shuffles)
     const bool live = n0 < p.N && !((p.wly && y == 0) || (p.why && y == p.ny - 1));
     float d0[9], d1[9], q0[10], q1[10];
-    gather_pairs<ST, 9, DirF>(p, b.fsrc, live, y, x0, n0, lane, 1.f, d0, d1);
-    if (MHD) gather_pairs<ST, 10, DirG>(p, b.gsrc, live, y, x0, n0, lane, -1.f, q0, q1);
+    PairGather<9> gf;
+    PairGather<10> gg;
+    pair_loads<ST, 9, DirF>(p, b.fsrc, live, y, x0, n0, lane, gf);
+    if (MHD) pair_loads<ST, 10, DirG>(p, b.gsrc, live, y, x0, n0, lane, gg);
+    pair_shuffles<9, DirF>(p, x0, lane, 1.f, gf, d0, d1);
+    if (MHD) pair_shuffles<10, DirG>(p, x0, lane, -1.f, gg, q0, q1);
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float us0[4] = {0.f, 0.f, 0.f, 0.f}, us1[4] = {0.f, 0.f, 0.f, 0.f};
     if (MODE == M2_RESID && live && b.have_snap) {
@@ -886,17 +1083,50 @@ __global__ void __launch_bounds__(T2D) step2d_pair_kernel(const P2 p, const B2 b
         }
         const float z9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float z10[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        Node2 nd0, nd1;
-        float F0x, F0y, F1x, F1y, om0[9], og0[10], om1[9], og1[10];
-        node_update2<ST, MHD, true>(p, d0, z9, q0, z10, Fe.x, Fe.y, FLx.x, FLy.x, nd0, F0x, F0y, om0, og0);
-        node_update2<ST, MHD, true>(p, d1, z9, q1, z10, Fe1.x, Fe1.y, FLx.y, FLy.y, nd1, F1x, F1y, om1, og1);
+        float F0x, F0y, F1x, F1y;
+        if constexpr (ST == GLBE_BF16) {
+            // both nodes in packed FP32x2 instructions
+            V2 dv[9], qv[10], om[9], og[10], Fx, Fy;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) Pair2<ST>::st(b.fdst, (size_t)a * N + n0, d0[a] + om0[a], d1[a] + om1[a]);
-        if (MHD) {
+            for (int a = 0; a < 9; ++a) dv[a] = V2(d0[a], d1[a]);
+            if (MHD) {
 #pragma unroll
-            for (int i = 0; i < 10; ++i) Pair2<ST>::st(b.gdst, (size_t)i * N + n0, q0[i] + og0[i], q1[i] + og1[i]);
-            *reinterpret_cast<float2*>(b.FL + n0) = make_float2(nd0.FLx, nd1.FLx);
-            *reinterpret_cast<float2*>(b.FL + N + n0) = make_float2(nd0.FLy, nd1.FLy);
+                for (int i = 0; i < 10; ++i) qv[i] = V2(q0[i], q1[i]);
+            }
+            Node2V<V2> nd;
+            node_update2v<V2, MHD, true>(p, dv, qv, V2(Fe.x, Fe1.x), V2(Fe.y, Fe1.y), V2(FLx.x, FLx.y),
+                                         V2(FLy.x, FLy.y), nd, Fx, Fy, om, og);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const V2 v = vadd(dv[a], om[a]);
+                Pair2<ST>::st(b.fdst, (size_t)a * N + n0, v.v.x, v.v.y);
+            }
+            if (MHD) {
+#pragma unroll
+                for (int i = 0; i < 10; ++i) {
+                    const V2 v = vadd(qv[i], og[i]);
+                    Pair2<ST>::st(b.gdst, (size_t)i * N + n0, v.v.x, v.v.y);
+                }
+                *reinterpret_cast<float2*>(b.FL + n0) = nd.FLx.v;
+                *reinterpret_cast<float2*>(b.FL + N + n0) = nd.FLy.v;
+            }
+            F0x = Fx.v.x;
+            F1x = Fx.v.y;
+            F0y = Fy.v.x;
+            F1y = Fy.v.y;
+        } else {
+            Node2 nd0, nd1;
+            float om0[9], og0[10], om1[9], og1[10];
+            node_update2<ST, MHD, true>(p, d0, z9, q0, z10, Fe.x, Fe.y, FLx.x, FLy.x, nd0, F0x, F0y, om0, og0);
+            node_update2<ST, MHD, true>(p, d1, z9, q1, z10, Fe1.x, Fe1.y, FLx.y, FLy.y, nd1, F1x, F1y, om1, og1);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) Pair2<ST>::st(b.fdst, (size_t)a * N + n0, d0[a] + om0[a], d1[a] + om1[a]);
+            if (MHD) {
+#pragma unroll
+                for (int i = 0; i < 10; ++i) Pair2<ST>::st(b.gdst, (size_t)i * N + n0, q0[i] + og0[i], q1[i] + og1[i]);
+                *reinterpret_cast<float2*>(b.FL + n0) = make_float2(nd0.FLx, nd1.FLx);
+                *reinterpret_cast<float2*>(b.FL + N + n0) = make_float2(nd0.FLy, nd1.FLy);
+            }
         }
         if constexpr (MODE == M2_RESID) {
             resid_node(p, d0, z9, F0x, F0y, b.have_snap, us0, acc);
