@@ -1644,12 +1644,14 @@ __device__ __forceinline__ void step_body(const StepParams& p, const StepBuffers
     const uint32_t i = blockIdx.x * STEP_THREADS + threadIdx.x;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (MODE != MODE_STEP_RESID && !(i < p.N)) return;
-    // per-direction bases for the plain BF16 flow step only: measured on one
+    // per-direction bases for the plain BF16 steps only: measured on one
     // box against the plain addressing, BF16 0.598 vs 0.612 ms, but F16 0.679
-    // vs 0.631 ms, F32 1.058 vs 0.898 ms and the BF16 residual step 0.914 vs
-    // 0.842 ms; with induction they raise the register count past a block
-    // per SM
-    scalar_node_step<ST, MHD, MODE, false, COLL == 0 && !MHD && base_storage(ST) == ST_BF16 && MODE == MODE_STEP, false,
+    // vs 0.631 ms, F32 1.058 vs 0.898 ms (with induction they raise its
+    // register count past a block per SM) and the BF16 residual step 0.914
+    // vs 0.842 ms; the coupled BF16 step keeps 80 registers with them: f
+    // 1.2586 against 1.3008 ms on the 512 x 256 x 256 duct (the 21 g rows
+    // from such bases too: 1.3385 ms)
+    scalar_node_step<ST, MHD, MODE, false, COLL == 0 && base_storage(ST) == ST_BF16 && MODE == MODE_STEP, false,
                      COLL>(p, b, fo, i, acc);
     if (MODE == MODE_STEP_RESID) block_partials<STEP_THREADS>(acc, b.partials);
 }
