@@ -1696,9 +1696,10 @@ constexpr int step_dense_blocks()
 // flow update with F = F_ext + F_L.  The arithmetic and its order are the
 // one-pass update's, so the result is bit for bit the same, but the
 // registers of the two parts are not live together: 172 registers in one
-// pass (one block of 256 per SM) against at most 128 here.
+// pass (one block of 256 per SM) against at most 128 here (F32C; the F32
+// and BF16 residual steps are held to three blocks).
 template <int ST, int MODE>
-__global__ void __launch_bounds__(STEP_THREADS, ST == ST_F32 ? 3 : 2)
+__global__ void __launch_bounds__(STEP_THREADS, ST == ST_F32C ? 2 : 3)
     step_kernel_coupled2(const StepParams p, const StepBuffers b, const FieldOut fo)
 {
     if (b.stop != nullptr && *b.stop) return;
@@ -2118,18 +2119,24 @@ cudaError_t launch_mode(const StepParams& p, const StepBuffers& b_in, const Fiel
             static const long long wave = resident_wave(step_kernel_dense<ST, MINB>, STEP_THREADS);
             b.pf_ahead = wave;
             step_kernel_dense<ST, MINB><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
-        } else if (MHD && (ST == ST_F32C || (ST == ST_F32 && MODE == MODE_STEP_RESID)) && MODE != MODE_FIELDS &&
+        } else if (MHD && (ST == ST_F32C || ((ST == ST_F32 || ST == ST_BF16) && MODE == MODE_STEP_RESID)) &&
+                   MODE != MODE_FIELDS &&
                    p.variant == 0 && grid > 2 * one_pass_wave<ST, MODE>()) {
             // F32C: both steps; F32: the residual step only (its one-pass form
             // spills; the plain F32 step keeps one pass, 1.853 against 1.894 ms
             // on the 512 x 256 x 256 coupled duct, while the residual level
-            // drops from about 3.3 to 2.3 ms)
-            if constexpr (MHD && (ST == ST_F32C || (ST == ST_F32 && MODE == MODE_STEP_RESID)) && MODE != MODE_FIELDS) {
+            // drops from about 3.3 to 2.3 ms); BF16: the residual step only
+            // (one pass: 90 registers, two blocks per SM; two: 80, three
+            // blocks; the residual level about 1.90 -> 1.73 ms)
+            if constexpr (MHD && (ST == ST_F32C || ((ST == ST_F32 || ST == ST_BF16) && MODE == MODE_STEP_RESID)) &&
+                          MODE != MODE_FIELDS) {
                 // L2 prefetch half a wave ahead, on grids of several waves
                 // (on a 48^3 duct it cost 0.0164 -> 0.0192 ms; on 144^3 it
                 // took the step from 0.3235 to 0.3132 ms)
+                // (not the BF16 residual step: the coupled BF16 steps are
+                // slower with it)
                 static const long long wave = resident_wave(step_kernel_coupled2<ST, MODE>, STEP_THREADS);
-                b.pf_ahead = (long long)grid > 4 * wave ? wave / 2 : 0;
+                b.pf_ahead = ST != ST_BF16 && (long long)grid > 4 * wave ? wave / 2 : 0;
                 step_kernel_coupled2<ST, MODE><<<grid, STEP_THREADS, 0, st>>>(p, b, fo);
             }
         } else {

@@ -227,18 +227,18 @@ def test_tile_kernel_matches_one_node_kernel_bitwise(orc, nx, storage, mhd):
     assert abs(r1.mass - r3.mass) <= 1e-9 * r1.mass
 
 
-# The coupled compensated steps (and the FP32 residual steps) run in two passes per thread (induction,
-# then flow with this step's Lorentz force) under the automatic choice on
+# The coupled compensated steps (and the FP32 and BF16 residual steps) run in two passes per thread
+# (induction, then flow with this step's Lorentz force) under the automatic choice on
 # grids of more than two resident waves of the one-pass kernel (152 SMs x one
-# block of 256 nodes for the F32C one): the one-pass arithmetic in the same
+# or two blocks of 256 nodes): the one-pass arithmetic in the same
 # order, bit for bit, with walls on y and z (general-path nodes), the x seam,
 # a force field and two residual levels.
-@pytest.mark.parametrize("storage", ["f32c", "f32"])
+@pytest.mark.parametrize("storage", ["f32c", "f32", "bf16"])
 @pytest.mark.parametrize("nx,walls", [(37, ((0, 1, 1), (0, 1, 0))), (64, ((1, 1, 0), (0, 1, 1)))])
 def test_coupled_two_pass_matches_one_pass_bitwise(orc, nx, walls, storage):
     from paper_0809_4730_gb300.inputs import random_force
-    cfg = _cfg(orc, True, gamma=0.3, nx=nx, ny=64, nz=64, wall_lo=walls[0], wall_hi=walls[1])
-    assert cfg.nx * cfg.ny * cfg.nz > 3 * 152 * 256
+    cfg = _cfg(orc, True, gamma=0.3, nx=nx, ny=64, nz=80, wall_lo=walls[0], wall_hi=walls[1])
+    assert cfg.nx * cfg.ny * cfg.nz > 4 * 152 * 256
     Fext = random_force(cfg.nx, cfg.ny, cfg.nz, 3e-5, seed=31)
     S, G0 = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=0)
     _, G1 = make_pair(orc, cfg, Fext=Fext, storage=storage, variant=1)
