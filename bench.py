@@ -82,8 +82,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "adjoint", "sweeps", "coupled", "cavity", "tts", "2d",
-                                           "cpu-configs"],
+    ap.add_argument("--workload", choices=["duct", "batch", "batch-single", "adjoint", "sweeps", "coupled", "cavity",
+                                           "tts", "2d", "cpu-configs"],
                     default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
@@ -564,6 +564,46 @@ def batch_bounded(hbm_peak: float, levels: int = 200):
             "achieved_gbs": round(byt / sec / 1e9, 1), "hbm_frac": round(byt / sec / 1e9 / hbm_peak, 4),
             "launch": {"block_threads": bt, "blocks_per_sm": bps}, "status": st,
             "note": "one persistent cooperative launch over all 64 domains, F32C storage, device time"}
+
+
+def batch_against_single(levels: int = 200, steps: int = 100):
+    """The cost of batching: device time per level of the 64-duct F32C batch
+    in one persistent launch (autotuned, CUDA graph) against the sum over the
+    same 64 ducts of one single-context plain step each (CUDA events around
+    `steps` steps per duct; the smallest ducts are launch-bound there)."""
+    import torch
+    from paper_0809_4730_gb300.glbe import Batch, Solver
+    doms, meta = batch_domains("f32c")
+    B = Batch(doms)
+    bt, bps, _ = B.autotune(10)
+    _, _, sec = B.solve(1e-300, levels, use_graph=True)
+    B.close()
+    del B
+    torch.cuda.empty_cache()
+    total, per = 0.0, []
+    for m in meta:
+        n = m["n"]
+        kw = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=m["gamma"], nu=0.1, F=(1e-6, 0, 0), storage="f32c")
+        if m["Ha"] > 0:
+            L = (n - 2) / 2
+            kw.update(induction=1, gamma_m=m["gamma"], eta=0.1, chi=0.01, mu=1.0,
+                      B0=(0, m["Ha"] * math.sqrt(0.1 * 0.1) / L, 0))
+        G = Solver(n, n, n, **kw)
+        G.step(21)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.step(steps)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        total += ms
+        per.append({"n": n, "Ha": m["Ha"], "gamma": m["gamma"], "ms": round(ms, 4)})
+        G.close()
+    return {"metric": "device ms per level: 64-duct F32C batch in one launch vs the ducts as single contexts",
+            "batch_ms_per_level": round(sec / levels * 1e3, 4), "single_sum_ms_per_level": round(total, 4),
+            "batch_over_single": round(sec / levels * 1e3 / total, 4), "launch": {"block_threads": bt,
+                                                                                  "blocks_per_sm": bps},
+            "higher_is_better": False, "data": "synthetic", "dtype": "f32", "per_domain": per}
 
 
 def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
@@ -1440,6 +1480,8 @@ def main():
     rank, ws = dist_init(args)
     if args.workload == "batch":
         line = run_batch(args, rank, ws)
+    elif args.workload == "batch-single":
+        line = batch_against_single()
     elif args.workload == "sweeps":
         line = run_sweeps(args, rank, ws)
     elif args.workload == "coupled":
