@@ -20,7 +20,12 @@
 // at the fixed point s*: its spectrum is the one of the forward step, so the
 // gamma preconditioning accelerates it the same way.  Its convergence is
 // measured on the gradient field itself,
-// r = ||dQdF_k - dQdF_{k-10}|| / ||dQdF_k||, every 10 iterations.
+// r = ||dQdF_k - dQdF_{k-10}|| / ||dQdF_k||, every 10 iterations.  The map is
+// linear in lam with coefficients from 16 forward quantities per node
+// (NodeLin: 1/rho, j, F, B, u0, J), and s* does not change: the steady
+// adjoint writes them once and every iteration reads them in place of the
+// gathered state; the unrolled sweep, whose state changes every level,
+// gathers it.
 #include <cstring>
 
 #include "glbe.h"
