@@ -82,8 +82,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0, help="kernel form: 0 automatic, 1 one node/thread, 2 paired")
-    ap.add_argument("--workload", choices=["duct", "batch", "batch-single", "adjoint", "sweeps", "coupled", "cavity",
-                                           "tts", "2d", "cpu-configs"],
+    ap.add_argument("--workload", choices=["duct", "batch", "batch-single", "batch-small", "adjoint", "sweeps",
+                                           "coupled", "cavity", "tts", "2d", "cpu-configs"],
                     default="duct",
                     help="duct: the timed duct step (default); batch: 64 seeded ducts solved to 1e-8 in one "
                          "launch; adjoint: steady and unrolled dQ/dF on the 128^3 Hartmann duct")
@@ -604,6 +604,45 @@ def batch_against_single(levels: int = 200, steps: int = 100):
             "batch_over_single": round(sec / levels * 1e3 / total, 4), "launch": {"block_threads": bt,
                                                                                   "blocks_per_sm": bps},
             "higher_is_better": False, "data": "synthetic", "dtype": "f32", "per_domain": per}
+
+
+def batch_small(n: int = 96, levels: int = 20):
+    """A small batch for profiling the persistent kernel: four n^3 F32C
+    ducts (two flow, two coupled at Ha = 5; gamma = gamma_m = 0.1, nu = eta =
+    0.1, chi = 0.01, F_x = 1e-6), `levels` levels in one launch of 256-thread
+    blocks, two per SM, without a CUDA graph; and the same ducts as single
+    contexts."""
+    import torch
+    from paper_0809_4730_gb300.glbe import Batch, Solver, make_params
+
+    def kw(Ha):
+        k = dict(wall_lo=(0, 1, 1), wall_hi=(0, 1, 1), gamma=0.1, nu=0.1, F=(1e-6, 0, 0), storage="f32c")
+        if Ha > 0:
+            L = (n - 2) / 2
+            k.update(induction=1, gamma_m=0.1, eta=0.1, chi=0.01, mu=1.0, B0=(0, Ha * math.sqrt(0.1 * 0.1) / L, 0))
+        return k
+
+    has = (0.0, 5.0, 0.0, 5.0)
+    B = Batch([make_params(n, n, n, **kw(h)) for h in has])
+    B.set_launch(256, 2)
+    _, _, sec = B.solve(1e-300, levels, use_graph=False)
+    B.close()
+    del B
+    single = 0.0
+    for h in has:
+        G = Solver(n, n, n, **kw(h))
+        G.step(21)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.step(100)
+        e1.record()
+        e1.synchronize()
+        single += e0.elapsed_time(e1) / 100
+        G.close()
+    return {"metric": "device ms per level: four %d^3 F32C ducts (two coupled) in one batch launch vs single "
+                      "contexts" % n, "batch_ms_per_level": round(sec / levels * 1e3, 4),
+            "single_sum_ms_per_level": round(single, 4), "higher_is_better": False, "data": "synthetic",
+            "dtype": "f32", "launch": {"block_threads": 256, "blocks_per_sm": 2, "levels": levels}}
 
 
 def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
@@ -1482,6 +1521,8 @@ def main():
         line = run_batch(args, rank, ws)
     elif args.workload == "batch-single":
         line = batch_against_single()
+    elif args.workload == "batch-small":
+        line = batch_small()
     elif args.workload == "sweeps":
         line = run_sweeps(args, rank, ws)
     elif args.workload == "coupled":
