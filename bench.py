@@ -48,7 +48,7 @@ DUCT = dict(nx=512, ny=256, nz=256, gamma=0.1, nu=0.5, F0=1e-6)
 # choice launches (PLAIN_STEP_KERNEL), per fluid node, from `ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum -c 1`: BF16 on one launch of the
 # timed 512 x 256 x 256 duct itself (33,032,192 fluid nodes; 79.9 B against
-# the algorithmic 80 B; profiles/step_pair_kernel_bf16_duct.md); F16 and F32
+# the algorithmic 80 B); F16 and F32
 # on the 256 x 128 x 128 duct (4,064,256 fluid nodes), whose 335 MB state
 # leaves part of the written data in L2 (below the algorithmic 80 / 156 B),
 # scaled by fluid nodes.
@@ -1395,12 +1395,9 @@ def adjoint_duct(n: int, storage: str = "f32c"):
     return G, F, fluid
 
 
-# DRAM bytes (read + write) per fluid node of one adjoint launch, from `ncu --metrics
-# dram__bytes_read.sum,dram__bytes_write.sum -k regex:adjoint_kernel -s 40 -c 1` on the 96^3 coupled
-# duct (848,256 fluid nodes; profiles/adjoint_kernel_hartmann_duct.md).  The captured launch was a
-# convergence-check iteration, which also reads and writes the 12 B gradient snapshot per node.
-# DRAM bytes of one plain steady-adjoint launch per fluid node: ncu on the
-# 128^3 bench duct (2,032,128 fluid nodes), read + write
+# DRAM bytes of one plain steady-adjoint launch per fluid node: `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum -k regex:adjoint_kernel -s 41 -c 1` on the 128^3
+# bench duct (2,032,128 fluid nodes), read + write
 ADJ_TRAFFIC_B_PER_FLUID_NODE = (479625472 + 339030016) / 2032128
 
 
