@@ -520,6 +520,10 @@ def variants(args, hbm_peak, stream):
         del G
         torch.cuda.empty_cache()
     out["batch_64_ducts_bounded"] = batch_bounded(hbm_peak)
+    try:
+        out["adjoint_steady_128_bounded"] = adjoint_bounded(hbm_peak)
+    except Exception as e:       # reported in the line, not fatal to it
+        out["adjoint_steady_128_bounded"] = {"error": str(e)[:300]}
     out["time_to_1e-8_hartmann_64x64x8"] = time_to_solution()
     # the 2D lattices: the fused D2Q9 + D2Q5 step on the 4096^2 Hartmann channel
     for st in ("f32", "bf16"):
@@ -643,6 +647,37 @@ def batch_small(n: int = 96, levels: int = 20):
                       "contexts" % n, "batch_ms_per_level": round(sec / levels * 1e3, 4),
             "single_sum_ms_per_level": round(single, 4), "higher_is_better": False, "data": "synthetic",
             "dtype": "f32", "launch": {"block_threads": 256, "blocks_per_sm": 2, "levels": levels}}
+
+
+def adjoint_bounded(hbm_peak: float, n: int = 128, fwd_steps: int = 500, iters: int = 500):
+    """The steady adjoint iteration of the adjoint workload (n^3 Hartmann
+    duct, F32C state, FP32 cotangents), bounded: glbe_adjoint_steady for
+    `iters` iterations at the state `fwd_steps` steps from rest (an iteration
+    costs the same at any state; the full workload first solves to 1e-7).
+    Device time per iteration, including the one linearisation launch and
+    the finalize every 10 iterations."""
+    import torch
+    G, F, fluid = adjoint_duct(n)
+    G.step(fwd_steps)
+    G.adjoint_steady(None, tol=1e-30, max_iters=10)      # workspace allocated outside the timed region
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, st, it, _ = G.adjoint_steady(None, tol=1e-30, max_iters=iters)
+    e1.record(stream)
+    e1.synchronize()
+    # stopped by max_iters (a multiple of 10): all `iters` iterations ran; `it`
+    # is the last level whose gradient change was evaluated
+    per_it = e0.elapsed_time(e1) / 1e3 / iters
+    bpn = adjoint_bytes_per_node(True)
+    G.close()
+    del G, F
+    torch.cuda.empty_cache()
+    return {"iterations": iters, "last_evaluated": it, "ms_per_iteration": round(per_it * 1e3, 4),
+            "bytes_per_node": bpn,
+            "mlups": round(fluid / per_it / 1e6, 1), "hbm_frac": round(bpn * fluid / per_it / 1e9 / hbm_peak, 4),
+            "status": st, "note": "stopped at max_iters by design (status 4); one linearisation launch included"}
 
 
 def hartmann_analytic(ny, Ha, F=1e-6, nu=0.01):
