@@ -174,3 +174,26 @@ def test_2d_init_rejects_null_and_small_workspace_and_null_context(lib):
     assert lib.glbe2d_sync(None) == glbe.GLBE_ERR_ARG
     assert lib.glbe2d_set_force(None, None) == glbe.GLBE_ERR_ARG
     lib.glbe2d_destroy(None)
+
+
+def test_adjoint_workspace_holds_cotangents_and_linearisation_rows(lib):
+    """Steady adjoint: two cotangent buffers of 43N floats and the 16N
+    linearisation rows of the fixed state (7N without induction); the
+    unrolled form adds ceil(nsteps/K) checkpoints and min(K, nsteps)
+    recomputed states instead of the rows."""
+    from paper_0809_4730_gb300 import glbe
+    pm = _params(induction=1, gamma_m=0.5, eta=0.01, chi=0.1)
+    pf = _params()
+    N = 8 * 10 * 6
+    steady_m = glbe.glbe_adjoint_workspace_bytes(pm, 0, 1)
+    steady_f = glbe.glbe_adjoint_workspace_bytes(pf, 0, 1)
+    assert steady_m >= 2 * 43 * N * 4 + 16 * N * 4
+    assert steady_f >= 2 * 43 * N * 4 + 7 * N * 4
+    assert steady_m - steady_f >= 9 * N * 4 - 256
+    state_m = 19 * N * 4 + 21 * N * 4 + 3 * N * 4
+    unrolled = glbe.glbe_adjoint_workspace_bytes(pm, 200, 20)
+    assert unrolled >= 2 * 43 * N * 4 + (10 + 20) * state_m
+    with pytest.raises(glbe.GlbeError):
+        glbe.glbe_adjoint_workspace_bytes(pm, -1, 1)
+    with pytest.raises(glbe.GlbeError):
+        glbe.glbe_adjoint_workspace_bytes(pm, 10, 0)
