@@ -113,9 +113,10 @@ typedef struct {
     int variant;              /* kernel form: 0 = automatic (on grids without walls along x and an even
                                  nx, without induction, with BF16 or F16 storage: the paired form,
                                  as measured faster; else one node per thread; with induction the F32C
-                                 steps, the F32 and BF16 residual steps and the FP32 cavity steps
-                                 update a node in two passes, induction then flow, on grids of more
-                                 than two resident waves: the one-pass results bit for bit);
+                                 steps and the F32 and BF16 residual steps update a node in two
+                                 passes, induction then flow, on grids of more than two resident
+                                 waves, and so do the FP32 cavity steps: the one-pass results bit for
+                                 bit);
                                  1 = one node per thread; 2 = two x-adjacent
                                  nodes per thread with packed FP32x2 arithmetic (needs an even nx and
                                  no walls along x, else the one-node form is used); 3 = tiles of 128
